@@ -1,0 +1,249 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+identities (Eq. 2 pair sum vs the mean-field Eqs. 5-7), the definition of a
+force as minus the gradient of the Hamiltonians of Eqs. 1-3 (central finite
+differences), the order and time reversibility of the Eq. 4 splitting (exact
+harmonic-oscillator flow, Delta t^4 energy-error slope), conservation laws that
+follow from pair antisymmetry, special cases with known answers, and finite
+differences of the discrete adjoint.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1212_0262_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _state(model, N, seed):
+    if model == 0:
+        return inputs.waterbag(N, seed)
+    if model == 1:
+        return inputs.ring_state(N, seed)
+    return inputs.disk_state(N, seed)
+
+
+# ------------------------------------------------------------ Eq. 4 -------
+
+def test_yoshida_matches_published_weights(ora):
+    B0, B1, D0, D1 = ora.yoshida()
+    vals = {}
+    with open(os.path.join(GOLDEN, "yoshida_coefficients.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    assert abs(D0 - vals["w1"]) < 1e-14
+    assert abs(D1 - vals["w0"]) < 1e-14
+    assert abs(B0 - vals["w1"] / 2) < 1e-14
+    assert abs(B1 - (vals["w0"] + vals["w1"]) / 2) < 1e-14
+
+
+def test_yoshida_consistency_and_order_conditions(ora):
+    B0, B1, D0, D1 = ora.yoshida()
+    assert abs(2 * B0 + 2 * B1 - 1.0) < 1e-15      # kicks sum to one step
+    assert abs(2 * D0 + D1 - 1.0) < 1e-15          # drifts sum to one step
+    assert abs(2 * D0 ** 3 + D1 ** 3) < 1e-14      # third-order error cancels
+
+
+def test_harmonic_local_error_is_fifth_order(ora):
+    """One step of the oracle on q'' = -q against the exact rotation: the local
+    error is O(dt^5), so halving dt divides it by 32."""
+    q0, p0 = np.array([1.0]), np.array([0.3])
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        q, p = ora.step(ora.HARMONIC, q0, p0, 0.0, h, 1)
+        qe = q0[0] * math.cos(h) + p0[0] * math.sin(h)
+        pe = -q0[0] * math.sin(h) + p0[0] * math.cos(h)
+        errs.append(math.hypot(q[0] - qe, p[0] - pe))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 28 < r1 < 36 and 28 < r2 < 36, (errs, r1, r2)
+
+
+def test_harmonic_global_error_is_fourth_order(ora):
+    q0, p0 = np.array([1.0]), np.array([0.0])
+    errs = []
+    for n in (20, 40, 80):
+        q, p = ora.step(ora.HARMONIC, q0, p0, 0.0, 4.0 / n, n)
+        errs.append(abs(q[0] - math.cos(4.0)) + abs(p[0] + math.sin(4.0)))
+    assert 14 < errs[0] / errs[1] < 18 and 14 < errs[1] / errs[2] < 18, errs
+
+
+def test_energy_error_slope_is_four_hmf_waterbag(ora):
+    """Max |E(t) - E0| over a fixed time window scales as dt^4 (HMF water-bag)."""
+    q0, p0 = inputs.waterbag(500, 11)
+    e0 = ora.energy(ora.HMF, q0, p0)
+    T = 3.2
+    dts = [0.2, 0.1, 0.05, 0.025]
+    errs = []
+    for dt in dts:
+        q, p = q0.copy(), p0.copy()
+        worst = 0.0
+        for _ in range(int(round(T / dt))):
+            q, p = ora.step(ora.HMF, q, p, 0.0, dt, 1)
+            worst = max(worst, abs(ora.energy(ora.HMF, q, p) - e0))
+        errs.append(worst)
+    slope = np.polyfit(np.log(dts), np.log(errs), 1)[0]
+    assert 3.7 < slope < 4.3, (errs, slope)
+
+
+def test_time_reversibility(ora):
+    """n steps, negate p, n steps, negate p: back to the start (Sec. 3, Eq. 4)."""
+    for model, eps in ((0, 0.0), (1, 0.01), (2, 1e-3)):
+        q0, p0 = _state(model, 32, 5 + model)
+        q, p = ora.step(model, q0, p0, eps, 0.02, 10)
+        q, p = ora.step(model, q, -p, eps, 0.02, 10)
+        assert np.max(np.abs(q - q0)) < 1e-12
+        assert np.max(np.abs(-p - p0)) < 1e-12
+
+
+# ------------------------------------------------- models (Eqs. 1-3, 5-7) --
+
+@pytest.mark.parametrize("N", [1, 2, 7, 64])
+def test_hmf_meanfield_equals_pairwise(ora, N):
+    q, _ = inputs.waterbag(N, 100 + N, -3.0, 3.0)
+    f_mf = ora.force(ora.HMF, q)
+    f_pw = ora.force_hmf_pairwise(q)
+    scale = ora.force_abs(ora.HMF, q) + 1e-300
+    assert np.max(np.abs(f_mf - f_pw) / np.maximum(scale, 1.0 / N)) < 1e-13
+    v_mf = ora.potential(ora.HMF, q)
+    v_pw = ora.potential_hmf_pairwise(q)
+    assert abs(v_mf - v_pw) <= 1e-13 * max(1.0, N)
+
+
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5)])
+def test_force_is_minus_gradient_of_potential(ora, model, eps):
+    N = 12
+    q, _ = _state(model, N, 21)
+    f = ora.force(model, q, eps)
+    h = 1e-5
+    fd = np.empty_like(q)
+    for k in range(q.size):
+        qp, qm = q.copy(), q.copy()
+        qp[k] += h
+        qm[k] -= h
+        fd[k] = -(ora.potential(model, qp, eps) - ora.potential(model, qm, eps)) / (2 * h)
+    scale = np.max(np.abs(f))
+    assert np.max(np.abs(fd - f)) < 2e-7 * scale, np.max(np.abs(fd - f)) / scale
+
+
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+def test_total_momentum_conserved(ora, model, eps):
+    N = 40
+    q0, p0 = _state(model, N, 31)
+    q, p = ora.step(model, q0, p0, eps, 0.05, 20)
+    d = 2 if model == 2 else 1
+    for c in range(d):
+        tot0 = p0[c * N:(c + 1) * N].sum()
+        tot = p[c * N:(c + 1) * N].sum()
+        assert abs(tot - tot0) < 1e-13 * np.abs(p0).sum() * 20
+
+
+def test_angular_momentum_conserved_2d(ora):
+    N = 40
+    q0, p0 = inputs.disk_state(N, 41)
+    q, p = ora.step(2, q0, p0, 1e-3, 0.05, 20)
+
+    def lz(q, p):
+        return np.sum(q[:N] * p[N:] - q[N:] * p[:N])
+
+    assert abs(lz(q, p) - lz(q0, p0)) < 1e-12 * np.sum(np.abs(q0) * np.abs(p0).max()) * 20
+
+
+def test_special_cases(ora):
+    # one HMF particle feels no force and drifts freely
+    q, p = ora.step(ora.HMF, np.array([0.7]), np.array([0.25]), 0.0, 0.1, 10)
+    assert ora.force(ora.HMF, np.array([0.7]))[0] == 0.0
+    assert abs(q[0] - (0.7 + 10 * 0.1 * 0.25)) < 1e-14 and p[0] == 0.25
+    # equally spaced angles: M = 0 and zero force (HMF and Ring, by symmetry)
+    N = 64
+    lat = 2 * np.pi * np.arange(N) / N - np.pi
+    assert np.max(np.abs(ora.force(ora.HMF, lat))) < 1e-15
+    fr = ora.force(ora.RING, lat, 0.01)
+    assert np.max(np.abs(fr)) < 1e-13 * np.max(ora.force_abs(ora.RING, lat, 0.01))
+    # two bodies: equal and opposite forces
+    for model, eps, q in ((1, 0.01, np.array([0.3, -0.4])),
+                          (2, 1e-3, np.array([0.1, -0.2, 0.05, 0.3]))):
+        f = ora.force(model, q, eps)
+        if model == 1:
+            assert abs(f[0] + f[1]) < 1e-16
+            assert f[0] < 0  # attraction: particle 0 sits at larger angle
+        else:
+            assert abs(f[0] + f[1]) < 1e-16 and abs(f[2] + f[3]) < 1e-16
+            assert f[0] < 0 and f[2] > 0  # pulled toward particle 1
+    # particles at rest have K = 0
+    assert ora.kinetic(np.zeros(10)) == 0.0
+
+
+def test_two_body_energy_conservation(ora):
+    q0 = np.array([0.5, -0.5, 0.0, 0.0])
+    p0 = np.array([0.0, 0.0, 0.4, -0.4])
+    e0 = ora.energy(2, q0, p0, 1e-3)
+    q, p = ora.step(2, q0, p0, 1e-3, 0.01, 200)
+    assert abs(ora.energy(2, q, p, 1e-3) - e0) < 1e-7 * abs(e0)
+
+
+# --------------------------------------------- derivatives and the adjoint -
+
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+def test_hvp_matches_finite_difference_of_force(ora, model, eps):
+    N = 16
+    q, _ = _state(model, N, 51)
+    v = inputs.uniform(52, 0, q.size) - 0.5
+    jv = ora.hvp(model, q, v, eps)
+    h = 1e-6
+    fd = (ora.force(model, q + h * v, eps) - ora.force(model, q - h * v, eps)) / (2 * h)
+    assert np.max(np.abs(jv - fd)) < 1e-7 * np.max(np.abs(jv))
+    if model == 0:
+        jmf = ora.hvp_hmf_meanfield(q, v)
+        assert np.max(np.abs(jmf - jv)) < 1e-13 * np.max(np.abs(jv))
+
+
+@pytest.mark.parametrize("model,eps", [(1, 0.01), (2, 1e-3)])
+def test_dforce_deps_matches_finite_difference(ora, model, eps):
+    q, _ = _state(model, 16, 61)
+    h = 1e-7 * eps
+    fd = (ora.force(model, q, eps + h) - ora.force(model, q, eps - h)) / (2 * h)
+    de = ora.dforce_deps(model, q, eps)
+    assert np.max(np.abs(de - fd)) < 1e-6 * np.max(np.abs(de))
+
+
+@pytest.mark.parametrize("model,eps,obs", [(0, 0.0, 0), (0, 0.0, 1), (1, 0.01, 0), (1, 0.01, 1),
+                                           (2, 1e-3, 0)])
+def test_adjoint_matches_central_differences(ora, model, eps, obs):
+    N, dt, ns = 12, 0.05, 6
+    q0, p0 = _state(model, N, 71 + model)
+    val, gq, gp, ge = ora.grad(model, q0, p0, eps, dt, ns, obs)
+    assert abs(val - ora.observable_after(model, q0, p0, eps, dt, ns, obs)) < 1e-14 * abs(val)
+    h = 1e-6
+    # every component
+    for g, which in ((gq, 0), (gp, 1)):
+        fd = np.empty_like(g)
+        for k in range(g.size):
+            a, b = q0.copy(), p0.copy()
+            (a if which == 0 else b)[k] += h
+            vp = ora.observable_after(model, a, b, eps, dt, ns, obs)
+            (a if which == 0 else b)[k] -= 2 * h
+            vm = ora.observable_after(model, a, b, eps, dt, ns, obs)
+            fd[k] = (vp - vm) / (2 * h)
+        assert np.max(np.abs(fd - g)) < 1e-6 * max(np.max(np.abs(g)), 1e-3), (which, fd, g)
+    if model != 0:
+        he = 1e-6 * eps
+        fde = (ora.observable_after(model, q0, p0, eps + he, dt, ns, obs)
+               - ora.observable_after(model, q0, p0, eps - he, dt, ns, obs)) / (2 * he)
+        assert abs(fde - ge) < 1e-5 * max(abs(ge), 1e-6), (fde, ge)
+    else:
+        assert ge == 0.0
+
+
+def test_step_matches_grad_forward_pass(ora):
+    """The adjoint's forward pass re-evaluates f at every kick; its trajectory
+    must be identical to the first-same-as-last step list."""
+    q0, p0 = inputs.ring_state(20, 81)
+    q, p = ora.step(1, q0, p0, 0.01, 0.05, 7)
+    val, *_ = ora.grad(1, q0, p0, 0.01, 0.05, 7, 0)
+    assert val == ora.kinetic(p)
