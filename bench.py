@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""Throughput of the force-evaluation hot path (one JSON line on rank 0).
+
+Default workload: HMF model, N = 50,000,000, water-bag initial state
+(theta ~ U[-1,1), p ~ U[-1.2,1.2), seed 2), dt = 0.1; one benchmark step is one
+integrator step of Sec. 3 (three fused force + kick + drift stages).  Metric:
+particle-steps/s on the FP32-sine/FP64-state ("mixed") path, with the FP64 path
+and the relative energy errors of both reported beside it.
+
+Other workloads (--workload ring | grav2d) time the all-pairs kernels on the
+Ring (N = 131,072, eps = 0.01, dt = 0.05) and 2D (N = 262,144, eps = 1e-4,
+dt = 0.01) systems in pair-interactions/s (3 N^2 per step).
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Under torchrun (N > 1 GPUs) every rank runs an independent replica (the systems
+are independent; weak scaling) and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s & particle-steps/s, mixed vs FP64, at stated energy error"
+WORKLOADS = {
+    "hmf": dict(model=0, N=50_000_000, eps=0.0, dt=0.1, seed=2, unit="particle-steps/s",
+                name="HMF water-bag N=50,000,000 dt=0.1 (fused reduction+kick/drift)"),
+    "ring": dict(model=1, N=131_072, eps=0.01, dt=0.05, seed=3, unit="pair-interactions/s",
+                 name="Ring N=131,072 eps=0.01 dt=0.05 (all-pairs)"),
+    "grav2d": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
+                   name="2D self-gravitating N=262,144 eps=1e-4 dt=0.01 (all-pairs)"),
+}
+# algorithmic bytes per particle per fused HMF stage: read + write FP64 theta and p
+HMF_BYTES_PER_PARTICLE_STAGE = 32
+# FP32-pipe operations and SFU operations per pair in the mixed pair kernels
+PAIR_OPS = {1: (8, 1), 2: (6, 1)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hmf", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    a = ap.parse_args()
+    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3)}[a.workload]
+    if a.steps is None:
+        a.steps = dflt[0]
+    if a.warmup is None:
+        a.warmup = dflt[1]
+    return a
+
+
+# ------------------------------------------------------------ utilities ---
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def src_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, files, units: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `units`
+    (particles), or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("src_digest") != src_digest(files):
+        return None
+    return rec["dram_bytes_per_launch"] * units / rec["units"]
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [l.split(",") for l in self.tmp.read().splitlines() if l.count(",") >= 8]
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    seen.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(seen),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].strip()
+                                                          not in ("", "[N/A]"))}
+
+
+def device_uuid(dev):
+    import torch
+
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ oracle legs -
+
+def oracle_steps(w, n: int, steps: int, warmup: int = 0):
+    """Run the FP64 CPU oracle on a sample of the workload and return
+    (units processed in the timed steps, seconds, description).
+    HMF: the first n particles' recipe (an n-particle water-bag drawn from the
+    workload's seed), `steps` integrator steps in one call (3 force evaluations
+    per step plus one at the start).  Ring/2D: per step, 3 force evaluations of
+    n sampled rows against all N partners (direct pair sums)."""
+    import numpy as np
+
+    import oracle as ora
+    from paper_1212_0262_gb300 import inputs
+
+    model, N = w["model"], w["N"]
+    if model == 0:
+        q, p = inputs.waterbag(n, w["seed"])
+        if warmup:
+            q, p = ora.step(0, q, p, 0.0, w["dt"], warmup)
+        t0 = time.perf_counter()
+        ora.step(0, q, p, 0.0, w["dt"], steps)
+        el = time.perf_counter() - t0
+        return n * steps, el, f"{n}-particle HMF water-bag (seed {w['seed']}), {steps} oracle steps in one call"
+    q, _ = inputs.default_state(model, N, w["seed"])
+    rows = np.linspace(0, N - 1, n).astype(np.int64)
+    for _ in range(3 * warmup):
+        ora.force_rows(model, q, rows, w["eps"])
+    t0 = time.perf_counter()
+    for _ in range(3 * steps):
+        ora.force_rows(model, q, rows, w["eps"])
+    el = time.perf_counter() - t0
+    return 3 * n * N * steps, el, (f"{n} of {N} rows x {N} partners, 3 force evaluations per step, "
+                                   f"{steps} steps (direct pair sums)")
+
+
+def oracle_sample_size(w, seconds: float, steps: int) -> int:
+    """Sample size so that `steps` oracle steps take about `seconds` here."""
+    model, N = w["model"], w["N"]
+    n0 = 20000 if model == 0 else 2
+    units, el, _ = oracle_steps(w, n0, 1)
+    per_unit = el / units
+    per_step_units = seconds / steps / per_unit
+    n = int(per_step_units if model == 0 else per_step_units / (3 * N))
+    return max(1000 if model == 0 else 1, min(N, n))
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+    n = oracle_sample_size(w, 60.0, K + W)
+    units, el, sample = oracle_steps(w, n, K, W)
+    rate = units / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": w["unit"], "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"]},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": rate, "unit": w["unit"]},
+        "e2e": {"value": rate, "unit": w["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ our path ----
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    from paper_1212_0262_gb300 import System, binding
+    from paper_1212_0262_gb300.system import stage_schedule
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    model, N, K, W = w["model"], w["N"], args.steps, args.warmup
+    sysm = System(model, N, w["eps"], w["dt"], w["seed"] + 1000 * rank, precision=args.prec)
+    sysm.set_stream(stream)
+    e0 = sum(sysm.energy())
+
+    sched = stage_schedule(K)
+    lib = binding.load()
+    h = sysm._h
+
+    def run_schedule(steps, events=None):
+        sc = stage_schedule(steps)
+        with torch.cuda.stream(stream):
+            if events is not None:
+                events[0].record(stream)
+            for k, (b, d) in enumerate(sc):
+                binding.check(lib.md_stage(h, b, d), h)
+                if events is not None:
+                    events[k + 1].record(stream)
+
+    if W:
+        run_schedule(W)
+    flush = None
+    if model != 0:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+
+    sampler = ClockSampler(device_uuid(local))
+    launches0 = sysm.launch_count
+    stage_ms = []
+    if model == 0:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(sched) + 1)]
+        torch.cuda.synchronize()
+        run_schedule(K, ev)
+        ev[-1].synchronize()
+        stage_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(sched))]
+        elapsed_ms = ev[0].elapsed_time(ev[-1])
+    else:
+        # compute-bound kernels on L2-sized inputs: flush L2 between timed steps
+        elapsed_ms = 0.0
+        for s in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))
+            sc = sched[3 * s:3 * s + 3] + ([sched[-1]] if s == K - 1 else [])
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(sc) + 1)]
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                for k, (b, d) in enumerate(sc):
+                    binding.check(lib.md_stage(h, b, d), h)
+                    ev[k + 1].record(stream)
+            ev[-1].synchronize()
+            ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(sc))]
+            stage_ms += ms
+            elapsed_ms += sum(ms)
+    torch.cuda.synchronize()
+    launches = sysm.launch_count - launches0
+    clocks = sampler.stop()
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    e1 = sum(sysm.energy())
+    de_mixed = abs((e1 - e0) / e0)
+
+    if model == 0:
+        units_per_step = N
+        value = ws * N * K / (elapsed_ms * 1e-3)
+        drift_stage = [ms for (b, d), ms in zip(sched, stage_ms) if d != 0.0]
+        avg_ms = sum(drift_stage) / len(drift_stage)
+        peaks, src = measured_peaks()
+        achieved = HMF_BYTES_PER_PARTICLE_STAGE * N / (avg_ms * 1e-3) / 1e9
+        traffic = recorded_traffic("hmf_stage_mixed", ["paper_1212_0262_gb300/csrc/hmf.cu",
+                                                       "paper_1212_0262_gb300/csrc/md_internal.cuh"], N)
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "kernel": f"hmf_stage_kernel<{'mixed' if args.prec == 'mixed' else 'fp64'}, kick+drift>",
+                    "algorithmic_bytes_per_launch": HMF_BYTES_PER_PARTICLE_STAGE * N,
+                    "avg_launch_ms": avg_ms, "launches": len(drift_stage), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        units_per_step = 3 * N * N
+        value = ws * 3 * N * N * K / (elapsed_ms * 1e-3)
+        avg_ms = sum(stage_ms) / len(stage_ms)
+        rates = np.zeros(17)
+        binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 17)
+        nsm = rates[0]
+        fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
+        sfu_rate = rates[5] if model == 1 else rates[7]
+        fops, sops = PAIR_OPS[model]
+        pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops)
+        mhz = clocks.get("sm_mhz") or rates[2]
+        peak = nsm * pairs_per_clk * mhz * 1e6
+        achieved = N * N / (avg_ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pair-interactions/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": f"pair_stage_kernel<{'Ring' if model == 1 else '2D'}, {args.prec}>",
+                    "peak_derivation": {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
+                                        "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
+                                        "sfu_ops_per_pair": sops, "sm_mhz": mhz},
+                    "avg_launch_ms": avg_ms}
+
+    # FP64 path on the same workload (few steps) and the matching mixed energy error
+    extra = {}
+    if not args.no_fp64 and rank == 0:
+        ksh = 10 if model == 0 else 2
+        res = {}
+        for prec in ("fp64", "mixed"):
+            with System(model, N, w["eps"], w["dt"], w["seed"], precision=prec) as s2:
+                s2.set_stream(stream)
+                e_a = sum(s2.energy())
+                s2.step(1)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s2.step(ksh)
+                b.record(stream)
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                e_b = sum(s2.energy())
+                units = N * ksh if model == 0 else 3 * N * N * ksh
+                res[prec] = {"value": units / (ms * 1e-3), "ms_per_step": ms / ksh,
+                             "rel_energy_error": abs((e_b - e_a) / e_a), "steps": ksh + 1}
+        extra["fp64_path"] = res["fp64"]
+        extra["energy_error"] = {"mixed_after_%d_steps" % (res["mixed"]["steps"]): res["mixed"]["rel_energy_error"],
+                                 "fp64_after_%d_steps" % (res["fp64"]["steps"]): res["fp64"]["rel_energy_error"],
+                                 "mixed_timed_run": de_mixed, "timed_run_steps": W + K}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if rank == 0:
+        n = sysm.dim * N
+        qh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        ph = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        sysm.get_state_device  # noqa: B018  (API presence)
+        qn, pn = qh.numpy(), ph.numpy()
+        lib.md_get_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data))
+        ke = K if model == 0 else max(1, min(K, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.check(lib.md_set_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data)), h)
+        binding.check(lib.md_step(h, ke), h)
+        kk, vv = ctypes.c_double(), ctypes.c_double()
+        binding.check(lib.md_energy(h, ctypes.byref(kk), ctypes.byref(vv)), h) if model == 0 else None
+        binding.check(lib.md_get_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data)), h)
+        el = time.perf_counter() - t0
+        e2e = {"value": (N * ke if model == 0 else 3 * N * N * ke) / el, "unit": w["unit"],
+               "h2d_bytes_per_step": 2 * 8 * n / ke, "d2h_bytes_per_step": (2 * 8 * n + (16 if model == 0 else 0)) / ke,
+               "steps": ke, "note": "md_set_state(host) + md_step + md_energy + md_get_state(host), wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ksteps = 4 if model == 0 else 1
+        n = oracle_sample_size(w, 12.0, ksteps)
+        units, el, sample = oracle_steps(w, n, ksteps)
+        cpu = {"value": units / el, "unit": w["unit"], "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": el}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": elapsed_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 state / f32 " + ("sin,cos" if model == 0 else "pair arithmetic") if args.prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "N": N, "eps": w["eps"], "dt": w["dt"], "seed": w["seed"],
+                       "precision": args.prec, "parallelism": f"replicas x{ws}",
+                       "l2": "state 800 MB > L2 (no flush needed)" if model == 0 else "L2 flushed (256 MB write) between timed steps"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "rel_energy_error": de_mixed,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    sysm.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        ws, rank, _ = dist_info()
+        return
+    run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

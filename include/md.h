@@ -1,0 +1,204 @@
+/*
+ * md.h -- C ABI of libmd, a GB300 (sm_103a) implementation of the force
+ * evaluation inside the fourth-order symplectic integrator of arXiv 1212.0262
+ * (Rocha Filho, "Molecular dynamics for long-range interacting systems on
+ * Graphic Processing Units") for three models:
+ *
+ *   MD_HMF     Hamiltonian Mean Field, Sec. 2 Eq. 2; mean-field force Eqs. 5-7
+ *   MD_RING    Ring model, Sec. 2 Eq. 1; pair force Eqs. 8-9 (sign: minus the
+ *              gradient of Eq. 1)
+ *   MD_GRAV2D  2D self-gravitating particles, Sec. 2 Eq. 3 (natural log)
+ *
+ * Conventions shared by every call:
+ *  - Return value: MD_OK (0) or a positive MD_E* code.  No C++ exception crosses
+ *    the ABI.  The message of the last failure is md_last_error(ctx) (or
+ *    md_last_error(NULL) when no context exists yet, e.g. md_init failing).
+ *  - Layout: positions q and momenta p are structure-of-arrays of dim*N doubles,
+ *    dim = 1 for HMF and Ring (q = theta) and dim = 2 for 2D
+ *    (q = [x_0..x_{N-1}, y_0..y_{N-1}], p = [px..., py...]).
+ *  - "host" pointers are ordinary (pageable or pinned) CPU memory owned by the
+ *    caller and only read or written during the call.  "device" pointers are
+ *    CUDA global memory on the context's device, owned by the caller.
+ *  - Work is queued on the context's stream (md_set_stream; default: a stream the
+ *    context creates).  Calls that return host values synchronise that stream.
+ *  - A context is used by one host thread at a time.  Contexts are independent.
+ *  - Floating point: the state (q, p), kicks, drifts and every reduction are FP64.
+ *    MD_FP64 evaluates pair and mean-field forces in FP64; MD_MIXED evaluates
+ *    the pair arithmetic (Ring, 2D) and the sines and cosines (HMF) in FP32 and
+ *    accumulates per-particle sums in FP64 per tile (Sec. 3.2, last paragraph;
+ *    Sec. 5).
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* models */
+#define MD_HMF 0
+#define MD_RING 1
+#define MD_GRAV2D 2
+
+/* precisions */
+#define MD_FP64 0
+#define MD_MIXED 1
+
+/* status codes */
+#define MD_OK 0
+#define MD_EINVAL 1     /* bad argument (size, model, NULL, value out of range) */
+#define MD_ENOMEM 2     /* device or host allocation failed */
+#define MD_ECUDA 3      /* a CUDA call failed (message has the CUDA error string) */
+#define MD_ETIMEOUT 4   /* a bounded device-side wait gave up */
+#define MD_ENONFINITE 5 /* the state or an observable is NaN or infinite */
+#define MD_ESTATE 6     /* call not valid in the context's current state */
+
+/* initial-condition kinds for md_set_ic (all seeded, counter-based SplitMix64) */
+#define MD_IC_WATERBAG 0     /* params[4] = {th_lo, th_hi, p_lo, p_hi}: theta~U[th_lo,th_hi), p~U[p_lo,p_hi) */
+#define MD_IC_RING 1         /* params[1] = {sigma}: theta~U[-pi,pi), p~N(0,sigma^2) */
+#define MD_IC_DISK 2         /* params[1] = {sigma}: uniform unit disk, p~N(0,sigma^2) per component */
+#define MD_IC_ANNULUS 3      /* params[2] = {r1, r2}: uniform annulus r1<=r<r2, at rest */
+#define MD_IC_UNIFORM_REST 4 /* params unused: theta~U[-pi,pi), at rest */
+
+/* observables for md_grad */
+#define MD_OBS_KINETIC 0       /* O = (1/2) sum p^2 at the final time */
+#define MD_OBS_MAGNETIZATION 1 /* O = |M| of Eq. 7 at the final time (HMF, Ring) */
+
+typedef struct md_ctx md_ctx;
+typedef struct md_batch md_batch;
+
+/* Create a system of N particles of `model` with softening eps (Ring, 2D; must be
+ * > 0 there, ignored for HMF but must be >= 0) and time step dt (Sec. 3, Eq. 4),
+ * on the current CUDA device.  The state is drawn from `seed` with the model's
+ * default recipe: water-bag theta~U[-1,1), p~U[-1.2,1.2) (HMF); theta~U[-pi,pi),
+ * p~N(0,0.5^2) (Ring); uniform unit disk, p~N(0,0.3^2) per component (2D).
+ * Precision defaults to MD_FP64.  Returns NULL on failure (see md_last_error(NULL)).
+ * The context owns its device memory until md_free. */
+md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed);
+
+/* Release a context and its device memory.  NULL is ignored. */
+void md_free(md_ctx *ctx);
+
+/* Message of the last failure on ctx, or of the last failure of a call without a
+ * context when ctx is NULL.  Never NULL; owned by the library. */
+const char *md_last_error(const md_ctx *ctx);
+
+/* MD_FP64 or MD_MIXED.  Takes effect for the next md_step / md_force / md_grad. */
+int md_set_precision(md_ctx *ctx, int precision);
+
+/* Queue all later work of ctx on `stream` (a cudaStream_t; NULL = legacy default
+ * stream).  The caller keeps ownership of the stream. */
+int md_set_stream(md_ctx *ctx, void *stream);
+
+/* Change the time step (Sec. 3, Eq. 4).  dt may be negative (backward flow). */
+int md_set_dt(md_ctx *ctx, double dt);
+
+/* Tuning knobs of the kernels (used by the autotuner; defaults are sensible):
+ *   "r_mixed"          i-particles per thread of the FP32 pair kernels (4 or 8)
+ *   "r_fp64"           i-particles per thread of the FP64 pair kernels (2 or 4)
+ *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
+ *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = occupancy limit)
+ * MD_EINVAL for an unknown key or value. */
+int md_set_tuning(md_ctx *ctx, const char *key, int64_t value);
+
+/* Redraw the state with recipe `kind` (MD_IC_*) and `params` from `seed`.
+ * Draw order: positions (counters 0..dim*N-1; the disk and annulus use two
+ * counters per particle), then momenta; Gaussians by Box-Muller from two
+ * consecutive counters. */
+int md_set_ic(md_ctx *ctx, int kind, const double *params, uint64_t seed);
+
+/* Copy dim*N positions and momenta from host (set) or to host (get). */
+int md_set_state(md_ctx *ctx, const double *q, const double *p);
+int md_get_state(md_ctx *ctx, double *q, double *p);
+
+/* Same with device pointers on the context's device (stream-ordered, async). */
+int md_set_state_device(md_ctx *ctx, const double *q, const double *p);
+int md_get_state_device(md_ctx *ctx, double *q, double *p);
+
+/* Advance nsteps >= 0 integration steps of Sec. 3 (items 1-12 with Eq. 4's
+ * splitting; three force evaluations per step, the force at the end of a step
+ * reused by the next one).  Queued on the stream; returns without waiting.
+ * After the call p and q sit on the step boundary. */
+int md_step(md_ctx *ctx, int64_t nsteps);
+
+/* One fused integrator stage (Sec. 3 step list): evaluate the force at the
+ * current positions, kick p += b*dt*f, then drift q += d*dt*p (d == 0: kick only,
+ * and for Ring/2D the force is kept for the next md_step).  md_step(n) is the
+ * sequence (B0,D0) (B1,D1) (B1,D0), then n-1 times (2*B0,D0) (B1,D1) (B1,D0),
+ * then (B0,0), with the Eq. 4 constants B0 = w1/2, B1 = (w0+w1)/2, D0 = w1,
+ * D1 = w0 (w1 = 1/(2-2^(1/3)), w0 = -2^(1/3)/(2-2^(1/3))).  Asynchronous. */
+int md_stage(md_ctx *ctx, double b, double d);
+
+/* The four constants B0, B1, D0, D1 of Eq. 4 used by md_step (host array of 4). */
+void md_yoshida(double *c4);
+
+/* Forces at the current positions (Eq. 6 for HMF, minus the gradient of Eqs. 1/3
+ * for Ring/2D) into host f[dim*N], at the context's precision.  Synchronous. */
+int md_force(md_ctx *ctx, double *f);
+
+/* Same into device f[dim*N] (stream-ordered). */
+int md_force_device(md_ctx *ctx, double *f);
+
+/* Total kinetic energy K = (1/2) sum p^2 and potential V (Eq. 5 for HMF; the
+ * i<j pair sums of Eqs. 1 and 3 for Ring and 2D), both in FP64.  Synchronous.
+ * MD_ENONFINITE if either is not finite.  Either pointer may be NULL. */
+int md_energy(md_ctx *ctx, double *K, double *V);
+
+/* Magnetization (Mx, My) of Eq. 7 in FP64 (HMF and Ring; MD_EINVAL for 2D). */
+int md_magnetization(md_ctx *ctx, double *mx, double *my);
+
+/* Gradient of an observable of the state reached after nsteps from the current
+ * state, with respect to that current state and eps: a pure function of the
+ * context (its state is unchanged afterwards).  Discrete adjoint of md_step's
+ * map: reversed integration rebuilds the kick positions, restarting from an FP64
+ * checkpoint stored every `checkpoint_every` steps (>= 1).
+ * grad_q, grad_p: host arrays of dim*N (required); grad_eps, value: host scalars
+ * (may be NULL; grad_eps is 0 for HMF).  Synchronous.  Uses the context's
+ * precision for the force and Jacobian-vector products. */
+int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
+            double *grad_q, double *grad_p, double *grad_eps, double *value);
+
+/* Route the library's device allocations through alloc(bytes, user) and
+ * free(ptr, user) (for example a caching allocator of the host framework).
+ * alloc returns NULL on failure, which the library reports as MD_ENOMEM.
+ * Passing NULL for both restores cudaMalloc / cudaFree.  Applies to allocations
+ * made after the call; memory is freed by the allocator that made it. */
+int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(void *ptr, void *user),
+                     void *user);
+
+/* Wait for all work queued on the context's stream. */
+int md_synchronize(md_ctx *ctx);
+
+/* Number of kernel launches the context has queued since it was created. */
+int64_t md_launch_count(const md_ctx *ctx);
+
+/* ----- batched ensembles: many independent systems advanced together ----- */
+
+/* nsys independent Ring / 2D systems (model[s] in {MD_RING, MD_GRAV2D}) with
+ * N[s] >= 1 particles, softening eps[s] > 0, step dt[s] and default initial
+ * states drawn from seed[s].  All systems share one persistent force launch per
+ * integrator stage and one captured CUDA graph per block of steps.  Precision is
+ * MD_MIXED (FP32 pair arithmetic, FP64 state) unless md_batch_set_precision.
+ * Returns NULL on failure (md_last_error(NULL)). */
+md_batch *md_batch_init(int nsys, const int *model, const int64_t *N, const double *eps,
+                        const double *dt, const uint64_t *seed);
+void md_batch_free(md_batch *b);
+int md_batch_set_precision(md_batch *b, int precision);
+int md_batch_set_stream(md_batch *b, void *stream);
+/* Advance every system by nsteps steps of Sec. 3 (asynchronous). */
+int md_batch_step(md_batch *b, int64_t nsteps);
+/* K[s], V[s] for every system (host arrays of nsys).  Synchronous. */
+int md_batch_energy(md_batch *b, double *K, double *V);
+/* Host state of system s (dim*N[s] doubles each). */
+int md_batch_get_state(md_batch *b, int s, double *q, double *p);
+int md_batch_set_state(md_batch *b, int s, const double *q, const double *p);
+const char *md_batch_last_error(const md_batch *b);
+int64_t md_batch_launch_count(const md_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_H */

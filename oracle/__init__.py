@@ -57,6 +57,7 @@ def _load():
                 "ora_potential": (d, [i32, i64, d, P]),
                 "ora_kinetic": (d, [i64, P]),
                 "ora_force_abs": (None, [i32, i64, d, P, P]),
+                "ora_force_rows": (None, [i32, i64, d, P, ctypes.POINTER(ctypes.c_int64), i64, P, P]),
                 "ora_step": (i32, [i32, i64, d, d, i64, P, P]),
                 "ora_hvp": (None, [i32, i64, d, P, P, P]),
                 "ora_hvp_hmf_meanfield": (None, [i64, P, P, P]),
@@ -143,6 +144,20 @@ def force_abs(model: int, q, eps: float = 0.0) -> np.ndarray:
     out = np.empty_like(q)
     _load().ora_force_abs(model, q.size // dim(model), eps, _p(q), _p(out))
     return out
+
+
+def force_rows(model: int, q, rows, eps: float = 0.0, with_abs: bool = False):
+    """Forces on the listed particles only, shape (dim, len(rows)); with_abs also
+    returns sum_j |f_ij| for those rows."""
+    q = _arr(q)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty(dim(model) * rows.size)
+    ab = np.empty_like(out)
+    _load().ora_force_rows(model, q.size // dim(model), eps, _p(q),
+                           rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rows.size, _p(out), _p(ab))
+    if with_abs:
+        return out.reshape(dim(model), rows.size), ab.reshape(dim(model), rows.size)
+    return out.reshape(dim(model), rows.size)
 
 
 def step(model: int, q, p, eps: float, dt: float, nsteps: int) -> tuple[np.ndarray, np.ndarray]:

@@ -239,6 +239,63 @@ void ora_force_abs(int model, int64_t N, double eps, const double *q, double *ou
   }
 }
 
+/* Forces on the particles listed in rows[0..nrows-1] only (same definitions as
+ * ora_force; HMF uses the mean field of all N angles).  out has nrows*dim
+ * entries: [f_row0.., (fy_row0..)]; out_abs (may be NULL) gets sum_j |f_ij| in
+ * the same layout.  Used to check large systems on samples. */
+void ora_force_rows(int model, int64_t N, double eps, const double *q, const int64_t *rows,
+                    int64_t nrows, double *out, double *out_abs) {
+  if (model == ORA_HMF) {
+    double mx, my, ac = 0.0, as = 0.0;
+    ora_magnetization(N, q, &mx, &my);
+    for (int64_t j = 0; j < N; j++) {
+      ac += fabs(cos(q[j]));
+      as += fabs(sin(q[j]));
+    }
+    for (int64_t r = 0; r < nrows; r++) {
+      double t = q[rows[r]];
+      out[r] = cos(t) * my - sin(t) * mx;
+      if (out_abs) out_abs[r] = (fabs(cos(t)) * as + fabs(sin(t)) * ac) / (double)N;
+    }
+  } else if (model == ORA_RING) {
+    double c = 1.0 / (2.0 * sqrt(2.0) * (double)N);
+    for (int64_t r = 0; r < nrows; r++) {
+      int64_t i = rows[r];
+      double s = 0.0, sa = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double d = q[i] - q[j];
+        double D = 1.0 - cos(d) + eps;
+        s += sin(d) / (D * sqrt(D));
+        sa += fabs(sin(d)) / (D * sqrt(D));
+      }
+      out[r] = -c * s;
+      if (out_abs) out_abs[r] = c * sa;
+    }
+  } else if (model == ORA_GRAV2D) {
+    const double *x = q, *y = q + N;
+    for (int64_t r = 0; r < nrows; r++) {
+      int64_t i = rows[r];
+      double sx = 0.0, sy = 0.0, ax = 0.0, ay = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double dx = x[i] - x[j], dy = y[i] - y[j];
+        double s = dx * dx + dy * dy + eps;
+        sx += dx / s;
+        sy += dy / s;
+        ax += fabs(dx) / s;
+        ay += fabs(dy) / s;
+      }
+      out[r] = -2.0 * sx / (double)N;
+      out[nrows + r] = -2.0 * sy / (double)N;
+      if (out_abs) {
+        out_abs[r] = 2.0 * ax / (double)N;
+        out_abs[nrows + r] = 2.0 * ay / (double)N;
+      }
+    }
+  }
+}
+
 /* ------------------------------------------------------------ integrator -- */
 
 static void kick(int64_t n, double coef, const double *f, double *p) {

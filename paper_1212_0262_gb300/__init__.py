@@ -1,1 +1,14 @@
-"""GB300-native long-range molecular dynamics (HMF, Ring, 2D self-gravitating)."""
+"""GB300-native long-range molecular dynamics after arXiv 1212.0262.
+
+The force evaluation inside the fourth-order symplectic integrator of Sec. 3 for
+the HMF (Eqs. 2, 5-7), Ring (Eqs. 1, 8-9) and 2D self-gravitating (Eq. 3)
+models, as hand-written sm_103a CUDA kernels behind the C ABI of include/md.h.
+"""
+from . import binding
+from .binding import MDError
+from .system import Ensemble, System
+
+HMF, RING, GRAV2D = 0, 1, 2
+FP64, MIXED = 0, 1
+
+__all__ = ["binding", "MDError", "System", "Ensemble", "HMF", "RING", "GRAV2D", "FP64", "MIXED"]

@@ -1,0 +1,434 @@
+// C ABI of libmd: contexts, state I/O, the integrator schedule, observables.
+//
+// Integrator (Sec. 3, Eq. 4 and its step list, items 1-12): a step is
+//   kick(B0) drift(D0) kick(B1) drift(D1) kick(B1) drift(D0) kick(B0)
+// with kick p += b dt f(q) and drift q += d dt p.  Each "stage" kernel fuses
+// one force evaluation with the kick that uses it and the drift that follows,
+// so a step is three stage launches.  The closing kick of a step and the opening
+// kick of the next use the same force (item 12), so inside md_step they merge
+// into one kick with 2 B0; md_step ends with a kick-only stage that leaves p on
+// the step boundary and keeps that force for the next call.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <new>
+#include <unordered_map>
+
+#include "md_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_alloc_mu;
+void *(*g_alloc)(size_t, void *) = nullptr;
+void (*g_free)(void *, void *) = nullptr;
+void *g_alloc_user = nullptr;
+
+int fail_global(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+bool is_finite(double x) { return x == x && x - x == 0.0; }
+
+}  // namespace
+
+int set_err(md_ctx *c, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  g_err = buf;
+  return code;
+}
+
+int cuda_err(md_ctx *c, cudaError_t e, const char *what) {
+  return set_err(c, MD_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Each block remembers the allocator that made it (host-side registry), so a
+// block made before md_set_allocator is released by the allocator that made it.
+namespace {
+struct AllocRec {
+  void (*free_fn)(void *, void *);
+  void *user;
+};
+std::unordered_map<void *, AllocRec> g_blocks;
+}  // namespace
+
+void *dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  void *ptr = nullptr;
+  if (g_alloc) {
+    ptr = g_alloc(bytes, g_alloc_user);
+    if (!ptr) return nullptr;
+    g_blocks[ptr] = AllocRec{g_free, g_alloc_user};
+  } else {
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_blocks[ptr] = AllocRec{nullptr, nullptr};
+  }
+  return ptr;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  AllocRec r{nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_blocks.find(p);
+    if (it == g_blocks.end()) return;
+    r = it->second;
+    g_blocks.erase(it);
+  }
+  if (r.free_fn)
+    r.free_fn(p, r.user);
+  else
+    cudaFree(p);
+}
+
+void yoshida_coefficients(double c[4]) {
+  const double t = cbrt(2.0);
+  const double w1 = 1.0 / (2.0 - t), w0 = -t / (2.0 - t);
+  c[0] = 0.5 * w1;         // B0
+  c[1] = 0.5 * (w0 + w1);  // B1
+  c[2] = w1;               // D0
+  c[3] = w0;               // D1
+}
+
+// ------------------------------------------------------------------ ABI ---
+
+extern "C" {
+
+const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int md_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail_global(MD_EINVAL, "md_set_allocator: give both alloc and free, or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return MD_OK;
+}
+
+void md_free(md_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dev_free(c->q);
+  dev_free(c->p);
+  dev_free(c->f);
+  dev_free(c->hmf_partials);
+  dev_free(c->hmf_m);
+  dev_free(c->hmf_ticket);
+  dev_free(c->mirror[0]);
+  dev_free(c->mirror[1]);
+  dev_free(c->sk_slots);
+  dev_free(c->sk_tickets);
+  dev_free(c->red);
+  if (c->host_scalars) cudaFreeHost(c->host_scalars);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
+  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D) {
+    fail_global(MD_EINVAL, "md_init: unknown model %d", model);
+    return nullptr;
+  }
+  if (N < 1 || N > (int64_t)1 << 40) {
+    fail_global(MD_EINVAL, "md_init: N must be in [1, 2^40], got %lld", (long long)N);
+    return nullptr;
+  }
+  if (!is_finite(eps) || eps < 0.0 || (model != MD_HMF && !(eps > 0.0))) {
+    fail_global(MD_EINVAL, "md_init: eps must be finite and %s, got %g", model == MD_HMF ? ">= 0" : "> 0", eps);
+    return nullptr;
+  }
+  if (!is_finite(dt)) {
+    fail_global(MD_EINVAL, "md_init: dt must be finite");
+    return nullptr;
+  }
+  md_ctx *c = new (std::nothrow) md_ctx();
+  if (!c) {
+    fail_global(MD_ENOMEM, "md_init: host allocation");
+    return nullptr;
+  }
+  c->model = model;
+  c->dim = model == MD_GRAV2D ? 2 : 1;
+  c->N = N;
+  c->eps = eps;
+  c->dt = dt;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cuda_err(c, e, "md_init: device setup");
+    cudaGetLastError();
+    md_free(c);
+    return nullptr;
+  }
+  c->own_stream = true;
+  const size_t nb = sizeof(double) * (size_t)(c->dim * N);
+  c->hmf_grid_max = c->nsm * (2048 / kStreamThreads);
+  c->q = (double *)dev_alloc(nb);
+  c->p = (double *)dev_alloc(nb);
+  c->f = (double *)dev_alloc(nb);
+  c->hmf_partials = (double *)dev_alloc(sizeof(double) * 2 * c->hmf_grid_max);
+  c->hmf_m = (double *)dev_alloc(sizeof(double) * 16);
+  c->hmf_ticket = (unsigned *)dev_alloc(sizeof(unsigned) * 4);
+  if (!c->q || !c->p || !c->f || !c->hmf_partials || !c->hmf_m || !c->hmf_ticket) {
+    set_err(c, MD_ENOMEM, "md_init: device allocation of %zu bytes failed", 3 * nb);
+    md_free(c);
+    return nullptr;
+  }
+  if (cudaMallocHost(&c->host_scalars, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->host_scalars = nullptr;
+    set_err(c, MD_ENOMEM, "md_init: pinned host scalars");
+    md_free(c);
+    return nullptr;
+  }
+  if (cudaMemsetAsync(c->hmf_ticket, 0, sizeof(unsigned) * 4, c->stream) != cudaSuccess) {
+    cuda_err(c, cudaGetLastError(), "md_init: memset");
+    md_free(c);
+    return nullptr;
+  }
+  const int kind = model == MD_HMF ? MD_IC_WATERBAG : model == MD_RING ? MD_IC_RING : MD_IC_DISK;
+  if (ic_draw(c, kind, nullptr, seed) != MD_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    g_err = c->err.empty() ? std::string("md_init: initial state") : c->err;
+    md_free(c);
+    return nullptr;
+  }
+  return c;
+}
+
+#define CHECK_CTX(c)                                              \
+  do {                                                            \
+    if (!(c)) return fail_global(MD_EINVAL, "NULL context");      \
+  } while (0)
+
+int md_set_precision(md_ctx *c, int prec) {
+  CHECK_CTX(c);
+  if (prec != MD_FP64 && prec != MD_MIXED) return set_err(c, MD_EINVAL, "unknown precision %d", prec);
+  c->prec = prec;
+  return MD_OK;
+}
+
+int md_set_stream(md_ctx *c, void *stream) {
+  CHECK_CTX(c);
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  c->stream = (cudaStream_t)stream;
+  c->own_stream = false;
+  return MD_OK;
+}
+
+int md_set_dt(md_ctx *c, double dt) {
+  CHECK_CTX(c);
+  if (!is_finite(dt)) return set_err(c, MD_EINVAL, "dt must be finite");
+  c->dt = dt;
+  return MD_OK;
+}
+
+int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
+  CHECK_CTX(c);
+  if (!key) return set_err(c, MD_EINVAL, "NULL key");
+  std::string k(key);
+  if (k == "r_mixed" && (value == 4 || value == 8)) c->pt.r_mixed = (int)value;
+  else if (k == "r_fp64" && (value == 2 || value == 4)) c->pt.r_fp64 = (int)value;
+  else if (k == "pair_ctas_per_sm" && value >= 0 && value <= 32) c->pt.ctas_per_sm = (int)value;
+  else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
+  else return set_err(c, MD_EINVAL, "unknown tuning key or value: %s=%lld", key, (long long)value);
+  return MD_OK;
+}
+
+int md_set_ic(md_ctx *c, int kind, const double *params, uint64_t seed) {
+  CHECK_CTX(c);
+  return ic_draw(c, kind, params, seed);
+}
+
+static int invalidate(md_ctx *c) {
+  c->fsal_valid = false;
+  c->hmf_m_valid = false;
+  c->mirror_valid = false;
+  return MD_OK;
+}
+
+int md_set_state(md_ctx *c, const double *q, const double *p) {
+  CHECK_CTX(c);
+  if (!q || !p) return set_err(c, MD_EINVAL, "md_set_state: NULL array");
+  const size_t nb = sizeof(double) * (size_t)(c->dim * c->N);
+  MD_CUDA(c, cudaMemcpyAsync(c->q, q, nb, cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(c, cudaMemcpyAsync(c->p, p, nb, cudaMemcpyHostToDevice, c->stream));
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  return invalidate(c);
+}
+
+int md_get_state(md_ctx *c, double *q, double *p) {
+  CHECK_CTX(c);
+  const size_t nb = sizeof(double) * (size_t)(c->dim * c->N);
+  if (q) MD_CUDA(c, cudaMemcpyAsync(q, c->q, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (p) MD_CUDA(c, cudaMemcpyAsync(p, c->p, nb, cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+int md_set_state_device(md_ctx *c, const double *q, const double *p) {
+  CHECK_CTX(c);
+  if (!q || !p) return set_err(c, MD_EINVAL, "md_set_state_device: NULL array");
+  const size_t nb = sizeof(double) * (size_t)(c->dim * c->N);
+  MD_CUDA(c, cudaMemcpyAsync(c->q, q, nb, cudaMemcpyDeviceToDevice, c->stream));
+  MD_CUDA(c, cudaMemcpyAsync(c->p, p, nb, cudaMemcpyDeviceToDevice, c->stream));
+  return invalidate(c);
+}
+
+int md_get_state_device(md_ctx *c, double *q, double *p) {
+  CHECK_CTX(c);
+  const size_t nb = sizeof(double) * (size_t)(c->dim * c->N);
+  if (q) MD_CUDA(c, cudaMemcpyAsync(q, c->q, nb, cudaMemcpyDeviceToDevice, c->stream));
+  if (p) MD_CUDA(c, cudaMemcpyAsync(p, c->p, nb, cudaMemcpyDeviceToDevice, c->stream));
+  return MD_OK;
+}
+
+int md_step(md_ctx *c, int64_t nsteps) {
+  CHECK_CTX(c);
+  if (nsteps < 0) return set_err(c, MD_EINVAL, "md_step: nsteps < 0");
+  if (nsteps == 0) return MD_OK;
+  double k[4];
+  yoshida_coefficients(k);
+  const double h = c->dt, B0 = k[0], B1 = k[1], D0 = k[2], D1 = k[3];
+  int rc;
+  if (c->model == MD_HMF) {
+    for (int64_t s = 0; s < nsteps; s++) {
+      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, (s == 0 ? B0 : 2.0 * B0) * h, D0 * h, nullptr))) return rc;
+      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D1 * h, nullptr))) return rc;
+      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
+    }
+    return hmf_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, nullptr);
+  }
+  const bool cached = c->fsal_valid && c->fsal_prec == c->prec && c->mirror_valid && c->mirror_prec == c->prec;
+  c->fsal_valid = false;
+  for (int64_t s = 0; s < nsteps; s++) {
+    if (s == 0 && cached)
+      rc = kick_drift_cached(c, B0 * h, D0 * h);
+    else
+      rc = pair_stage(c, STAGE_KICK_DRIFT, (s == 0 ? B0 : 2.0 * B0) * h, D0 * h, nullptr);
+    if (rc) return rc;
+    if ((rc = pair_stage(c, STAGE_KICK_DRIFT, B1 * h, D1 * h, nullptr))) return rc;
+    if ((rc = pair_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
+  }
+  if ((rc = pair_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, c->f))) return rc;
+  c->fsal_valid = true;
+  c->fsal_prec = c->prec;
+  return MD_OK;
+}
+
+void md_yoshida(double *c4) {
+  if (c4) yoshida_coefficients(c4);
+}
+
+int md_stage(md_ctx *c, double b, double d) {
+  CHECK_CTX(c);
+  if (!is_finite(b) || !is_finite(d)) return set_err(c, MD_EINVAL, "md_stage: non-finite coefficient");
+  const double h = c->dt;
+  if (c->model == MD_HMF)
+    return d == 0.0 ? hmf_stage(c, STAGE_KICK_ONLY, b * h, 0.0, nullptr)
+                    : hmf_stage(c, STAGE_KICK_DRIFT, b * h, d * h, nullptr);
+  if (d == 0.0) {
+    int rc = pair_stage(c, STAGE_KICK_ONLY, b * h, 0.0, c->f);
+    if (rc) return rc;
+    c->fsal_valid = true;
+    c->fsal_prec = c->prec;
+    return MD_OK;
+  }
+  c->fsal_valid = false;
+  return pair_stage(c, STAGE_KICK_DRIFT, b * h, d * h, nullptr);
+}
+
+int md_force_device(md_ctx *c, double *f) {
+  CHECK_CTX(c);
+  if (!f) return set_err(c, MD_EINVAL, "md_force_device: NULL output");
+  if (c->model == MD_HMF) return hmf_stage(c, STAGE_FORCE_ONLY, 0.0, 0.0, f);
+  return pair_stage(c, STAGE_FORCE_ONLY, 0.0, 0.0, f);
+}
+
+int md_force(md_ctx *c, double *f) {
+  CHECK_CTX(c);
+  if (!f) return set_err(c, MD_EINVAL, "md_force: NULL output");
+  int rc = md_force_device(c, c->f);
+  if (rc) return rc;
+  if (c->model != MD_HMF) {
+    c->fsal_valid = true;
+    c->fsal_prec = c->prec;
+  }
+  const size_t nb = sizeof(double) * (size_t)(c->dim * c->N);
+  MD_CUDA(c, cudaMemcpyAsync(f, c->f, nb, cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+int md_energy(md_ctx *c, double *K, double *V) {
+  CHECK_CTX(c);
+  int rc;
+  double *d = c->hmf_m + 8;  // device scalars [8..11]
+  if ((rc = kinetic_fp64(c, d))) return rc;
+  if (c->model == MD_HMF) {
+    if ((rc = hmf_sums_fp64(c, d + 2))) return rc;
+  } else {
+    if ((rc = pair_potential_fp64(c, d + 1))) return rc;
+  }
+  MD_CUDA(c, cudaMemcpyAsync(c->host_scalars, d, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double n = (double)c->N;
+  const double kin = c->host_scalars[0];
+  double pot;
+  if (c->model == MD_HMF) {
+    const double mx = c->host_scalars[2] / n, my = c->host_scalars[3] / n;
+    pot = 0.5 * n * (1.0 - mx * mx - my * my);  // Eq. 5
+  } else if (c->model == MD_RING) {
+    pot = -c->host_scalars[1] / (2.0 * n);  // Eq. 1 with 1 - cos + eps = 2 (sin^2(d/2) + eps/2)
+  } else {
+    pot = c->host_scalars[1] / n;  // Eq. 3
+  }
+  if (K) *K = kin;
+  if (V) *V = pot;
+  if (!is_finite(kin) || !is_finite(pot)) return set_err(c, MD_ENONFINITE, "md_energy: non-finite energy (K=%g, V=%g)", kin, pot);
+  return MD_OK;
+}
+
+int md_magnetization(md_ctx *c, double *mx, double *my) {
+  CHECK_CTX(c);
+  if (c->model == MD_GRAV2D) return set_err(c, MD_EINVAL, "md_magnetization: not defined for the 2D model");
+  double *d = c->hmf_m + 12;
+  int rc = hmf_sums_fp64(c, d);
+  if (rc) return rc;
+  MD_CUDA(c, cudaMemcpyAsync(c->host_scalars + 4, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double n = (double)c->N;
+  if (mx) *mx = c->host_scalars[4] / n;
+  if (my) *my = c->host_scalars[5] / n;
+  if (!is_finite(c->host_scalars[4]) || !is_finite(c->host_scalars[5]))
+    return set_err(c, MD_ENONFINITE, "md_magnetization: non-finite");
+  return MD_OK;
+}
+
+int md_synchronize(md_ctx *c) {
+  CHECK_CTX(c);
+  MD_CUDA(c, cudaStreamSynchronize(c->stream));
+  return MD_OK;
+}
+
+int64_t md_launch_count(const md_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

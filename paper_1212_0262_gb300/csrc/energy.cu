@@ -1,0 +1,164 @@
+// FP64 observables: kinetic energy and the pair potentials of Eqs. 1 and 3.
+//
+// All sums are deterministic: per-thread sums, a fixed shuffle/block tree, one
+// partial per CTA (or per tile pair), and a final pass that adds the partials in
+// index order (the last CTA to finish does it; no waiting).
+#include "md_internal.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int PT = 256;  // potential tile (particles per side)
+
+__device__ __forceinline__ void finish_sum(double v, double *partials, double *out, unsigned *ticket) {
+  __shared__ double2 red[NT / 32];
+  __shared__ bool last;
+  double2 b = block_sum2<NT>(v, 0.0, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = b.x;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += NT) s += __ldcg(partials + j);
+  __syncthreads();
+  double2 t = block_sum2<NT>(s, 0.0, red);
+  if (threadIdx.x == 0) {
+    *out = t.x;
+    *ticket = 0u;
+  }
+}
+
+// SQUARE: sum of x^2 / 2, else plain sum.
+template <bool SQUARE>
+__global__ void __launch_bounds__(NT) sum_kernel(const double *__restrict__ x, int64_t n, double *partials,
+                                                 double *out, unsigned *ticket) {
+  double s = 0.0;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += G) {
+    double v = x[i];
+    s += SQUARE ? v * v : v;
+  }
+  if (SQUARE) s *= 0.5;
+  finish_sum(s, partials, out, ticket);
+}
+
+// (sin, cos) of half the range-reduced angle, for the Ring potential.
+__global__ void half_angle_kernel(const double *__restrict__ q, int64_t N, double2 *__restrict__ ag) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
+    double a, g;
+    sincos(0.5 * reduce_2pi(q[i]), &a, &g);
+    ag[i] = make_double2(a, g);
+  }
+}
+
+// One tile pair (ti <= tj) of the i<j potential sum.
+//  Ring: -(1/(2N)) sum d^(-1/2), d = sin^2((ti-tj)/2) + eps/2  (Eq. 1, with
+//        1 - cos d + eps = 2 d)
+//  2D:   (1/N) sum log(|r_ij|^2 + eps)                        (Eq. 3)
+// The prefactor is applied on the host.
+template <int MODEL>
+__global__ void __launch_bounds__(NT) potential_tiles_kernel(const double *__restrict__ q,
+                                                              const double2 *__restrict__ ag, int64_t N,
+                                                              int ntiles, double epsd, double *unit_sums) {
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (tj < ti) return;
+  __shared__ double2 sj[PT];
+  const int64_t j0 = (int64_t)tj * PT;
+  for (int t = threadIdx.x; t < PT; t += NT) {
+    int64_t j = j0 + t;
+    if (j < N) sj[t] = MODEL == MD_RING ? ag[j] : make_double2(q[j], q[N + j]);
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)ti * PT + threadIdx.x;
+  double s = 0.0;
+  if (i < N) {
+    const double2 me = MODEL == MD_RING ? ag[i] : make_double2(q[i], q[N + i]);
+    int kbeg = 0;
+    if (ti == tj) kbeg = threadIdx.x + 1;  // j > i inside the diagonal tile
+    int kend = (int)((N - j0) < PT ? (N - j0) : PT);
+    for (int k = kbeg; k < kend; k++) {
+      const double2 o = sj[k];
+      if (MODEL == MD_RING) {
+        double sh = fma(me.x, o.y, -(me.y * o.x));
+        s += rsqrt_nr(fma(sh, sh, epsd));
+      } else {
+        double dx = me.x - o.x, dy = me.y - o.y;
+        s += log(fma(dx, dx, fma(dy, dy, epsd)));
+      }
+    }
+  }
+  __shared__ double2 red[NT / 32];
+  double2 b = block_sum2<NT>(s, 0.0, red);
+  if (threadIdx.x == 0) unit_sums[(int64_t)ti * ntiles + tj] = b.x;
+}
+
+int grid_sum(md_ctx *c, int64_t n) {
+  int64_t g = (n + NT - 1) / NT;
+  int64_t cap = (int64_t)c->nsm * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int reduce_scratch(md_ctx *c, size_t bytes) {
+  if (bytes <= c->red_bytes) return MD_OK;
+  dev_free(c->red);
+  c->red = (double *)dev_alloc(bytes);
+  if (!c->red) {
+    c->red_bytes = 0;
+    return set_err(c, MD_ENOMEM, "reduction scratch: %zu bytes", bytes);
+  }
+  c->red_bytes = bytes;
+  return MD_OK;
+}
+
+// Kinetic energy (1/2) sum p^2 into device *d_out.  The CTA partials use the
+// HMF partial buffer and ticket (sized for the largest streaming grid).
+int kinetic_fp64(md_ctx *c, double *d_out) {
+  const int64_t n = (int64_t)c->dim * c->N;
+  int g = grid_sum(c, n);
+  if (g > c->hmf_grid_max) g = c->hmf_grid_max;
+  sum_kernel<true><<<g, NT, 0, c->stream>>>(c->p, n, c->hmf_partials, d_out, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
+// Pair-sum part of the potential of Eq. 1 (Ring) or Eq. 3 (2D), prefactor
+// applied, into device *d_out.  Uses ctx->red as scratch.
+int pair_potential_fp64(md_ctx *c, double *d_out) {
+  const int64_t N = c->N;
+  const int ntiles = (int)((N + PT - 1) / PT);
+  if (ntiles > 65535) return set_err(c, MD_EINVAL, "potential: N too large for the tile grid");
+  size_t units = (size_t)ntiles * ntiles;
+  const size_t units_al = (units + 1) & ~(size_t)1;  // keeps the double2 array 16-byte aligned
+  size_t need = units_al * sizeof(double) + (c->model == MD_RING ? (size_t)N * sizeof(double2) : 0) + 64;
+  int rc = reduce_scratch(c, need);
+  if (rc) return rc;
+  double *unit_sums = c->red;
+  double2 *ag = (double2 *)(c->red + units_al);
+  MD_CUDA(c, cudaMemsetAsync(unit_sums, 0, units * sizeof(double), c->stream));
+  if (c->model == MD_RING) {
+    int64_t b = (N + 255) / 256;
+    if (b > (int64_t)c->nsm * 16) b = (int64_t)c->nsm * 16;
+    half_angle_kernel<<<(int)b, 256, 0, c->stream>>>(c->q, N, ag);
+    MD_LAUNCHED(c);
+    potential_tiles_kernel<MD_RING><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, ag, N, ntiles, 0.5 * c->eps,
+                                                                                unit_sums);
+  } else {
+    potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, nullptr, N, ntiles, c->eps,
+                                                                                  unit_sums);
+  }
+  MD_LAUNCHED(c);
+  int g = grid_sum(c, (int64_t)units);
+  if (g > c->hmf_grid_max) g = c->hmf_grid_max;
+  sum_kernel<false><<<g, NT, 0, c->stream>>>(unit_sums, (int64_t)units, c->hmf_partials, d_out, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}

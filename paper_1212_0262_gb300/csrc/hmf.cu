@@ -1,0 +1,263 @@
+// HMF model (Sec. 3.1): one fused, memory-bound pass per integrator stage.
+//
+// The force of Eq. 6 needs the magnetization of Eq. 7 of the *current* angles.
+// Each stage kernel reads the sums (sum cos, sum sin) that the previous stage
+// left behind, and per particle
+//     f = cos(theta) My - sin(theta) Mx                  (Eq. 6)
+//     p += kick * f ;  theta += drift * p                (Sec. 3 step list)
+//     accumulate cos(theta_new), sin(theta_new)          (Eq. 7 for the next stage)
+// so the state is read once and written once per stage (32 B per particle).
+// The paper instead stores sin and cos in global memory and reloads them; here
+// they are recomputed, which is cheaper than the extra 16 B of traffic.
+//
+// Reduction: per-thread sums, warp shuffles and a block tree give one FP64
+// partial per CTA; the last CTA to finish (atomic ticket, no waiting) adds the
+// partials in CTA order, so the result is deterministic.
+#include "md_internal.cuh"
+
+namespace {
+
+constexpr int NT = kStreamThreads;
+constexpr int UNROLL = 2;  // double2 loads of theta and of p in flight per thread
+
+struct HmfArgs {
+  double *q, *p;
+  int64_t N;
+  double invN;
+  const double *m_in;  // (sum cos, sum sin) of the current angles
+  double kick, drift;
+  double *partials;  // 2 per CTA
+  double *m_out;     // (sum cos, sum sin) of the new angles
+  unsigned *ticket;
+  double *fout;  // STAGE_FORCE_ONLY output
+};
+
+// One particle of a stage.  MIXED: FP64 state update, FP32 sine/cosine of the
+// FP64-range-reduced angle; the new angle's reduced value is carried in FP32.
+template <bool MIXED, int MODE>
+__device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfArgs &a, float mxf,
+                                             float myf, double mx, double my, float dtf, float &acf,
+                                             float &asf, double &acd, double &asd, int64_t i) {
+  if (MIXED) {
+    float r = (float)reduce_2pi(th);
+    float s, c;
+    sincos_small(r, &s, &c);
+    float f = c * myf - s * mxf;
+    if (MODE == STAGE_FORCE_ONLY) {
+      a.fout[i] = (double)f;
+      return;
+    }
+    pp = fma(a.kick, (double)f, pp);
+    if (MODE == STAGE_KICK_DRIFT) {
+      th = fma(a.drift, pp, th);
+      float r2 = fmaf(dtf, (float)pp, r);
+      sincos_small(r2, &s, &c);
+      acf += c;
+      asf += s;
+    }
+  } else {
+    double s, c;
+    sincos(th, &s, &c);
+    double f = c * my - s * mx;
+    if (MODE == STAGE_FORCE_ONLY) {
+      a.fout[i] = f;
+      return;
+    }
+    pp = fma(a.kick, f, pp);
+    if (MODE == STAGE_KICK_DRIFT) {
+      th = fma(a.drift, pp, th);
+      sincos(th, &s, &c);
+      acd += c;
+      asd += s;
+    }
+  }
+}
+
+// Grid finish: write this CTA's partial; the last CTA sums all partials in order.
+__device__ __forceinline__ void grid_finish(double sc, double ss, double *partials, double *m_out,
+                                            unsigned *ticket) {
+  __shared__ double2 red[NT / 32];
+  __shared__ bool last;
+  double2 b = block_sum2<NT>(sc, ss, red);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b.x;
+    partials[2 * blockIdx.x + 1] = b.y;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double c0 = 0.0, c1 = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += NT) {
+    c0 += __ldcg(partials + 2 * j);
+    c1 += __ldcg(partials + 2 * j + 1);
+  }
+  __syncthreads();
+  double2 t = block_sum2<NT>(c0, c1, red);
+  if (threadIdx.x == 0) {
+    m_out[0] = t.x;
+    m_out[1] = t.y;
+    *ticket = 0u;
+  }
+}
+
+template <bool MIXED, int MODE>
+__global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
+  const double mx = a.m_in[0] * a.invN, my = a.m_in[1] * a.invN;
+  const float mxf = (float)mx, myf = (float)my, dtf = (float)a.drift;
+  float acf = 0.f, asf = 0.f;
+  double acd = 0.0, asd = 0.0;
+  const int64_t npairs = a.N >> 1;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  const int64_t t0 = (int64_t)blockIdx.x * NT + threadIdx.x;
+  double2 *q2 = reinterpret_cast<double2 *>(a.q);
+  double2 *p2 = reinterpret_cast<double2 *>(a.p);
+  for (int64_t k = t0; k < npairs; k += UNROLL * G) {
+    double2 qv[UNROLL], pv[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      int64_t kk = k + u * G;
+      if (kk < npairs) {
+        qv[u] = q2[kk];
+        pv[u] = p2[kk];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      int64_t kk = k + u * G;
+      if (kk < npairs) {
+        hmf_particle<MIXED, MODE>(qv[u].x, pv[u].x, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, 2 * kk);
+        hmf_particle<MIXED, MODE>(qv[u].y, pv[u].y, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, 2 * kk + 1);
+        if (MODE == STAGE_KICK_DRIFT) q2[kk] = qv[u];
+        if (MODE != STAGE_FORCE_ONLY) p2[kk] = pv[u];
+      }
+    }
+  }
+  if ((a.N & 1) && t0 == 0) {
+    int64_t i = a.N - 1;
+    double th = a.q[i], pp = a.p[i];
+    hmf_particle<MIXED, MODE>(th, pp, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, i);
+    if (MODE == STAGE_KICK_DRIFT) a.q[i] = th;
+    if (MODE != STAGE_FORCE_ONLY) a.p[i] = pp;
+  }
+  if (MODE == STAGE_KICK_DRIFT) {
+    if (MIXED) {
+      acd = (double)acf;
+      asd = (double)asf;
+    }
+    grid_finish(acd, asd, a.partials, a.m_out, a.ticket);
+  }
+}
+
+// (sum cos, sum sin) of the given angles.  MIXED: FP32 sine/cosine after FP64
+// range reduction, FP32 per-thread sums; otherwise FP64 throughout.
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__ q, int64_t N,
+                                                      double *partials, double *m_out, unsigned *ticket) {
+  float acf = 0.f, asf = 0.f;
+  double acd = 0.0, asd = 0.0;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < N; i += G) {
+    double th = q[i];
+    if (MIXED) {
+      float s, c;
+      sincos_small((float)reduce_2pi(th), &s, &c);
+      acf += c;
+      asf += s;
+    } else {
+      double s, c;
+      sincos(th, &s, &c);
+      acd += c;
+      asd += s;
+    }
+  }
+  if (MIXED) {
+    acd = (double)acf;
+    asd = (double)asf;
+  }
+  grid_finish(acd, asd, partials, m_out, ticket);
+}
+
+int grid_for(md_ctx *c, const void *kern, int64_t work_items) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+  if (c->ht.ctas_per_sm > 0 && c->ht.ctas_per_sm < occ) occ = c->ht.ctas_per_sm;
+  int64_t g = (int64_t)c->nsm * (occ > 0 ? occ : 1);
+  int64_t need = (work_items + NT - 1) / NT;
+  if (need < 1) need = 1;
+  if (g > need) g = need;
+  if (g > c->hmf_grid_max) g = c->hmf_grid_max;
+  return (int)g;
+}
+
+template <bool MIXED, int MODE>
+int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
+  HmfArgs a;
+  a.q = c->q;
+  a.p = c->p;
+  a.N = c->N;
+  a.invN = 1.0 / (double)c->N;
+  a.m_in = c->hmf_m + 2 * c->hmf_cur;
+  a.kick = kick;
+  a.drift = drift;
+  a.partials = c->hmf_partials;
+  a.m_out = c->hmf_m + 2 * (1 - c->hmf_cur);
+  a.ticket = c->hmf_ticket;
+  a.fout = fout;
+  auto kern = hmf_stage_kernel<MIXED, MODE>;
+  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1);
+  kern<<<g, NT, 0, c->stream>>>(a);
+  MD_LAUNCHED(c);
+  if (MODE == STAGE_KICK_DRIFT) c->hmf_cur = 1 - c->hmf_cur;
+  return MD_OK;
+}
+
+}  // namespace
+
+int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2) {
+  auto kern = hmf_sums_kernel<false>;
+  int g = grid_for(c, (const void *)kern, c->N);
+  kern<<<g, NT, 0, c->stream>>>(q, c->N, c->hmf_partials, d_out2, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
+int hmf_sums_fp64(md_ctx *c, double *d_out2) { return hmf_sums_fp64_of(c, c->q, d_out2); }
+
+// Sums of the current angles into the current magnetization slot.
+int hmf_prime(md_ctx *c) {
+  double *out = c->hmf_m + 2 * c->hmf_cur;
+  if (c->prec == MD_MIXED) {
+    auto kern = hmf_sums_kernel<true>;
+    int g = grid_for(c, (const void *)kern, c->N);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket);
+    MD_LAUNCHED(c);
+  } else {
+    int rc = hmf_sums_fp64_of(c, c->q, out);
+    if (rc) return rc;
+  }
+  c->hmf_m_valid = true;
+  c->hmf_m_prec = c->prec;
+  return MD_OK;
+}
+
+int hmf_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
+  if (!c->hmf_m_valid || c->hmf_m_prec != c->prec) {
+    int rc = hmf_prime(c);
+    if (rc) return rc;
+  }
+  const bool mixed = c->prec == MD_MIXED;
+  switch (mode) {
+  case STAGE_KICK_DRIFT:
+    return mixed ? launch_stage<true, STAGE_KICK_DRIFT>(c, kick, drift, fout)
+                 : launch_stage<false, STAGE_KICK_DRIFT>(c, kick, drift, fout);
+  case STAGE_KICK_ONLY:
+    return mixed ? launch_stage<true, STAGE_KICK_ONLY>(c, kick, drift, fout)
+                 : launch_stage<false, STAGE_KICK_ONLY>(c, kick, drift, fout);
+  default:
+    return mixed ? launch_stage<true, STAGE_FORCE_ONLY>(c, kick, drift, fout)
+                 : launch_stage<false, STAGE_FORCE_ONLY>(c, kick, drift, fout);
+  }
+}

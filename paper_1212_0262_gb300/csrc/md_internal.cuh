@@ -1,0 +1,221 @@
+// Internal declarations shared by the libmd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "md.h"
+
+// ------------------------------------------------------------------ tuning --
+
+// Threads per CTA of the streaming (HMF, elementwise) kernels.
+constexpr int kStreamThreads = 256;
+// Threads per CTA of the all-pairs kernels.
+constexpr int kPairThreads = 128;
+
+struct PairTuning {
+  int r_mixed = 8;    // i-particles per thread, FP32 pair path
+  int r_fp64 = 2;     // i-particles per thread, FP64 pair path
+  int tj = 256;       // j-tile (particles staged in shared memory per unit)
+  int ctas_per_sm = 0;  // 0: occupancy-derived
+};
+
+struct HmfTuning {
+  int ctas_per_sm = 0;  // 0: occupancy-derived
+};
+
+// ----------------------------------------------------------------- context --
+
+struct md_ctx {
+  int model = 0, dim = 1, prec = MD_FP64;
+  int64_t N = 0;
+  double eps = 0.0, dt = 0.0;
+  int device = 0, nsm = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  double *q = nullptr, *p = nullptr;  // dim*N each (FP64 state)
+  double *f = nullptr;                // dim*N: first-same-as-last force cache / scratch force
+  bool fsal_valid = false;            // f holds the force at the current q
+  int fsal_prec = -1;
+
+  // HMF: per-CTA partial sums, magnetization double buffer, finish ticket
+  double *hmf_partials = nullptr;  // 2 * hmf_grid_max
+  double *hmf_m = nullptr;         // [2][2]: (sum cos, sum sin) of the current / next angles
+  unsigned *hmf_ticket = nullptr;
+  int hmf_grid_max = 0;
+  int hmf_cur = 0;
+  bool hmf_m_valid = false;
+  int hmf_m_prec = -1;
+
+  // Ring / 2D: position mirrors (ping-pong), stream-K partial slots and tickets
+  void *mirror[2] = {nullptr, nullptr};
+  size_t mirror_bytes = 0;
+  int mirror_cur = 0;
+  bool mirror_valid = false;
+  int mirror_prec = -1;
+  double *sk_slots = nullptr;
+  size_t sk_slots_bytes = 0;
+  unsigned *sk_tickets = nullptr;
+  size_t sk_tickets_count = 0;
+
+  // reductions (energies)
+  double *red = nullptr;
+  size_t red_bytes = 0;
+  double *host_scalars = nullptr;  // pinned, 16 doubles
+
+  PairTuning pt;
+  HmfTuning ht;
+  int64_t launches = 0;
+  std::string err;
+};
+
+// ------------------------------------------------------------ host helpers --
+
+int set_err(md_ctx *c, int code, const char *fmt, ...);
+int cuda_err(md_ctx *c, cudaError_t e, const char *what);
+void *dev_alloc(size_t bytes);
+void dev_free(void *p);
+#define MD_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_err((ctx), e_, #call);     \
+  } while (0)
+#define MD_LAUNCHED(ctx)                                                      \
+  do {                                                                        \
+    (ctx)->launches++;                                                        \
+    cudaError_t e_ = cudaGetLastError();                                      \
+    if (e_ != cudaSuccess) return cuda_err((ctx), e_, "kernel launch");       \
+  } while (0)
+
+// Yoshida coefficients of Eq. 4 (B0, B1, D0, D1), from the triple-jump closed form.
+void yoshida_coefficients(double c[4]);
+
+// ---------------------------------------------------------- kernel drivers --
+
+// Stage modes of the fused force kernels.
+enum StageMode {
+  STAGE_KICK_DRIFT = 0,  // f(q); p += kick f; q += drift p; refresh mirror / reduction
+  STAGE_KICK_ONLY = 1,   // f(q); p += kick f; store f in ctx->f (first-same-as-last cache)
+  STAGE_FORCE_ONLY = 2,  // f(q) into an output array
+};
+
+// hmf.cu
+int hmf_prime(md_ctx *c);                                         // sums of the current angles
+int hmf_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
+int hmf_sums_fp64(md_ctx *c, double *d_out2);                     // FP64 (sum cos, sum sin) into device out
+int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2);
+
+// pairs.cu
+int mirror_refresh(md_ctx *c);                                    // mirror[mirror_cur] from q
+int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
+int kick_drift_cached(md_ctx *c, double kick, double drift);      // first stage from the cached force
+
+// energy.cu
+int kinetic_fp64(md_ctx *c, double *d_out);                       // (1/2) sum p^2 into device out
+int pair_potential_fp64(md_ctx *c, double *d_out);                // i<j sum of Eq. 1 / Eq. 3
+int reduce_scratch(md_ctx *c, size_t bytes);
+
+// ic.cu
+int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed);
+
+// -------------------------------------------------------- device helpers ----
+#ifdef __CUDACC__
+
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// 1/sqrt(d) in FP64: FP32 hardware seed refined by two Newton-Raphson steps for
+// y^-2 = d (y <- y + y (1 - d y^2) / 2); each step squares the relative error.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  double y = (double)mufu_rsqrt((float)d);
+  double e = fma(-(d * y), y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-(d * y), y, 1.0);
+  y = fma(0.5 * y, e, y);
+  return y;
+}
+
+// 1/s in FP64: FP32 hardware seed refined by two Newton-Raphson steps for
+// 1/y = s (y <- y + y (1 - s y)).
+__device__ __forceinline__ double rcp_nr(double s) {
+  double y = (double)mufu_rcp((float)s);
+  double e = fma(-s, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-s, y, 1.0);
+  y = fma(y, e, y);
+  return y;
+}
+
+// sin and cos of a float of modest size (|x| < 2^20), for arguments that were
+// already range-reduced in FP64.  x = k pi/2 + y with k the nearest integer
+// (found with the 1.5*2^23 rounding constant, which also leaves k mod 4 in the
+// low mantissa bits) and pi/2 split into two floats (each FMA keeps k*C exact
+// before its single rounding); then the Taylor series of sin and cos on
+// |y| <= pi/4, whose truncation errors there are 1.8e-9 and 1.2e-10.
+__device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
+  const float t = fmaf(x, 0.636619772f, 12582912.0f);
+  const int q = __float_as_int(t) & 3;
+  const float k = t - 12582912.0f;
+  float y = fmaf(-k, 1.5707963705062866f, x);
+  y = fmaf(-k, -4.371138828673793e-08f, y);
+  const float z = y * y;
+  float ps = fmaf(z, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(z, ps, 1.0f / 120.0f);
+  ps = fmaf(z, ps, -1.0f / 6.0f);
+  const float sy = fmaf(y * z, ps, y);
+  float pc = fmaf(z, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(z, pc, -1.0f / 720.0f);
+  pc = fmaf(z, pc, 1.0f / 24.0f);
+  pc = fmaf(z, pc, -0.5f);
+  const float cy = fmaf(z, pc, 1.0f);
+  const float a = (q & 1) ? cy : sy;
+  const float b = (q & 1) ? sy : cy;
+  *s = (q & 2) ? -a : a;
+  *c = ((q + 1) & 2) ? -b : b;
+}
+
+// theta - 2 pi k with k = rint(theta / 2 pi), in FP64 (two-constant Cody-Waite).
+__device__ __forceinline__ double reduce_2pi(double th) {
+  const double inv2pi = 0.15915494309189535;
+  const double hi = 6.283185307179586;       // 2 pi rounded to double
+  const double lo = 2.4492935982947064e-16;  // 2 pi - hi
+  double k = rint(th * inv2pi);
+  double r = fma(-k, hi, th);
+  return fma(-k, lo, r);
+}
+
+// Deterministic block sum of two doubles (fixed shuffle tree, then warps in order).
+template <int NT>
+__device__ __forceinline__ double2 block_sum2(double a, double b, double2 *smem) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) smem[w] = make_double2(a, b);
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NT / 32; i++) {
+      r.x += smem[i].x;
+      r.y += smem[i].y;
+    }
+  }
+  return r;  // valid in thread 0
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,229 @@
+"""Python objects over the C ABI: one simulated system, one ensemble.
+
+Only argument marshalling lives here; each method is one libmd call.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import binding as B
+
+MODELS = {"hmf": 0, "ring": 1, "grav2d": 2, "2d": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+def _model(m) -> int:
+    return MODELS[m.lower()] if isinstance(m, str) else int(m)
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p.lower()] if isinstance(p, str) else int(p)
+
+
+def yoshida() -> np.ndarray:
+    """(B0, B1, D0, D1) of Eq. 4 as used by md_step."""
+    c = np.zeros(4)
+    B.load().md_yoshida(c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return c
+
+
+def stage_schedule(nsteps: int):
+    """The (b, d) stage coefficients that md_step(nsteps) runs, in order."""
+    B0, B1, D0, D1 = yoshida()
+    out = []
+    for s in range(nsteps):
+        out += [((B0 if s == 0 else 2 * B0), D0), (B1, D1), (B1, D0)]
+    if nsteps:
+        out.append((B0, 0.0))
+    return out
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class System:
+    """N particles of one model (md_init .. md_free)."""
+
+    def __init__(self, model, N: int, eps: float = 0.0, dt: float = 0.1, seed: int = 0,
+                 precision="fp64"):
+        lib = B.load()
+        self.model = _model(model)
+        self.N = int(N)
+        self.dim = 2 if self.model == 2 else 1
+        h = lib.md_init(self.model, self.N, float(eps), float(dt), int(seed) & (2**64 - 1))
+        if not h:
+            raise B.MDError(B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
+        self._h = ctypes.c_void_p(h)
+        self.set_precision(precision)
+
+    # -- lifecycle
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            B.load().md_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, rc: int) -> None:
+        B.check(rc, self._h)
+
+    # -- configuration
+    def set_precision(self, precision) -> None:
+        self._chk(B.load().md_set_precision(self._h, _prec(precision)))
+
+    def set_dt(self, dt: float) -> None:
+        self._chk(B.load().md_set_dt(self._h, float(dt)))
+
+    def set_tuning(self, key: str, value: int) -> None:
+        self._chk(B.load().md_set_tuning(self._h, key.encode(), int(value)))
+
+    def set_stream(self, stream) -> None:
+        """A cudaStream_t as int, or a torch.cuda.Stream."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._chk(B.load().md_set_stream(self._h, ctypes.c_void_p(int(handle or 0))))
+
+    def set_ic(self, kind: int, params=None, seed: int = 0) -> None:
+        arr = None if params is None else _f64(params)
+        p = None if arr is None else arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._chk(B.load().md_set_ic(self._h, int(kind), p, int(seed) & (2**64 - 1)))
+
+    # -- state
+    def set_state(self, q, p) -> None:
+        q, p = _f64(q), _f64(p)
+        n = self.dim * self.N
+        if q.size != n or p.size != n:
+            raise ValueError(f"state arrays must have {n} elements")
+        self._chk(B.load().md_set_state(self._h, _ptr(q), _ptr(p)))
+
+    def get_state(self):
+        n = self.dim * self.N
+        q, p = np.empty(n), np.empty(n)
+        self._chk(B.load().md_get_state(self._h, _ptr(q), _ptr(p)))
+        return q, p
+
+    def set_state_device(self, q_ptr: int, p_ptr: int) -> None:
+        self._chk(B.load().md_set_state_device(self._h, ctypes.c_void_p(q_ptr), ctypes.c_void_p(p_ptr)))
+
+    def get_state_device(self, q_ptr: int, p_ptr: int) -> None:
+        self._chk(B.load().md_get_state_device(self._h, ctypes.c_void_p(q_ptr), ctypes.c_void_p(p_ptr)))
+
+    # -- dynamics and observables
+    def step(self, nsteps: int = 1) -> None:
+        self._chk(B.load().md_step(self._h, int(nsteps)))
+
+    def stage(self, b: float, d: float) -> None:
+        """One fused force + kick(b dt) + drift(d dt) stage (d == 0: kick only)."""
+        self._chk(B.load().md_stage(self._h, float(b), float(d)))
+
+    def synchronize(self) -> None:
+        self._chk(B.load().md_synchronize(self._h))
+
+    def force(self) -> np.ndarray:
+        f = np.empty(self.dim * self.N)
+        self._chk(B.load().md_force(self._h, _ptr(f)))
+        return f
+
+    def force_device(self, f_ptr: int) -> None:
+        self._chk(B.load().md_force_device(self._h, ctypes.c_void_p(f_ptr)))
+
+    def energy(self):
+        k, v = ctypes.c_double(), ctypes.c_double()
+        self._chk(B.load().md_energy(self._h, ctypes.byref(k), ctypes.byref(v)))
+        return k.value, v.value
+
+    def magnetization(self):
+        mx, my = ctypes.c_double(), ctypes.c_double()
+        self._chk(B.load().md_magnetization(self._h, ctypes.byref(mx), ctypes.byref(my)))
+        return mx.value, my.value
+
+    def grad(self, nsteps: int, observable: int = 0, checkpoint_every: int = 20):
+        """(value, grad_q, grad_p, grad_eps) of the observable after nsteps."""
+        n = self.dim * self.N
+        gq, gp = np.empty(n), np.empty(n)
+        ge, val = ctypes.c_double(), ctypes.c_double()
+        self._chk(B.load().md_grad(self._h, int(observable), int(nsteps), int(checkpoint_every),
+                                   _ptr(gq), _ptr(gp), ctypes.byref(ge), ctypes.byref(val)))
+        return val.value, gq, gp, ge.value
+
+    @property
+    def launch_count(self) -> int:
+        return int(B.load().md_launch_count(self._h))
+
+
+class Ensemble:
+    """Independent Ring / 2D systems advanced together (md_batch_*)."""
+
+    def __init__(self, models, Ns, eps, dts, seeds, precision="mixed"):
+        lib = B.load()
+        self.nsys = len(Ns)
+        self.models = np.ascontiguousarray([_model(m) for m in models], dtype=np.int32)
+        self.Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+        self._eps = _f64(eps)
+        self._dts = _f64(dts)
+        self._seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        h = lib.md_batch_init(self.nsys, _ptr(self.models), _ptr(self.Ns), _ptr(self._eps), _ptr(self._dts),
+                              _ptr(self._seeds))
+        if not h:
+            raise B.MDError(B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
+        self._h = ctypes.c_void_p(h)
+        self.set_precision(precision)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            B.load().md_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc: int) -> None:
+        B.check(rc, self._h, batch=True)
+
+    def set_precision(self, precision) -> None:
+        self._chk(B.load().md_batch_set_precision(self._h, _prec(precision)))
+
+    def set_stream(self, stream) -> None:
+        handle = getattr(stream, "cuda_stream", stream)
+        self._chk(B.load().md_batch_set_stream(self._h, ctypes.c_void_p(int(handle or 0))))
+
+    def step(self, nsteps: int = 1) -> None:
+        self._chk(B.load().md_batch_step(self._h, int(nsteps)))
+
+    def energy(self):
+        k, v = np.empty(self.nsys), np.empty(self.nsys)
+        self._chk(B.load().md_batch_energy(self._h, _ptr(k), _ptr(v)))
+        return k, v
+
+    def get_state(self, s: int):
+        n = (2 if self.models[s] == 2 else 1) * int(self.Ns[s])
+        q, p = np.empty(n), np.empty(n)
+        self._chk(B.load().md_batch_get_state(self._h, int(s), _ptr(q), _ptr(p)))
+        return q, p
+
+    def set_state(self, s: int, q, p) -> None:
+        q, p = _f64(q), _f64(p)
+        self._chk(B.load().md_batch_set_state(self._h, int(s), _ptr(q), _ptr(p)))
+
+    @property
+    def launch_count(self) -> int:
+        return int(B.load().md_batch_launch_count(self._h))

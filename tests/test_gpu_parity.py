@@ -1,0 +1,179 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances:
+  FP64 forces   |f_gpu - f_ora| <= 1e-12 * sum_j |f_ij|   (per particle and
+                component; the summation-order bound, since plain relative error is
+                ill-conditioned where the pair forces cancel)
+  FP64 one step |dq| <= 1e-12 max(1, |q|_inf), |dp| <= 1e-12 (|p|_inf + dt |sum_j |f_ij||_inf)
+  mixed forces  |f_mix - f_ora| <= 2e-5 * sum_j |f_ij|  (FP32 pair arithmetic and
+                FP32 positions; the FP64 state is exact)
+  energies      1e-12 relative (FP64 reductions)
+"""
+import numpy as np
+import pytest
+
+import oracle as ora
+from paper_1212_0262_gb300 import System, inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = {0: 0.0, 1: 0.01, 2: 1e-3}
+SIZES = [1, 2, 3, 31, 32, 33, 1000, 1024, 4097]
+
+
+def _sys(model, N, prec="fp64", dt=0.05, seed=7):
+    s = System(model, N, EPS[model], dt, seed, precision=prec)
+    q, p = inputs.default_state(model, N, 1000 + N)
+    s.set_state(q, p)
+    return s, q, p
+
+
+def _force_err(model, q, f_gpu):
+    f_ora = ora.force(model, q, EPS[model])
+    scale = ora.force_abs(model, q, EPS[model])
+    err = np.abs(f_gpu - f_ora)
+    return err, scale, f_ora
+
+
+# ------------------------------------------------------------------ IC ----
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_device_initial_state_matches_input_generator(model):
+    N = 5000
+    with System(model, N, EPS[model] or 0.0, 0.1, 1234) as s:
+        q, p = s.get_state()
+    qe, pe = inputs.default_state(model, N, 1234)
+    if model == 0:
+        assert np.array_equal(q, qe) and np.array_equal(p, pe)
+    elif model == 1:
+        assert np.array_equal(q, qe)
+        np.testing.assert_allclose(p, pe, rtol=1e-14, atol=1e-15)
+    else:
+        np.testing.assert_allclose(q, qe, rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(p, pe, rtol=1e-14, atol=1e-15)
+
+
+# --------------------------------------------------------------- forces ---
+
+@pytest.mark.parametrize("N", SIZES)
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_force_parity(model, N):
+    s, q, p = _sys(model, N)
+    f = s.force()
+    err, scale, f_ora = _force_err(model, q, f)
+    assert np.all(err <= 1e-12 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+    if N == 1:
+        assert np.all(f == 0.0)
+
+
+@pytest.mark.parametrize("N", SIZES)
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_mixed_force_error_bound(model, N):
+    s, q, p = _sys(model, N, "mixed")
+    f = s.force()
+    err, scale, _ = _force_err(model, q, f)
+    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+
+
+# ---------------------------------------------------------- integration ---
+
+@pytest.mark.parametrize("N", [1, 2, 33, 1000, 4097])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_one_step_parity(model, N):
+    dt = 0.05
+    s, q0, p0 = _sys(model, N, dt=dt)
+    s.step(1)
+    q, p = s.get_state()
+    qo, po = ora.step(model, q0, p0, EPS[model], dt, 1)
+    fs = ora.force_abs(model, q0, EPS[model]).max()
+    assert np.max(np.abs(q - qo)) <= 1e-12 * max(1.0, np.abs(qo).max())
+    assert np.max(np.abs(p - po)) <= 1e-12 * (np.abs(po).max() + dt * fs)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_fp64_ten_steps_parity_small(model):
+    dt = 0.02
+    s, q0, p0 = _sys(model, 33, dt=dt)
+    s.step(4)
+    s.step(6)  # two calls: exercises the first-same-as-last force cache
+    q, p = s.get_state()
+    qo, po = ora.step(model, q0, p0, EPS[model], dt, 10)
+    assert np.max(np.abs(q - qo)) <= 1e-11 * max(1.0, np.abs(qo).max())
+    assert np.max(np.abs(p - po)) <= 1e-11 * max(1.0, np.abs(po).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_runs_are_bitwise_deterministic(model, prec):
+    out = []
+    for _ in range(2):
+        s, _, _ = _sys(model, 3000, prec)
+        s.step(3)
+        out.append(s.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_total_momentum_conserved(model, prec):
+    N = 4097
+    s, q0, p0 = _sys(model, N, prec)
+    s.step(20)
+    q, p = s.get_state()
+    d = 2 if model == 2 else 1
+    for c in range(d):
+        drift = abs(p[c * N:(c + 1) * N].sum() - p0[c * N:(c + 1) * N].sum())
+        assert drift < (1e-12 if prec == "fp64" else 1e-6) * np.abs(p0).sum(), drift
+
+
+# ---------------------------------------------------------- observables ---
+
+@pytest.mark.parametrize("N", [1, 2, 33, 1000, 4097])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_energy_parity(model, N):
+    s, q, p = _sys(model, N)
+    K, V = s.energy()
+    assert abs(K - ora.kinetic(p)) <= 1e-12 * max(abs(K), 1e-300)
+    Vo = ora.potential(model, q, EPS[model])
+    assert abs(V - Vo) <= 1e-12 * max(abs(Vo), 1.0), (V, Vo)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_magnetization_parity(model):
+    s, q, p = _sys(model, 10001)
+    mx, my = s.magnetization()
+    ox, oy = ora.magnetization(q)
+    assert abs(mx - ox) < 1e-13 and abs(my - oy) < 1e-13
+
+
+def test_mixed_energy_error_within_twice_fp64():
+    """Long run judged by the relative energy error (Sec. 4): the mixed path's
+    stays within twice the FP64 path's (plus a floor at FP64 resolution)."""
+    res = {}
+    for model, N, dt, nst in ((1, 2048, 0.05, 100), (2, 2048, 0.01, 100), (0, 100000, 0.1, 100)):
+        for prec in ("fp64", "mixed"):
+            s, q, p = _sys(model, N, prec, dt=dt)
+            e0 = sum(s.energy())
+            worst = 0.0
+            for _ in range(10):
+                s.step(nst // 10)
+                worst = max(worst, abs((sum(s.energy()) - e0) / e0))
+            res[(model, prec)] = worst
+        assert res[(model, "mixed")] <= 2 * res[(model, "fp64")] + 1e-12, res
+
+
+# ------------------------------------------------ full-size sampled checks --
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("model,N,eps", [(0, 50_000_000, 0.0), (1, 131072, 0.01), (2, 262144, 1e-4)])
+def test_full_size_sampled_force_parity(model, N, eps, prec):
+    """Bench-size systems in the bench's launch configuration: forces on 64
+    sampled particles against the oracle's direct sums."""
+    s = System(model, N, eps, 0.05, 42 + model, precision=prec)
+    q, _ = s.get_state()
+    f = s.force().reshape(2 if model == 2 else 1, N)
+    rows = np.unique(np.concatenate([[0, N - 1], inputs.splitmix64(9, np.arange(62)) % np.uint64(N)]).astype(np.int64))
+    fo, scale = ora.force_rows(model, q, rows, eps, with_abs=True)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.all(np.abs(f[:, rows] - fo) <= tol * scale), (np.abs(f[:, rows] - fo) / scale).max()
+    s.close()

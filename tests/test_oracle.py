@@ -247,3 +247,14 @@ def test_step_matches_grad_forward_pass(ora):
     q, p = ora.step(1, q0, p0, 0.01, 0.05, 7)
     val, *_ = ora.grad(1, q0, p0, 0.01, 0.05, 7, 0)
     assert val == ora.kinetic(p)
+
+
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+def test_force_rows_equals_full_force(ora, model, eps):
+    q, _ = _state(model, 50, 91)
+    rows = np.array([0, 7, 49, 23])
+    full = ora.force(model, q, eps).reshape(2 if model == 2 else 1, 50)
+    part, ab = ora.force_rows(model, q, rows, eps, with_abs=True)
+    assert np.array_equal(full[:, rows], part)
+    fa = ora.force_abs(model, q, eps).reshape(full.shape)
+    np.testing.assert_allclose(ab, fa[:, rows], rtol=1e-14)
