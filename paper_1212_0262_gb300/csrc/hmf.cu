@@ -42,7 +42,7 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
     float r = (float)reduce_2pi(th);
     float s, c;
     sincos_small(r, &s, &c);
-    float f = c * myf - s * mxf;
+    float f = __fsub_rn(__fmul_rn(c, myf), __fmul_rn(s, mxf));
     if (MODE == STAGE_FORCE_ONLY) {
       a.fout[i] = (double)f;
       return;
@@ -58,7 +58,7 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
   } else {
     double s, c;
     sincos(th, &s, &c);
-    double f = c * my - s * mx;
+    double f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
     if (MODE == STAGE_FORCE_ONLY) {
       a.fout[i] = f;
       return;

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT) pipe_kernel(const float *in, float *out, l
       if (OP == OP_FFMA) a[c] = fmaf(a[c], x, y);
       if (OP == OP_FFMA2) b[c] = __ffma2_rn(b[c], x2, y2);
       if (OP == OP_RSQ) a[c] = sfu_rsqrt(a[c]);
-      if (OP == OP_RCP) a[c] = sfu_rcp(a[c]);
+      if (OP == OP_RCP) a[c] = sfu_rcp(a[c] + y);  // the add keeps rcp(rcp(x)) from folding
       if (OP == OP_SIN) a[c] = sfu_sin(a[c]);
       if (OP == OP_LG2EX2) a[c] = sfu_ex2(sfu_lg2(a[c]));
       if (OP == OP_DFMA) d[c] = fma(d[c], xd, yd);
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(NT) pipe_kernel(const float *in, float *out, l
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
-// operations counted per chain-iteration
+// SFU / FMA operations counted per chain-iteration (the rcp chain's add is not counted)
 const double kOpsPerIter[OP_COUNT] = {1, 2, 1, 1, 1, 2, 1, 2};
 
 template <int OP>
