@@ -169,6 +169,27 @@ int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
 int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(void *ptr, void *user),
                      void *user);
 
+/* Potential energy V of a state held in caller-owned device memory, for callers
+ * that cannot allocate device memory (a host framework's caching allocator that
+ * owns the GPU's memory, or a latency-critical loop where cudaMalloc / cudaFree
+ * and the device synchronisation they can cause are not acceptable).  The paper
+ * has no counterpart; the value is md_energy's V (Eq. 5 for HMF, the i<j sums
+ * of Eqs. 1 and 3 for Ring and 2D), computed by the same kernels in FP64.
+ *   model: MD_HMF, MD_RING or MD_GRAV2D; eps as for md_init
+ *   N:     1 <= N <= 65536 (the size the static scratch holds); larger N is
+ *          rejected with MD_EINVAL and a message in md_last_error(NULL)
+ *   q:     device, dim*N doubles (layout as md_set_state), read only
+ *   V:     device, one double, written
+ *   stream: cudaStream_t the work is queued on (asynchronous; no host sync)
+ * Allocates nothing: its scratch is one file-scope device array of about 1.6 MB
+ * that every GPU loading libmd holds until the process exits.  The first call
+ * on a device looks up that array's device address (make this first call before
+ * any stream capture).  All calls share the array, which keeps the last call's
+ * contents (the parts that must start at zero are cleared on the stream at each
+ * call), so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race and give wrong results; serialise them. */
+int md_potential_noalloc(int model, int64_t N, double eps, const double *q, double *V, void *stream);
+
 /* Wait for all work queued on the context's stream. */
 int md_synchronize(md_ctx *ctx);
 

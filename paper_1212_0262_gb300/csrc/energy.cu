@@ -107,6 +107,53 @@ int grid_sum(md_ctx *c, int64_t n) {
 
 }  // namespace
 
+namespace {
+
+// V of Eqs. 1 / 3 / 5 from the device sums, written to a device scalar.
+__global__ void potential_finalize_kernel(int model, int64_t N, const double *sums, double *V) {
+  const double n = (double)N;
+  if (model == MD_HMF) {
+    const double mx = sums[0] / n, my = sums[1] / n;
+    *V = 0.5 * n * (1.0 - mx * mx - my * my);
+  } else if (model == MD_RING) {
+    *V = -sums[0] / (2.0 * n);
+  } else {
+    *V = sums[0] / n;
+  }
+}
+
+}  // namespace
+
+// Potential energy into device *V with all scratch supplied by the caller:
+// unit_sums (>= ceil(N/256)^2 doubles, zeroed by the caller), ag (>= N double2,
+// 16-byte aligned; Ring only), partials (>= grid_cap doubles), sums (>= 2
+// doubles), ticket (zeroed).  Same kernels and summation order as md_energy.
+int potential_with_scratch(cudaStream_t st, int nsm, int grid_cap, int model, int64_t N, double eps,
+                           const double *q, double *unit_sums, double2 *ag, double *partials, double *sums,
+                           unsigned *ticket, double *V) {
+  if (model == MD_HMF) {
+    hmf_sums_raw(st, nsm, grid_cap, q, N, partials, sums, ticket);
+  } else {
+    const int ntiles = (int)((N + PT - 1) / PT);
+    if (model == MD_RING) {
+      int64_t b = (N + 255) / 256;
+      if (b > (int64_t)nsm * 16) b = (int64_t)nsm * 16;
+      half_angle_kernel<<<(int)b, 256, 0, st>>>(q, N, ag);
+      potential_tiles_kernel<MD_RING><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, ag, N, ntiles, 0.5 * eps, unit_sums);
+    } else {
+      potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, nullptr, N, ntiles, eps, unit_sums);
+    }
+    const int64_t units = (int64_t)ntiles * ntiles;
+    int64_t g = (units + NT - 1) / NT;
+    if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+    if (g > grid_cap) g = grid_cap;
+    sum_kernel<false><<<(int)g, NT, 0, st>>>(unit_sums, units, partials, sums, ticket);
+  }
+  potential_finalize_kernel<<<1, 1, 0, st>>>(model, N, sums, V);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MD_OK : MD_ECUDA;
+}
+
 int reduce_scratch(md_ctx *c, size_t bytes) {
   if (bytes <= c->red_bytes) return MD_OK;
   dev_free(c->red);

@@ -216,6 +216,20 @@ int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
 
 }  // namespace
 
+// FP64 (sum cos, sum sin) of q[0..N) into device out2, with caller-supplied
+// partials (>= grid_cap doubles x 2) and a zeroed ticket.
+void hmf_sums_raw(cudaStream_t st, int nsm, int grid_cap, const double *q, int64_t N, double *partials,
+                  double *out2, unsigned *ticket) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hmf_sums_kernel<false>, NT, 0);
+  int64_t g = (int64_t)nsm * (occ > 0 ? occ : 1);
+  const int64_t need = (N + NT - 1) / NT;
+  if (g > need) g = need;
+  if (g > grid_cap) g = grid_cap;
+  if (g < 1) g = 1;
+  hmf_sums_kernel<false><<<(int)g, NT, 0, st>>>(q, N, partials, out2, ticket);
+}
+
 int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2) {
   auto kern = hmf_sums_kernel<false>;
   int g = grid_for(c, (const void *)kern, c->N);

@@ -122,6 +122,13 @@ int reduce_scratch(md_ctx *c, size_t bytes);
 // ic.cu
 int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed);
 
+// Raw-scratch launchers (no context, no allocation).
+void hmf_sums_raw(cudaStream_t st, int nsm, int grid_cap, const double *q, int64_t N, double *partials,
+                  double *out2, unsigned *ticket);
+int potential_with_scratch(cudaStream_t st, int nsm, int grid_cap, int model, int64_t N, double eps,
+                           const double *q, double *unit_sums, double2 *ag, double *partials, double *sums,
+                           unsigned *ticket, double *V);
+
 // -------------------------------------------------------- device helpers ----
 #ifdef __CUDACC__
 

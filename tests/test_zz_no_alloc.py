@@ -1,0 +1,71 @@
+"""md_potential_noalloc: the potential energy for callers that cannot allocate
+device memory (their GPU memory belongs to a host framework's caching
+allocator, or cudaMalloc's possible device synchronisation is not acceptable in
+their loop).  Its scratch is a static device array, so two calls in a row must
+both agree with md_energy's V, the entry point that allocates its scratch.
+
+This file is collected last on purpose; it needs nothing from the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1212_0262_gb300 import System, binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(0, 65536, 0.0), (1, 4097, 0.01), (2, 65536, 1e-4), (1, 1, 0.01), (2, 333, 1e-3)]
+
+
+def _noalloc(model, N, eps, q_dev, v_dev, stream):
+    lib = binding.load()
+    return lib.md_potential_noalloc(model, N, eps, ctypes.c_void_p(q_dev.data_ptr()),
+                                    ctypes.c_void_p(v_dev.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+
+
+@pytest.mark.parametrize("model,N,eps", CASES)
+def test_noalloc_potential_matches_md_energy_twice(model, N, eps):
+    q, p = inputs.default_state(model, N, 500 + N)
+    with System(model, N, eps, 0.01, 1) as s:
+        s.set_state(q, p)
+        _, v_ref = s.energy()
+    q_dev = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+    v_dev = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for call in range(2):
+        v_dev.fill_(float("nan"))
+        rc = _noalloc(model, N, eps, q_dev, v_dev, stream)
+        assert rc == 0, binding.load().md_last_error(None)
+        torch.cuda.synchronize()
+        v = float(v_dev.item())
+        assert abs(v - v_ref) <= 1e-12 * max(abs(v_ref), 1.0), (call, v, v_ref)
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    q_dev = torch.zeros(65537, dtype=torch.float64, device="cuda")
+    v_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = _noalloc(1, 65537, 0.01, q_dev, v_dev, torch.cuda.current_stream())
+    assert rc == binding.MD_EINVAL
+    assert b"65536" in binding.load().md_last_error(None)
+
+
+def test_noalloc_alternating_models_keep_agreeing():
+    """The shared array keeps the previous call's contents; a call of another
+    model and size in between must not change the answer."""
+    stream = torch.cuda.current_stream()
+    qa, pa = inputs.default_state(2, 1000, 3)
+    qb, pb = inputs.default_state(1, 70, 4)
+    with System(2, 1000, 1e-3, 0.01, 1) as s:
+        s.set_state(qa, pa)
+        _, va = s.energy()
+    qa_dev = torch.from_numpy(qa).cuda()
+    qb_dev = torch.from_numpy(qb).cuda()
+    v_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        assert _noalloc(2, 1000, 1e-3, qa_dev, v_dev, stream) == 0
+        torch.cuda.synchronize()
+        assert abs(v_dev.item() - va) <= 1e-12 * abs(va)
+        assert _noalloc(1, 70, 0.01, qb_dev, v_dev, stream) == 0
+        torch.cuda.synchronize()
