@@ -38,6 +38,9 @@ WORKLOADS = {
                  name="Ring N=131,072 eps=0.01 dt=0.05 (all-pairs)"),
     "grav2d": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
                    name="2D self-gravitating N=262,144 eps=1e-4 dt=0.01 (all-pairs)"),
+    "ensemble": dict(model=-1, N=0, eps=0.0, dt=0.0, seed=1000, unit="pair-interactions/s",
+                     name="ensemble: 128 Ring (eps=0.01, dt=0.05) + 128 2D (eps=1e-4, dt=0.01), "
+                          "N log-uniform in [4096, 65536], one persistent launch per stage"),
 }
 # algorithmic bytes per particle per fused HMF stage: read + write FP64 theta and p
 HMF_BYTES_PER_PARTICLE_STAGE = 32
@@ -55,8 +58,10 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
     a = ap.parse_args()
-    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3)}[a.workload]
+    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "ensemble": (20, 3)}[a.workload]
     if a.steps is None:
         a.steps = dflt[0]
     if a.warmup is None:
@@ -209,9 +214,23 @@ def run_reference(args, w):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
-    n = oracle_sample_size(w, 60.0, K + W)
-    units, el, sample = oracle_steps(w, n, K, W)
-    rate = units / el
+    if w["model"] == -1:
+        # ensemble: the oracle on one Ring and one 2D member (the first of each half)
+        models, Ns, eps, dts, seeds = ensemble_spec()
+        units = el = 0.0
+        parts = []
+        for s in (0, len(Ns) // 2):
+            ws_ = dict(model=models[s], N=int(Ns[s]), eps=eps[s], dt=dts[s], seed=seeds[s])
+            n = oracle_sample_size(ws_, 30.0, K + W)
+            u_, e_, smp = oracle_steps(ws_, n, K, W)
+            units += u_
+            el += e_
+            parts.append(f"system {s} ({'Ring' if models[s] == 1 else '2D'}, N={Ns[s]}): {smp}")
+        rate, sample = units / el, "; ".join(parts)
+    else:
+        n = oracle_sample_size(w, 60.0, K + W)
+        units, el, sample = oracle_steps(w, n, K, W)
+        rate = units / el
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": w["unit"], "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
@@ -369,7 +388,7 @@ def run_ours(args, w):
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         n = sysm.dim * N
         qh = torch.empty(n, dtype=torch.float64, pin_memory=True)
         ph = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -416,12 +435,109 @@ def run_ours(args, w):
         torch.distributed.destroy_process_group()
 
 
+def ensemble_spec(nsys=256, seed=1000):
+    """Models, sizes, softenings, steps and seeds of the batched-ensemble workload."""
+    from paper_1212_0262_gb300 import inputs
+
+    Ns = inputs.ensemble_sizes(nsys, seed)
+    models = [1 if s < nsys // 2 else 2 for s in range(nsys)]
+    eps = [0.01 if m == 1 else 1e-4 for m in models]
+    dts = [0.05 if m == 1 else 0.01 for m in models]
+    seeds = [seed + s for s in range(nsys)]
+    return models, Ns, eps, dts, seeds
+
+
+def run_ensemble(args, w):
+    import ctypes as _c
+
+    import numpy as np
+    import torch
+
+    from paper_1212_0262_gb300 import Ensemble, binding
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    models, Ns, eps, dts, seeds = ensemble_spec()
+    ens = Ensemble(models, Ns, eps, dts, seeds, precision=args.prec)
+    ens.set_stream(stream)
+    t0 = time.perf_counter()
+    tuned_ms = ens.autotune()
+    tune_s = time.perf_counter() - t0
+    K0, V0 = ens.energy()
+    K, W = args.steps, args.warmup
+    if W:
+        ens.step(W)
+    pairs_per_stage = float(np.sum(np.asarray(Ns, dtype=np.float64) ** 2))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(device_uuid(local))
+    l0 = ens.launch_count
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    ens.step(K)
+    b.record(stream)
+    b.synchronize()
+    launches = ens.launch_count - l0
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    K1, V1 = ens.energy()
+    e0, e1 = K0 + V0, K1 + V1
+    de = np.abs((e1 - e0) / e0)
+    value = ws * 3 * pairs_per_stage * K / (ms * 1e-3)
+    nl = 3 * K + 1
+    avg_ms = ms / nl
+    rates = np.zeros(17)
+    binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(_c.POINTER(_c.c_double)), 17)
+    nsm = rates[0]
+    fp32 = max(rates[1], rates[3])
+    per_clk_ring = min(fp32 / PAIR_OPS[1][0], rates[5] / PAIR_OPS[1][1])
+    per_clk_2d = min(fp32 / PAIR_OPS[2][0], rates[7] / PAIR_OPS[2][1])
+    w_ring = float(sum(n * n for n, m in zip(Ns, models) if m == 1))
+    w_2d = pairs_per_stage - w_ring
+    mhz = clocks.get("sm_mhz") or rates[2]
+    # time-optimal pair rate for this mix of Ring and 2D pairs
+    peak = pairs_per_stage / (w_ring / (nsm * per_clk_ring * mhz * 1e6) + w_2d / (nsm * per_clk_2d * mhz * 1e6))
+    achieved = pairs_per_stage / (avg_ms * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 state / f32 pair arithmetic" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "systems": len(Ns), "sum_N": int(np.sum(Ns)),
+                       "sum_N2": pairs_per_stage, "precision": args.prec,
+                       "l2": "state and mirrors of all systems ~180 MB > L2"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pair-interactions/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch_kernel (Ring + 2D parts)",
+                         "avg_launch_ms": avg_ms, "launches": nl},
+            "autotune": {"seconds": tune_s, "best_force_launch_ms": tuned_ms},
+            "rel_energy_error": {"max": float(de.max()), "median": float(np.median(de))},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+
+
 def main():
     args = parse()
-    w = WORKLOADS[args.workload]
+    if args.workload == "ensemble" and args.impl == "ours":
+        run_ensemble(args, WORKLOADS["ensemble"])
+        return
+    w = dict(WORKLOADS[args.workload])
+    if args.n:
+        w["N"] = args.n
+        w["name"] = w["name"].split(" N=")[0] + f" N={args.n:,} (reduced size)"
     if args.impl == "reference":
         run_reference(args, w)
-        ws, rank, _ = dist_info()
         return
     run_ours(args, w)
 

@@ -96,6 +96,9 @@ int md_set_stream(md_ctx *ctx, void *stream);
 /* Change the time step (Sec. 3, Eq. 4).  dt may be negative (backward flow). */
 int md_set_dt(md_ctx *ctx, double dt);
 
+/* Change the softening eps of Eqs. 1 and 3 (> 0 for Ring/2D, >= 0 for HMF). */
+int md_set_eps(md_ctx *ctx, double eps);
+
 /* Tuning knobs of the kernels (used by the autotuner; defaults are sensible):
  *   "r_mixed"          i-particles per thread of the FP32 pair kernels (4 or 8)
  *   "r_fp64"           i-particles per thread of the FP64 pair kernels (2 or 4)
@@ -209,8 +212,18 @@ md_batch *md_batch_init(int nsys, const int *model, const int64_t *N, const doub
 void md_batch_free(md_batch *b);
 int md_batch_set_precision(md_batch *b, int precision);
 int md_batch_set_stream(md_batch *b, void *stream);
-/* Advance every system by nsteps steps of Sec. 3 (asynchronous). */
+/* Advance every system by nsteps steps of Sec. 3 (asynchronous).  Three fused
+ * force + kick + drift launches per step cover all systems; blocks of steps are
+ * replayed from a captured CUDA graph. */
 int md_batch_step(md_batch *b, int64_t nsteps);
+/* Kernel shape of the batched launches: r i-particles per thread (4 or 8),
+ * fraction `split` (0, 1) of the CTAs given to the Ring systems, CTAs per SM
+ * (0 = occupancy limit). */
+int md_batch_set_tuning(md_batch *b, int r, double split, int ctas_per_sm);
+/* Time candidate shapes (r, split, CTAs per SM) on force-only launches, which
+ * leave every state unchanged, and keep the fastest.  *best_ms (may be NULL)
+ * receives the fastest launch time.  Synchronous. */
+int md_batch_autotune(md_batch *b, double *best_ms);
 /* K[s], V[s] for every system (host arrays of nsys).  Synchronous. */
 int md_batch_energy(md_batch *b, double *K, double *V);
 /* Host state of system s (dim*N[s] doubles each). */

@@ -42,6 +42,7 @@ _SIGS = {
     "md_set_precision": (_c.c_int, [_P, _c.c_int]),
     "md_set_stream": (_c.c_int, [_P, _P]),
     "md_set_dt": (_c.c_int, [_P, _c.c_double]),
+    "md_set_eps": (_c.c_int, [_P, _c.c_double]),
     "md_set_tuning": (_c.c_int, [_P, _c.c_char_p, _c.c_int64]),
     "md_set_ic": (_c.c_int, [_P, _c.c_int, _D, _c.c_uint64]),
     "md_set_state": (_c.c_int, [_P, _P, _P]),
@@ -65,6 +66,8 @@ _SIGS = {
     "md_batch_set_precision": (_c.c_int, [_P, _c.c_int]),
     "md_batch_set_stream": (_c.c_int, [_P, _P]),
     "md_batch_step": (_c.c_int, [_P, _c.c_int64]),
+    "md_batch_set_tuning": (_c.c_int, [_P, _c.c_int, _c.c_double, _c.c_int]),
+    "md_batch_autotune": (_c.c_int, [_P, _D]),
     "md_batch_energy": (_c.c_int, [_P, _P, _P]),
     "md_batch_get_state": (_c.c_int, [_P, _c.c_int, _P, _P]),
     "md_batch_set_state": (_c.c_int, [_P, _c.c_int, _P, _P]),

@@ -137,6 +137,7 @@ void md_free(md_ctx *c) {
   dev_free(c->sk_slots);
   dev_free(c->sk_tickets);
   dev_free(c->red);
+  dev_free(c->gw);
   if (c->host_scalars) cudaFreeHost(c->host_scalars);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -184,7 +185,7 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
   c->q = (double *)dev_alloc(nb);
   c->p = (double *)dev_alloc(nb);
   c->f = (double *)dev_alloc(nb);
-  c->hmf_partials = (double *)dev_alloc(sizeof(double) * 2 * c->hmf_grid_max);
+  c->hmf_partials = (double *)dev_alloc(sizeof(double) * 4 * c->hmf_grid_max);
   c->hmf_m = (double *)dev_alloc(sizeof(double) * 16);
   c->hmf_ticket = (unsigned *)dev_alloc(sizeof(unsigned) * 4);
   if (!c->q || !c->p || !c->f || !c->hmf_partials || !c->hmf_m || !c->hmf_ticket) {
@@ -304,6 +305,12 @@ int md_get_state_device(md_ctx *c, double *q, double *p) {
 int md_step(md_ctx *c, int64_t nsteps) {
   CHECK_CTX(c);
   if (nsteps < 0) return set_err(c, MD_EINVAL, "md_step: nsteps < 0");
+  return integrate(c, nsteps);
+}
+
+}  // extern "C"
+
+int integrate(md_ctx *c, int64_t nsteps) {
   if (nsteps == 0) return MD_OK;
   double k[4];
   yoshida_coefficients(k);
@@ -333,6 +340,8 @@ int md_step(md_ctx *c, int64_t nsteps) {
   c->fsal_prec = c->prec;
   return MD_OK;
 }
+
+extern "C" {
 
 void md_yoshida(double *c4) {
   if (c4) yoshida_coefficients(c4);

@@ -177,6 +177,15 @@ int kinetic_fp64(md_ctx *c, double *d_out) {
   return MD_OK;
 }
 
+// Deterministic FP64 sum of x[0..n) into device *d_out.
+int sum_fp64(md_ctx *c, const double *x, int64_t n, double *d_out) {
+  int g = grid_sum(c, n);
+  if (g > c->hmf_grid_max) g = c->hmf_grid_max;
+  sum_kernel<false><<<g, NT, 0, c->stream>>>(x, n, c->hmf_partials, d_out, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
 // Pair-sum part of the potential of Eq. 1 (Ring) or Eq. 3 (2D), prefactor
 // applied, into device *d_out.  Uses ctx->red as scratch.
 int pair_potential_fp64(md_ctx *c, double *d_out) {

@@ -39,18 +39,21 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
                                              float myf, double mx, double my, float dtf, float &acf,
                                              float &asf, double &acd, double &asd, int64_t i) {
   if (MIXED) {
-    float r = (float)reduce_2pi(th);
+    // Only the kick and the drift use the FP64 pipe (two DFMA per particle):
+    // range reduction and float<->double conversions move bits on the integer
+    // pipe, and the sines and cosines are FP32 polynomials.
+    float r = reduce_2pi_f(th);
     float s, c;
     sincos_small(r, &s, &c);
     float f = __fsub_rn(__fmul_rn(c, myf), __fmul_rn(s, mxf));
     if (MODE == STAGE_FORCE_ONLY) {
-      a.fout[i] = (double)f;
+      a.fout[i] = f2d_bits(f);
       return;
     }
-    pp = fma(a.kick, (double)f, pp);
+    pp = fma(a.kick, f2d_bits(f), pp);
     if (MODE == STAGE_KICK_DRIFT) {
       th = fma(a.drift, pp, th);
-      float r2 = fmaf(dtf, (float)pp, r);
+      float r2 = fmaf(dtf, d2f_trunc_bits(pp), r);
       sincos_small(r2, &s, &c);
       acf += c;
       asf += s;
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
     double th = q[i];
     if (MIXED) {
       float s, c;
-      sincos_small((float)reduce_2pi(th), &s, &c);
+      sincos_small(reduce_2pi_f(th), &s, &c);
       acf += c;
       asf += s;
     } else {
@@ -274,4 +277,182 @@ int hmf_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
     return mixed ? launch_stage<true, STAGE_FORCE_ONLY>(c, kick, drift, fout)
                  : launch_stage<false, STAGE_FORCE_ONLY>(c, kick, drift, fout);
   }
+}
+
+// ---------------------------------------------------------------- adjoint --
+//
+// Reverse stages of md_grad for HMF.  With Eqs. 6-7, J = df/dtheta gives
+//   (J v)_i = -(sin t_i My + cos t_i Mx) v_i + cos t_i A + sin t_i B,
+//   A = (1/N) sum cos t_k v_k,  B = (1/N) sum sin t_k v_k,
+// so each reverse stage needs the four sums (sum cos, sum sin, sum cos v,
+// sum sin v) of the current angles and lambda_p, which the previous reverse
+// stage leaves behind (same deterministic grid finish as the forward).
+
+namespace {
+
+struct HmfAdjArgs {
+  double *q, *p, *lq, *lp;
+  int64_t N;
+  double invN;
+  const double *s_in;  // 4 sums of the current (theta, lambda_p)
+  double b_adj, b_undo, drift;
+  double *partials;  // 4 per CTA
+  double *s_out;
+  unsigned *ticket;
+};
+
+__device__ __forceinline__ void grid_finish4(double v0, double v1, double v2, double v3, double *partials,
+                                             double *out, unsigned *ticket) {
+  __shared__ double2 red[NT / 32];
+  __shared__ bool last;
+  double2 b01 = block_sum2<NT>(v0, v1, red);
+  __syncthreads();
+  double2 b23 = block_sum2<NT>(v2, v3, red);
+  if (threadIdx.x == 0) {
+    partials[4 * blockIdx.x] = b01.x;
+    partials[4 * blockIdx.x + 1] = b01.y;
+    partials[4 * blockIdx.x + 2] = b23.x;
+    partials[4 * blockIdx.x + 3] = b23.y;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double c[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += NT)
+#pragma unroll
+    for (int k = 0; k < 4; k++) c[k] += __ldcg(partials + 4 * j + k);
+  __syncthreads();
+  double2 t01 = block_sum2<NT>(c[0], c[1], red);
+  __syncthreads();
+  double2 t23 = block_sum2<NT>(c[2], c[3], red);
+  if (threadIdx.x == 0) {
+    out[0] = t01.x;
+    out[1] = t01.y;
+    out[2] = t23.x;
+    out[3] = t23.y;
+    *ticket = 0u;
+  }
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void sc_of(double th, double &s, double &c) {
+  if (MIXED) {
+    float sf, cf;
+    sincos_small(reduce_2pi_f(th), &sf, &cf);
+    s = f2d_bits(sf);
+    c = f2d_bits(cf);
+  } else {
+    sincos(th, &s, &c);
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) hmf_adj_sums_kernel(const double *__restrict__ q, const double *__restrict__ lp,
+                                                          int64_t N, double *partials, double *out, unsigned *ticket) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < N; i += G) {
+    double s, c;
+    sc_of<MIXED>(q[i], s, c);
+    const double v = lp[i];
+    a0 += c;
+    a1 += s;
+    a2 = fma(c, v, a2);
+    a3 = fma(s, v, a3);
+  }
+  grid_finish4(a0, a1, a2, a3, partials, out, ticket);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) hmf_adj_stage_kernel(HmfAdjArgs a) {
+  const double mx = a.s_in[0] * a.invN, my = a.s_in[1] * a.invN;
+  const double A = a.s_in[2] * a.invN, B = a.s_in[3] * a.invN;
+  const float mxf = (float)mx, myf = (float)my;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.N; i += G) {
+    double th = a.q[i], pp = a.p[i], lq = a.lq[i], lp = a.lp[i];
+    double s, c, f;
+    sc_of<MIXED>(th, s, c);
+    if (MIXED)  // the same FP32 force as the forward stage, so the reversal undoes it
+      f = f2d_bits(__fsub_rn(__fmul_rn((float)c, myf), __fmul_rn((float)s, mxf)));
+    else
+      f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
+    const double jv = fma(-fma(s, my, c * mx), lp, fma(c, A, s * B));
+    lq = fma(a.b_adj, jv, lq);
+    pp = fma(-a.b_undo, f, pp);
+    if (a.drift != 0.0) {
+      lp = fma(a.drift, lq, lp);
+      th = fma(-a.drift, pp, th);
+      sc_of<MIXED>(th, s, c);
+      a0 += c;
+      a1 += s;
+      a2 = fma(c, lp, a2);
+      a3 = fma(s, lp, a3);
+      a.q[i] = th;
+      a.lp[i] = lp;
+    }
+    a.p[i] = pp;
+    a.lq[i] = lq;
+  }
+  if (a.drift != 0.0) grid_finish4(a0, a1, a2, a3, a.partials, a.s_out, a.ticket);
+}
+
+// lambda_q of the |M| observable: d|M|/dtheta_i = (My cos t_i - Mx sin t_i) / (N |M|).
+__global__ void hmf_mag_terminal_kernel(const double *__restrict__ q, int64_t N, double cx, double cy,
+                                        double *__restrict__ lq) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
+    double s, c;
+    sincos(q[i], &s, &c);
+    lq[i] = fma(cx, c, -cy * s);
+  }
+}
+
+}  // namespace
+
+// Four sums of the current (theta, lambda_p) into the current adjoint slot.
+int hmf_adjoint_prime(md_ctx *c, const double *lp, double *sums) {
+  const int g = grid_for(c, (const void *)hmf_adj_sums_kernel<true>, c->N);
+  if (c->prec == MD_MIXED)
+    hmf_adj_sums_kernel<true><<<g, NT, 0, c->stream>>>(c->q, lp, c->N, c->hmf_partials, sums, c->hmf_ticket);
+  else
+    hmf_adj_sums_kernel<false><<<g, NT, 0, c->stream>>>(c->q, lp, c->N, c->hmf_partials, sums, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
+int hmf_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, double *lq, double *lp,
+                      const double *s_in, double *s_out) {
+  HmfAdjArgs a;
+  a.q = c->q;
+  a.p = c->p;
+  a.lq = lq;
+  a.lp = lp;
+  a.N = c->N;
+  a.invN = 1.0 / (double)c->N;
+  a.s_in = s_in;
+  a.b_adj = b_adj;
+  a.b_undo = b_undo;
+  a.drift = drift;
+  a.partials = c->hmf_partials;
+  a.s_out = s_out;
+  a.ticket = c->hmf_ticket;
+  const int g = grid_for(c, (const void *)hmf_adj_stage_kernel<false>, c->N);
+  if (c->prec == MD_MIXED)
+    hmf_adj_stage_kernel<true><<<g, NT, 0, c->stream>>>(a);
+  else
+    hmf_adj_stage_kernel<false><<<g, NT, 0, c->stream>>>(a);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
+int hmf_magnetization_terminal(md_ctx *c, double cx, double cy, double *lq) {
+  int64_t b = (c->N + 255) / 256;
+  if (b > (int64_t)c->nsm * 16) b = (int64_t)c->nsm * 16;
+  hmf_mag_terminal_kernel<<<(int)b, 256, 0, c->stream>>>(c->q, c->N, cx, cy, lq);
+  MD_LAUNCHED(c);
+  return MD_OK;
 }

@@ -65,6 +65,9 @@ struct md_ctx {
   // reductions (energies)
   double *red = nullptr;
   size_t red_bytes = 0;
+  // md_grad workspace: checkpoints, lambda_q, lambda_p, eps terms, sums
+  double *gw = nullptr;
+  size_t gw_bytes = 0;
   double *host_scalars = nullptr;  // pinned, 16 doubles
 
   PairTuning pt;
@@ -101,7 +104,25 @@ enum StageMode {
   STAGE_KICK_DRIFT = 0,  // f(q); p += kick f; q += drift p; refresh mirror / reduction
   STAGE_KICK_ONLY = 1,   // f(q); p += kick f; store f in ctx->f (first-same-as-last cache)
   STAGE_FORCE_ONLY = 2,  // f(q) into an output array
+  STAGE_ADJOINT = 3,     // reverse stage of md_grad (kick adjoint and undo, drift adjoint and undo)
 };
+
+// api.cu: nsteps integrator steps of Sec. 3 on the context's state (md_step's body).
+int integrate(md_ctx *c, int64_t nsteps);
+
+// pairs.cu: adjoint records (position and lambda_p) and one reverse stage:
+//   lambda_q += b_adj J(q) lambda_p; epsacc += b_adj <lambda_p, df/deps>;
+//   p -= b_undo f(q); then, if drift != 0: lambda_p += drift lambda_q; q -= drift p.
+int adjoint_mirror_refresh(md_ctx *c, const double *lp);
+int pair_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, double *lq, double *lp,
+                       double *epsacc);
+
+// hmf.cu: the same reverse stage in mean-field form; sums = (sum cos, sum sin,
+// sum cos lambda_p, sum sin lambda_p) of the current state.
+int hmf_adjoint_prime(md_ctx *c, const double *lp, double *sums);
+int hmf_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, double *lq, double *lp,
+                      const double *s_in, double *s_out);
+int hmf_magnetization_terminal(md_ctx *c, double cx, double cy, double *lq);
 
 // hmf.cu
 int hmf_prime(md_ctx *c);                                         // sums of the current angles
@@ -118,6 +139,7 @@ int kick_drift_cached(md_ctx *c, double kick, double drift);      // first stage
 int kinetic_fp64(md_ctx *c, double *d_out);                       // (1/2) sum p^2 into device out
 int pair_potential_fp64(md_ctx *c, double *d_out);                // i<j sum of Eq. 1 / Eq. 3
 int reduce_scratch(md_ctx *c, size_t bytes);
+int sum_fp64(md_ctx *c, const double *x, int64_t n, double *d_out);  // deterministic sum into device out
 
 // ic.cu
 int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed);
@@ -191,6 +213,53 @@ __device__ __forceinline__ void sincos_small(float x, float *s, float *c) {
   const float b = (q & 1) ? sy : cy;
   *s = (q & 2) ? -a : a;
   *c = ((q + 1) & 2) ? -b : b;
+}
+
+// Exact float -> double by moving bits (no FP64 instruction): exponent rebias
+// 127 -> 1023 and mantissa shift 23 -> 52.  Zero and subnormal floats give a
+// signed zero; infinities and NaN are not handled (they never reach it).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned a = u & 0x7fffffffu;
+  unsigned hi = (u & 0x80000000u) | ((a >> 3) + 0x38000000u);
+  unsigned lo = a << 29;
+  if (a < 0x00800000u) {
+    hi = u & 0x80000000u;
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float by truncating the mantissa (moving bits, no FP64 instruction),
+// for |d| below 2^128; magnitudes below the float normal range give zero.
+__device__ __forceinline__ float d2f_trunc_bits(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned a = hi & 0x7fffffffu;
+  unsigned fb = ((a - 0x38000000u) << 3) | (lo >> 29);
+  if (a < 0x38100000u) fb = 0u;
+  return __uint_as_float((hi & 0x80000000u) | fb);
+}
+
+// theta - 2 pi k (k the nearest integer to theta / 2 pi) as a float, for
+// |theta| < 2^20, using no FP64 instruction.  theta = th_hi + th_lo exactly up
+// to its last 6 bits: th_hi is theta truncated to a float and th_lo the next 23
+// mantissa bits (an integer made exact by the 2^23 magic constant, scaled by a
+// power of two built from theta's exponent).  Then one Cody-Waite step with
+// 2 pi split into two floats.  Absolute error a few 1e-7.
+__device__ __forceinline__ float reduce_2pi_f(double th) {
+  const unsigned hi = (unsigned)__double2hiint(th), lo = (unsigned)__double2loint(th);
+  const unsigned sign = hi & 0x80000000u, a = hi & 0x7fffffffu, E = a >> 20;
+  float th_hi = __uint_as_float(sign | (((a - 0x38000000u) << 3) | (lo >> 29)));
+  const unsigned m23 = (lo & 0x1fffffffu) >> 6;  // weight of bit 0: 2^(E - 1069)
+  float th_lo = (__uint_as_float(0x4b000000u | m23) - 8388608.0f) * __uint_as_float((E - 942u) << 23);
+  th_lo = __uint_as_float(__float_as_uint(th_lo) | sign);
+  if (E < 943u) th_lo = 0.0f;
+  if (E < 897u) th_hi = 0.0f;
+  const float t = fmaf(th_hi, 0.15915493667125702f, 12582912.0f);
+  const float k = t - 12582912.0f;
+  float r = fmaf(-k, 6.2831854820251465f, th_hi);
+  r = fmaf(-k, -1.7484555314695172e-07f, r);
+  return r + th_lo;
 }
 
 // theta - 2 pi k with k = rint(theta / 2 pi), in FP64 (two-constant Cody-Waite).

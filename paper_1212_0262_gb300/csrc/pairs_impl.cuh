@@ -1,0 +1,622 @@
+// Shared pieces of the all-pairs kernels (single systems in pairs.cu, batched
+// ensembles in batch.cu): launch arguments, mirror records, per-model pair
+// policies (tile bodies) and epilogues.  See pairs.cu for the method.
+#pragma once
+#include <algorithm>
+
+#include "md_internal.cuh"
+
+namespace {
+
+constexpr int NT = kPairThreads;
+constexpr int kPadMultiple = 1024;  // mirror padding: multiple of every TI and TJ
+
+// bytes per particle of a mirror record
+template <int MODEL, bool MIXED, bool ADJ>
+struct RecordBytes {
+  static constexpr int value =
+      MODEL == MD_RING ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32)) : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
+};
+
+struct PairArgs {
+  const void *mirror_in;
+  void *mirror_out;
+  double *q, *p;
+  int64_t N;
+  int64_t n_it, n_jt, U;
+  int P;
+  double epsd;    // Ring: eps/2; 2D: eps
+  double kick, drift;
+  double *slots;  // [P][2][NACC][TI] FP64 partial sums
+  unsigned *tickets;
+  double *fout;   // STAGE_KICK_ONLY / STAGE_FORCE_ONLY force output (dim*N)
+  // adjoint stages
+  double *lq, *lp;   // lambda_q, lambda_p (dim*N)
+  double *epsacc;    // per-particle accumulated d O / d eps terms (N)
+  double undo;       // kick coefficient (times dt) removed from p
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+__host__ __device__ __forceinline__ int64_t unit_begin(int64_t U, int P, int64_t c) { return (U * c) / P; }
+// CTA whose range holds unit u: max c with U c / P <= u.
+__device__ __forceinline__ int64_t cta_of_unit(int64_t U, int P, int64_t u) { return ((u + 1) * P - 1) / U; }
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// ============================================================ records ======
+
+// Mirror record of particle i at FP64 position(s) (x, y) and, for adjoint
+// records, lambda_p (vx, vy).  FP32 records interleave particles 2k and 2k+1
+// so that one 128-bit load gives a packed operand for two j's.
+template <int MODEL, bool MIXED, bool ADJ>
+__device__ __forceinline__ void write_record(void *mirror, int64_t i, double x, double y, double vx, double vy) {
+  if constexpr (MODEL == MD_RING) {
+    const double r = reduce_2pi(x);
+    if constexpr (MIXED) {
+      float s, c, a, g;
+      sincos_small((float)r, &s, &c);
+      sincos_small(0.5f * (float)r, &a, &g);
+      float *m = (float *)mirror + (i >> 1) * (ADJ ? 12 : 8) + (i & 1);
+      m[0] = -s;
+      m[2] = c;
+      m[4] = -a;
+      m[6] = g;
+      if (ADJ) {
+        m[8] = -(float)vx;
+        m[10] = 0.f;
+      }
+    } else {
+      double s, c, a, g;
+      sincos(x, &s, &c);
+      sincos(0.5 * r, &a, &g);
+      double *m = (double *)mirror + i * (ADJ ? 6 : 4);
+      m[0] = s;
+      m[1] = c;
+      m[2] = a;
+      m[3] = g;
+      if (ADJ) {
+        m[4] = vx;
+        m[5] = 0.0;
+      }
+    }
+  } else {
+    if constexpr (MIXED) {
+      float *m = (float *)mirror + (i >> 1) * (ADJ ? 8 : 4) + (i & 1);
+      m[0] = -(float)x;
+      m[2] = -(float)y;
+      if (ADJ) {
+        m[4] = -(float)vx;
+        m[6] = -(float)vy;
+      }
+    } else {
+      double *m = (double *)mirror + i * (ADJ ? 4 : 2);
+      m[0] = x;
+      m[1] = y;
+      if (ADJ) {
+        m[2] = vx;
+        m[3] = vy;
+      }
+    }
+  }
+}
+
+// Padding record: contributes exactly zero to every sum.  Ring: all-zero
+// (sin d = 0 with a positive denominator).  2D: so far away that |r|^2 overflows
+// to +inf in FP32, whose reciprocal is 0 (FP64: 1e150, whose FP32 Newton seed
+// is +inf -> 0, and the Newton steps keep 0).
+template <int MODEL, bool MIXED, bool ADJ>
+__device__ __forceinline__ void write_pad(void *mirror, int64_t i) {
+  if constexpr (MODEL == MD_RING) {
+    if constexpr (MIXED) {
+      float *m = (float *)mirror + (i >> 1) * (ADJ ? 12 : 8) + (i & 1);
+      m[0] = m[2] = m[4] = m[6] = 0.f;
+      if (ADJ) m[8] = m[10] = 0.f;
+    } else {
+      double *m = (double *)mirror + i * (ADJ ? 6 : 4);
+      for (int k = 0; k < (ADJ ? 6 : 4); k++) m[k] = 0.0;
+    }
+  } else {
+    if constexpr (MIXED) {
+      float *m = (float *)mirror + (i >> 1) * (ADJ ? 8 : 4) + (i & 1);
+      m[0] = m[2] = -3.0e19f;
+      if (ADJ) m[4] = m[6] = 0.f;
+    } else {
+      double *m = (double *)mirror + i * (ADJ ? 4 : 2);
+      m[0] = m[1] = 1.0e150;
+      if (ADJ) m[2] = m[3] = 0.0;
+    }
+  }
+}
+
+// ============================================================ policies =====
+//
+// A policy gives the skeleton: R, TJ, the record size JB, the number NACC of
+// FP64 per-particle sums, whether the diagonal must be masked, the i-side state,
+// its loader, the tile body and the epilogue.
+
+// ---------------------------------------------------------- forward Ring FP32
+template <int R_, int TJ_, int MODE>
+struct RingMixed {
+  static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_RING, true, false>::value;
+  static constexpr bool MASK = true;
+  struct State {
+    float2 s[R], c[R], a[R], g[R], acc[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + (int64_t)r * NT;
+      const float *m = (const float *)mirror + (i >> 1) * 8 + (i & 1);
+      st.s[r] = f2(-m[0]);
+      st.c[r] = f2(m[2]);
+      st.a[r] = f2(-m[4]);
+      st.g[r] = f2(m[6]);
+      st.acc[r] = f2(0.f);
+      st.accd[r][0] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 he = f2((float)a.epsd);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 A = sm[2 * k], B = sm[2 * k + 1];
+      const float2 nsj = make_float2(A.x, A.y), cj = make_float2(A.z, A.w);
+      const float2 naj = make_float2(B.x, B.y), gj = make_float2(B.z, B.w);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        float2 S = __ffma2_rn(st.s[r], cj, __fmul2_rn(st.c[r], nsj));   // sin(theta_i - theta_j)
+        float2 sh = __ffma2_rn(st.a[r], gj, __fmul2_rn(st.g[r], naj));  // sin((theta_i - theta_j)/2)
+        float2 d = __ffma2_rn(sh, sh, he);                               // (1 - cos + eps)/2
+        float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+        float2 y2 = __fmul2_rn(y, y);
+        float2 qq = __fmul2_rn(S, y);
+        if (DIAG) {
+          const int64_t i = i0 + (int64_t)r * NT, j = j0 + 2 * k;
+          if (i == j) qq.x = 0.f;
+          if (i == j + 1) qq.y = 0.f;
+        }
+        st.acc[r] = __ffma2_rn(qq, y2, st.acc[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.accd[r][0] += (double)st.acc[r].x + (double)st.acc[r].y;
+      st.acc[r] = f2(0.f);
+    }
+  }
+};
+
+// ------------------------------------------------------------ forward 2D FP32
+template <int R_, int TJ_, int MODE>
+struct GravMixed {
+  static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
+  static constexpr bool MASK = false;
+  struct State {
+    float2 x[R], y[R], fx[R], fy[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + (int64_t)r * NT;
+      const float *m = (const float *)mirror + (i >> 1) * 4 + (i & 1);
+      st.x[r] = f2(-m[0]);
+      st.y[r] = f2(-m[2]);
+      st.fx[r] = st.fy[r] = f2(0.f);
+      st.accd[r][0] = st.accd[r][1] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 X = sm[k];
+      const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        float2 dx = __fadd2_rn(st.x[r], nx);
+        float2 dy = __fadd2_rn(st.y[r], ny);
+        float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+        float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+        st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
+        st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.accd[r][0] += (double)st.fx[r].x + (double)st.fx[r].y;
+      st.accd[r][1] += (double)st.fy[r].x + (double)st.fy[r].y;
+      st.fx[r] = st.fy[r] = f2(0.f);
+    }
+  }
+};
+
+// ------------------------------------------------------------ forward Ring FP64
+template <int R_, int TJ_, int MODE>
+struct RingF64 {
+  static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_RING, false, false>::value;
+  static constexpr bool MASK = true;
+  struct State {
+    double s[R], c[R], a[R], g[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 4;
+      st.s[r] = m[0];
+      st.c[r] = m[1];
+      st.a[r] = m[2];
+      st.g[r] = m[3];
+      st.accd[r][0] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const double2 *sm = (const double2 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double2 sc = sm[2 * k], ag = sm[2 * k + 1];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        double S = fma(st.s[r], sc.y, -(st.c[r] * sc.x));
+        double sh = fma(st.a[r], ag.y, -(st.g[r] * ag.x));
+        double y = rsqrt_nr(fma(sh, sh, a.epsd));
+        double qq = S * y;
+        if (DIAG && i0 + (int64_t)r * NT == j0 + k) qq = 0.0;
+        st.accd[r][0] = fma(qq, y * y, st.accd[r][0]);
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------ forward 2D FP64
+template <int R_, int TJ_, int MODE>
+struct GravF64 {
+  static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, false, false>::value;
+  static constexpr bool MASK = false;
+  struct State {
+    double x[R], y[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 2;
+      st.x[r] = m[0];
+      st.y[r] = m[1];
+      st.accd[r][0] = st.accd[r][1] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double2 *sm = (const double2 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double2 xy = sm[k];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        double dx = st.x[r] - xy.x, dy = st.y[r] - xy.y;
+        double inv = rcp_nr(fma(dx, dx, fma(dy, dy, a.epsd)));
+        st.accd[r][0] = fma(dx, inv, st.accd[r][0]);
+        st.accd[r][1] = fma(dy, inv, st.accd[r][1]);
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------ adjoint Ring FP32
+// accumulators: 0 = sum S dd^-3/2 (force), 1 = sum G w (J v), 2 = sum S dd^-5/2 (d/deps)
+template <int R_, int TJ_, int MODE>
+struct RingMixedAdj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_RING, true, true>::value;
+  static constexpr bool MASK = true;
+  struct State {
+    float2 s[R], c[R], a[R], g[R], ns[R], v[R], af[R], aj[R], ae[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + (int64_t)r * NT;
+      const float *m = (const float *)mirror + (i >> 1) * 12 + (i & 1);
+      st.s[r] = f2(-m[0]);
+      st.ns[r] = f2(m[0]);
+      st.c[r] = f2(m[2]);
+      st.a[r] = f2(-m[4]);
+      st.g[r] = f2(m[6]);
+      st.v[r] = f2(-m[8]);
+      st.af[r] = st.aj[r] = st.ae[r] = f2(0.f);
+      st.accd[r][0] = st.accd[r][1] = st.accd[r][2] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 he = f2((float)a.epsd), m34 = f2(-0.75f);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 A = sm[3 * k], B = sm[3 * k + 1], L = sm[3 * k + 2];
+      const float2 nsj = make_float2(A.x, A.y), cj = make_float2(A.z, A.w);
+      const float2 naj = make_float2(B.x, B.y), gj = make_float2(B.z, B.w);
+      const float2 nvj = make_float2(L.x, L.y);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        float2 S = __ffma2_rn(st.s[r], cj, __fmul2_rn(st.c[r], nsj));
+        float2 C = __ffma2_rn(st.c[r], cj, __fmul2_rn(st.ns[r], nsj));  // cos(theta_i - theta_j)
+        float2 sh = __ffma2_rn(st.a[r], gj, __fmul2_rn(st.g[r], naj));
+        float2 d = __ffma2_rn(sh, sh, he);
+        float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+        float2 y2 = __fmul2_rn(y, y);
+        float2 r3 = __fmul2_rn(y2, y);
+        float2 r5 = __fmul2_rn(r3, y2);
+        if (DIAG) {
+          const int64_t i = i0 + (int64_t)r * NT, j = j0 + 2 * k;
+          if (i == j) S.x = 0.f;
+          if (i == j + 1) S.y = 0.f;
+        }
+        st.af[r] = __ffma2_rn(S, r3, st.af[r]);
+        st.ae[r] = __ffma2_rn(S, r5, st.ae[r]);
+        float2 G = __ffma2_rn(__fmul2_rn(__fmul2_rn(S, S), m34), r5, __fmul2_rn(C, r3));
+        st.aj[r] = __ffma2_rn(G, __fadd2_rn(st.v[r], nvj), st.aj[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.accd[r][0] += (double)st.af[r].x + (double)st.af[r].y;
+      st.accd[r][1] += (double)st.aj[r].x + (double)st.aj[r].y;
+      st.accd[r][2] += (double)st.ae[r].x + (double)st.ae[r].y;
+      st.af[r] = st.aj[r] = st.ae[r] = f2(0.f);
+    }
+  }
+};
+
+// ------------------------------------------------------------ adjoint 2D FP32
+// accumulators: 0,1 = force (x,y); 2,3 = J v (x,y) without the -2/N factor; 4,5 = d/deps
+template <int R_, int TJ_, int MODE>
+struct GravMixedAdj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 6, JB = RecordBytes<MD_GRAV2D, true, true>::value;
+  static constexpr bool MASK = false;
+  struct State {
+    float2 x[R], y[R], vx[R], vy[R], fx[R], fy[R], jx[R], jy[R], ex[R], ey[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + (int64_t)r * NT;
+      const float *m = (const float *)mirror + (i >> 1) * 8 + (i & 1);
+      st.x[r] = f2(-m[0]);
+      st.y[r] = f2(-m[2]);
+      st.vx[r] = f2(-m[4]);
+      st.vy[r] = f2(-m[6]);
+      st.fx[r] = st.fy[r] = st.jx[r] = st.jy[r] = st.ex[r] = st.ey[r] = f2(0.f);
+#pragma unroll
+      for (int d = 0; d < NACC; d++) st.accd[r][d] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd), m2 = f2(-2.f);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 X = sm[2 * k], V = sm[2 * k + 1];
+      const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
+      const float2 nvx = make_float2(V.x, V.y), nvy = make_float2(V.z, V.w);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        float2 dx = __fadd2_rn(st.x[r], nx);
+        float2 dy = __fadd2_rn(st.y[r], ny);
+        float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+        float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+        float2 inv2 = __fmul2_rn(inv, inv);
+        float2 wx = __fadd2_rn(st.vx[r], nvx), wy = __fadd2_rn(st.vy[r], nvy);
+        float2 m2u = __fmul2_rn(__fmul2_rn(__ffma2_rn(dy, wy, __fmul2_rn(dx, wx)), inv2), m2);
+        st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
+        st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+        st.jx[r] = __ffma2_rn(m2u, dx, __ffma2_rn(wx, inv, st.jx[r]));
+        st.jy[r] = __ffma2_rn(m2u, dy, __ffma2_rn(wy, inv, st.jy[r]));
+        st.ex[r] = __ffma2_rn(dx, inv2, st.ex[r]);
+        st.ey[r] = __ffma2_rn(dy, inv2, st.ey[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.accd[r][0] += (double)st.fx[r].x + (double)st.fx[r].y;
+      st.accd[r][1] += (double)st.fy[r].x + (double)st.fy[r].y;
+      st.accd[r][2] += (double)st.jx[r].x + (double)st.jx[r].y;
+      st.accd[r][3] += (double)st.jy[r].x + (double)st.jy[r].y;
+      st.accd[r][4] += (double)st.ex[r].x + (double)st.ex[r].y;
+      st.accd[r][5] += (double)st.ey[r].x + (double)st.ey[r].y;
+      st.fx[r] = st.fy[r] = st.jx[r] = st.jy[r] = st.ex[r] = st.ey[r] = f2(0.f);
+    }
+  }
+};
+
+// ------------------------------------------------------------ adjoint Ring FP64
+template <int R_, int TJ_, int MODE>
+struct RingF64Adj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_RING, false, true>::value;
+  static constexpr bool MASK = true;
+  struct State {
+    double s[R], c[R], a[R], g[R], v[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 6;
+      st.s[r] = m[0];
+      st.c[r] = m[1];
+      st.a[r] = m[2];
+      st.g[r] = m[3];
+      st.v[r] = m[4];
+      st.accd[r][0] = st.accd[r][1] = st.accd[r][2] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const double2 *sm = (const double2 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double2 sc = sm[3 * k], ag = sm[3 * k + 1], vv = sm[3 * k + 2];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        double S = fma(st.s[r], sc.y, -(st.c[r] * sc.x));
+        double C = fma(st.c[r], sc.y, st.s[r] * sc.x);
+        double sh = fma(st.a[r], ag.y, -(st.g[r] * ag.x));
+        double y = rsqrt_nr(fma(sh, sh, a.epsd));
+        double y2 = y * y, r3 = y2 * y, r5 = r3 * y2;
+        if (DIAG && i0 + (int64_t)r * NT == j0 + k) S = 0.0;
+        st.accd[r][0] = fma(S, r3, st.accd[r][0]);
+        st.accd[r][2] = fma(S, r5, st.accd[r][2]);
+        double G = fma(-0.75 * S * S, r5, C * r3);
+        st.accd[r][1] = fma(G, st.v[r] - vv.x, st.accd[r][1]);
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------ adjoint 2D FP64
+template <int R_, int TJ_, int MODE>
+struct GravF64Adj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 6, JB = RecordBytes<MD_GRAV2D, false, true>::value;
+  static constexpr bool MASK = false;
+  struct State {
+    double x[R], y[R], vx[R], vy[R];
+    double accd[R][NACC];
+  };
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 4;
+      st.x[r] = m[0];
+      st.y[r] = m[1];
+      st.vx[r] = m[2];
+      st.vy[r] = m[3];
+#pragma unroll
+      for (int d = 0; d < NACC; d++) st.accd[r][d] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double2 *sm = (const double2 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double2 xy = sm[2 * k], vv = sm[2 * k + 1];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        double dx = st.x[r] - xy.x, dy = st.y[r] - xy.y;
+        double inv = rcp_nr(fma(dx, dx, fma(dy, dy, a.epsd)));
+        double inv2 = inv * inv;
+        double wx = st.vx[r] - vv.x, wy = st.vy[r] - vv.y;
+        double m2u = -2.0 * fma(dy, wy, dx * wx) * inv2;
+        st.accd[r][0] = fma(dx, inv, st.accd[r][0]);
+        st.accd[r][1] = fma(dy, inv, st.accd[r][1]);
+        st.accd[r][2] = fma(m2u, dx, fma(wx, inv, st.accd[r][2]));
+        st.accd[r][3] = fma(m2u, dy, fma(wy, inv, st.accd[r][3]));
+        st.accd[r][4] = fma(dx, inv2, st.accd[r][4]);
+        st.accd[r][5] = fma(dy, inv2, st.accd[r][5]);
+      }
+    }
+  }
+};
+
+// ============================================================ epilogues ====
+
+// Forward stages: kick, drift, new mirror record (or the force alone).
+template <int MODEL, bool MIXED, int MODE>
+__device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, const double *acc) {
+  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  if (i >= a.N) return;
+  const double scale = MODEL == MD_RING ? -1.0 / (8.0 * (double)a.N) : -2.0 / (double)a.N;
+  double f[D], x[D];
+#pragma unroll
+  for (int d = 0; d < D; d++) f[d] = scale * acc[d];
+  if (MODE == STAGE_FORCE_ONLY) {
+#pragma unroll
+    for (int d = 0; d < D; d++) a.fout[d * a.N + i] = f[d];
+    return;
+  }
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    const double pp = fma(a.kick, f[d], a.p[d * a.N + i]);
+    a.p[d * a.N + i] = pp;
+    if (MODE == STAGE_KICK_DRIFT) {
+      x[d] = fma(a.drift, pp, a.q[d * a.N + i]);
+      a.q[d * a.N + i] = x[d];
+    } else {
+      a.fout[d * a.N + i] = f[d];
+    }
+  }
+  if (MODE == STAGE_KICK_DRIFT) write_record<MODEL, MIXED, false>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+}
+
+// Reverse stages of md_grad, at the position q_s of one kick (b_adj = a.kick,
+// b_undo = a.undo) and the drift that preceded it (a.drift):
+//   lambda_q += b_adj J(q_s) lambda_p ;  epsacc += b_adj <lambda_p, df/deps(q_s)>
+//   p -= b_undo f(q_s)                          (undo the kick)
+//   lambda_p += d lambda_q ;  q -= d p          (adjoint and undo of the drift)
+template <int MODEL, bool MIXED>
+__device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, const double *acc) {
+  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  if (i >= a.N) return;
+  const double n = (double)a.N;
+  double f[D], jv[D], de[D];
+  if (MODEL == MD_RING) {
+    f[0] = -acc[0] / (8.0 * n);
+    jv[0] = -acc[1] / (8.0 * n);
+    de[0] = 3.0 * acc[2] / (32.0 * n);
+  } else {
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+      f[d] = -2.0 * acc[d] / n;
+      jv[d] = -2.0 * acc[2 + d] / n;
+      de[d] = 2.0 * acc[4 + d] / n;
+    }
+  }
+  double lq[D], lp[D], x[D], e = 0.0;
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    lp[d] = a.lp[d * a.N + i];
+    lq[d] = fma(a.kick, jv[d], a.lq[d * a.N + i]);
+    e = fma(lp[d], de[d], e);
+    double pp = fma(-a.undo, f[d], a.p[d * a.N + i]);
+    a.p[d * a.N + i] = pp;
+    x[d] = a.q[d * a.N + i];
+    if (a.drift != 0.0) {
+      lp[d] = fma(a.drift, lq[d], lp[d]);
+      x[d] = fma(-a.drift, pp, x[d]);
+      a.lp[d * a.N + i] = lp[d];
+      a.q[d * a.N + i] = x[d];
+    }
+    a.lq[d * a.N + i] = lq[d];
+  }
+  a.epsacc[i] = fma(a.kick, e, a.epsacc[i]);
+  if (a.drift != 0.0) write_record<MODEL, MIXED, true>(a.mirror_out, i, x[0], x[D - 1], lp[0], lp[D - 1]);
+}
+
+template <class Pol, int MODEL, bool MIXED, int MODE>
+__device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const double *acc) {
+  if constexpr (MODE == STAGE_ADJOINT)
+    finish_adjoint<MODEL, MIXED>(a, i, acc);
+  else
+    finish_forward<MODEL, MIXED, MODE>(a, i, acc);
+}
+
+}  // namespace

@@ -209,6 +209,15 @@ class Ensemble:
     def step(self, nsteps: int = 1) -> None:
         self._chk(B.load().md_batch_step(self._h, int(nsteps)))
 
+    def set_tuning(self, r: int, split: float, ctas_per_sm: int = 0) -> None:
+        self._chk(B.load().md_batch_set_tuning(self._h, int(r), float(split), int(ctas_per_sm)))
+
+    def autotune(self) -> float:
+        """Pick the fastest kernel shape; returns its force-launch time in ms."""
+        ms = ctypes.c_double()
+        self._chk(B.load().md_batch_autotune(self._h, ctypes.byref(ms)))
+        return ms.value
+
     def energy(self):
         k, v = np.empty(self.nsys), np.empty(self.nsys)
         self._chk(B.load().md_batch_energy(self._h, _ptr(k), _ptr(v)))

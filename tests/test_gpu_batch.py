@@ -1,0 +1,73 @@
+"""Batched ensembles (md_batch_*): every system of an uneven ensemble, advanced in
+shared persistent launches and replayed CUDA graphs, must match the same system
+advanced alone by md_step (same kernels and precision; only the stream-K split of
+the FP64 per-particle sums differs, so agreement is to rounding)."""
+import numpy as np
+import pytest
+
+from paper_1212_0262_gb300 import Ensemble, System, inputs
+
+pytestmark = pytest.mark.gpu
+
+MODELS = [1, 2, 1, 2, 2, 1]
+NS = [333, 1000, 2500, 4097, 777, 1500]
+EPS = [0.01, 1e-3, 0.01, 1e-4, 1e-3, 0.05]
+DTS = [0.05, 0.01, 0.05, 0.01, 0.01, 0.02]
+SEEDS = [1000 + s for s in range(6)]
+
+
+def _alone(s, nsteps, prec):
+    with System(MODELS[s], NS[s], EPS[s], DTS[s], SEEDS[s], precision=prec) as sy:
+        sy.step(nsteps)
+        return sy.get_state(), sy.energy()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("nsteps", [1, 25])
+def test_ensemble_matches_individual_runs(prec, nsteps):
+    ens = Ensemble(MODELS, NS, EPS, DTS, SEEDS, precision=prec)
+    ens.step(nsteps)
+    K, V = ens.energy()
+    for s in range(len(NS)):
+        (q, p), (k, v) = _alone(s, nsteps, prec)
+        qb, pb = ens.get_state(s)
+        tol = 1e-12 if prec == "fp64" else 1e-9
+        assert np.max(np.abs(qb - q)) <= tol * max(1.0, np.abs(q).max()), s
+        assert np.max(np.abs(pb - p)) <= tol * max(1.0, np.abs(p).max()), s
+        assert abs(K[s] - k) <= 1e-9 * abs(k) and abs(V[s] - v) <= 1e-9 * max(abs(v), 1.0)
+    ens.close()
+
+
+def test_autotune_leaves_states_unchanged_and_shapes_agree():
+    ens = Ensemble(MODELS, NS, EPS, DTS, SEEDS)
+    before = [ens.get_state(s) for s in range(len(NS))]
+    best = ens.autotune()
+    assert best > 0.0
+    for s in range(len(NS)):
+        q, p = ens.get_state(s)
+        assert np.array_equal(q, before[s][0]) and np.array_equal(p, before[s][1])
+    ens.step(12)
+    ref = [ens.get_state(s) for s in range(len(NS))]
+    for r, split, cps in ((4, 0.3, 0), (8, 0.7, 2)):
+        e2 = Ensemble(MODELS, NS, EPS, DTS, SEEDS)
+        e2.set_tuning(r, split, cps)
+        e2.step(12)
+        for s in range(len(NS)):
+            q, p = e2.get_state(s)
+            assert np.max(np.abs(q - ref[s][0])) <= 1e-9 * max(1.0, np.abs(q).max())
+        e2.close()
+    ens.close()
+
+
+def test_set_state_is_used_by_the_next_step():
+    ens = Ensemble(MODELS[:2], NS[:2], EPS[:2], DTS[:2], SEEDS[:2])
+    q, p = inputs.default_state(MODELS[1], NS[1], 5)
+    ens.set_state(1, q, p)
+    ens.step(3)
+    with System(MODELS[1], NS[1], EPS[1], DTS[1], 0, precision="mixed") as sy:
+        sy.set_state(q, p)
+        sy.step(3)
+        qa, pa = sy.get_state()
+    qb, pb = ens.get_state(1)
+    assert np.max(np.abs(qb - qa)) <= 1e-9 * max(1.0, np.abs(qa).max())
+    ens.close()
