@@ -217,6 +217,7 @@ struct md_batch {
   int64_t layout_ti = -1, layout_tj = -1;
   int64_t Ur = 0, Ug = 0, rows_r = 0, rows_g = 0;
   int nr = 0;
+  std::vector<std::pair<const void *, int>> occ_cache;  // occupancy per kernel, queried outside captures
   int64_t launches = 0;
   std::string err;
 };
@@ -303,9 +304,14 @@ int launch_batch(md_batch *b, double bc, double dc) {
   const int64_t Ur = b->Ur, Ug = b->Ug, rows_r = b->rows_r, rows_g = b->rows_g;
   const int nr = b->nr;
   auto kern = batch_kernel<PolR, PolG, MIXED, MODE>;
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
-  if (occ < 1) occ = 1;
+  int occ = 0;
+  for (const auto &kv : b->occ_cache)
+    if (kv.first == (const void *)kern) occ = kv.second;
+  if (occ == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+    if (occ < 1) occ = 1;
+    b->occ_cache.push_back({(const void *)kern, occ});
+  }
   if (b->cfg.ctas_per_sm > 0 && b->cfg.ctas_per_sm < occ) occ = b->cfg.ctas_per_sm;
   const int64_t P = (int64_t)b->nsm * occ;
   int64_t Pr = 0, Pg = 0;
