@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
+    ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
     dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "ensemble": (20, 3)}[a.workload]
     if a.steps is None:
@@ -262,6 +263,9 @@ def run_ours(args, w):
     model, N, K, W = w["model"], w["N"], args.steps, args.warmup
     sysm = System(model, N, w["eps"], w["dt"], w["seed"] + 1000 * rank, precision=args.prec)
     sysm.set_stream(stream)
+    for kv in args.tune:
+        k, v = kv.split("=")
+        sysm.set_tuning(k, int(v))
     e0 = sum(sysm.energy())
 
     sched = stage_schedule(K)
@@ -342,8 +346,8 @@ def run_ours(args, w):
         units_per_step = 3 * N * N
         value = ws * 3 * N * N * K / (elapsed_ms * 1e-3)
         avg_ms = sum(stage_ms) / len(stage_ms)
-        rates = np.zeros(17)
-        binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 17)
+        rates = np.zeros(19)
+        binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 19)
         nsm = rates[0]
         fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
         sfu_rate = rates[5] if model == 1 else rates[7]
@@ -423,7 +427,7 @@ def run_ours(args, w):
             "dtype": "f64 state / f32 " + ("sin,cos" if model == 0 else "pair arithmetic") if args.prec == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": w["name"], "N": N, "eps": w["eps"], "dt": w["dt"], "seed": w["seed"],
-                       "precision": args.prec, "parallelism": f"replicas x{ws}",
+                       "precision": args.prec, "parallelism": f"replicas x{ws}", "tuning": args.tune,
                        "l2": "state 800 MB > L2 (no flush needed)" if model == 0 else "L2 flushed (256 MB write) between timed steps"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_energy_error": de_mixed,
@@ -496,8 +500,8 @@ def run_ensemble(args, w):
     value = ws * 3 * pairs_per_stage * K / (ms * 1e-3)
     nl = 3 * K + 1
     avg_ms = ms / nl
-    rates = np.zeros(17)
-    binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(_c.POINTER(_c.c_double)), 17)
+    rates = np.zeros(19)
+    binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(_c.POINTER(_c.c_double)), 19)
     nsm = rates[0]
     fp32 = max(rates[1], rates[3])
     per_clk_ring = min(fp32 / PAIR_OPS[1][0], rates[5] / PAIR_OPS[1][1])

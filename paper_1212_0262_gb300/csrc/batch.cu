@@ -126,14 +126,21 @@ __device__ __noinline__ void batch_part(const PartArgs &A, int64_t cta) {
       const int64_t row = A.sys[s].rbeg + it;
       if (row_end && row_from_start) {
 #pragma unroll
-        for (int r = 0; r < R; r++) finish<Pol, MODEL, MIXED, MODE>(v, i0 + (int64_t)r * NT, st.accd[r]);
+        for (int r = 0; r < R; r++) {
+          double ex[NACC];
+          Pol::total(st, r, ex);
+          finish<Pol, MODEL, MIXED, MODE>(v, i0 + (int64_t)r * NT, ex);
+        }
       } else {
         const int slot = (row == first_row) ? 0 : 1;
         double *sp = A.slots + ((cta * 2 + slot) * NACC) * TI;
 #pragma unroll
-        for (int r = 0; r < R; r++)
+        for (int r = 0; r < R; r++) {
+          double ex[NACC];
+          Pol::total(st, r, ex);
 #pragma unroll
-          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = st.accd[r][d];
+          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = ex[d];
+        }
         __threadfence();
         __syncthreads();
         const int64_t ub = A.sys[s].ubeg + it * A.sys[s].n_jt;

@@ -20,6 +20,7 @@ struct PairTuning {
   int r_mixed = 8;    // i-particles per thread, FP32 pair path
   int r_fp64 = 2;     // i-particles per thread, FP64 pair path
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
+  int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
   int ctas_per_sm = 0;  // 0: occupancy-derived
 };
 

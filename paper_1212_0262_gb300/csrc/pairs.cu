@@ -90,15 +90,22 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
       if (row_end && row_from_start) {
         // this CTA covered the whole i-tile: finish it directly
 #pragma unroll
-        for (int r = 0; r < R; r++) finish<Pol, MODEL, MIXED, MODE>(a, i0 + (int64_t)r * NT, st.accd[r]);
+        for (int r = 0; r < R; r++) {
+          double ex[NACC];
+          Pol::total(st, r, ex);
+          finish<Pol, MODEL, MIXED, MODE>(a, i0 + (int64_t)r * NT, ex);
+        }
       } else {
         // partial coverage: publish, and let the last contributor finish
         const int slot = (it == first_row) ? 0 : 1;
         double *sp = a.slots + ((cta * 2 + slot) * NACC) * TI;
 #pragma unroll
-        for (int r = 0; r < R; r++)
+        for (int r = 0; r < R; r++) {
+          double ex[NACC];
+          Pol::total(st, r, ex);
 #pragma unroll
-          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = st.accd[r][d];
+          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = ex[d];
+        }
         __threadfence();
         __syncthreads();
         const int64_t cf = cta_of_unit(a.U, a.P, it * a.n_jt);
@@ -264,6 +271,7 @@ int dispatch_forward(md_ctx *c, PairArgs a) {
       else return launch_streamk<GravMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
     }
     if constexpr (MODEL == MD_RING) return launch_streamk<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
     else return launch_streamk<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
   } else {
     if (c->pt.r_fp64 == 4) {

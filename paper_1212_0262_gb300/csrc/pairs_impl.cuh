@@ -52,6 +52,25 @@ __device__ __forceinline__ int64_t cta_of_unit(int64_t U, int P, int64_t u) { re
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// Compensated FP32 running sum (Knuth's TwoSum: hi + lo carries the exact sum of
+// the added floats up to the rounding of lo).  Used for the per-particle sums of
+// the FP32 pair kernels across j-tiles, so the FP64 pipe stays out of the main
+// loop; the total is read out once, as the double hi + lo.
+struct CompSum {
+  float hi, lo;
+};
+__device__ __forceinline__ void csum_add(CompSum &c, float x) {
+  const float s = c.hi + x;
+  const float bp = s - c.hi;
+  c.lo += (c.hi - (s - bp)) + (x - bp);
+  c.hi = s;
+}
+__device__ __forceinline__ void csum_add2(CompSum &c, float2 x) {
+  csum_add(c, x.x);
+  csum_add(c, x.y);
+}
+__device__ __forceinline__ double csum_total(const CompSum &c) { return (double)c.hi + (double)c.lo; }
+
 // ============================================================ records ======
 
 // Mirror record of particle i at FP64 position(s) (x, y) and, for adjoint
@@ -150,8 +169,12 @@ struct RingMixed {
   static constexpr bool MASK = true;
   struct State {
     float2 s[R], c[R], a[R], g[R], acc[R];
-    double accd[R][NACC];
+    CompSum cs[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -162,7 +185,7 @@ struct RingMixed {
       st.a[r] = f2(-m[4]);
       st.g[r] = f2(m[6]);
       st.acc[r] = f2(0.f);
-      st.accd[r][0] = 0.0;
+      st.cs[r][0] = CompSum{0.f, 0.f};
     }
   }
   template <bool DIAG>
@@ -192,21 +215,47 @@ struct RingMixed {
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      st.accd[r][0] += (double)st.acc[r].x + (double)st.acc[r].y;
+      csum_add2(st.cs[r][0], st.acc[r]);
       st.acc[r] = f2(0.f);
     }
   }
 };
 
+// 1/s for two floats on the FMA pipe instead of the SFU: a bit-pattern seed
+// (0x7EF311C0 - bits(s), whose worst relative error over a binade is 5.1%,
+// found by direct search) and two cubic steps y <- y (1 + e + e^2), e = 1 - s y
+// (written with e' = s y - 1), each cubing the relative error: 5e-2 -> 1.3e-4
+// -> 1.1e-7.  Valid for normal positive s; +inf gives 0 like the SFU.
+__device__ __forceinline__ float2 rcp2_fma(float2 s) {
+  float2 y = make_float2(__uint_as_float(0x7EF311C0u - __float_as_uint(s.x)),
+                         __uint_as_float(0x7EF311C0u - __float_as_uint(s.y)));
+  const float2 m1 = f2(-1.f);
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const float2 e = __ffma2_rn(s, y, m1);
+    y = __ffma2_rn(y, __ffma2_rn(e, e, make_float2(-e.x, -e.y)), y);
+  }
+  if (isinf(s.x)) y.x = 0.f;  // padding records: 1/inf = 0 (the steps above give NaN there)
+  if (isinf(s.y)) y.y = 0.f;
+  return y;
+}
+
 // ------------------------------------------------------------ forward 2D FP32
-template <int R_, int TJ_, int MODE>
+// OFF > 0: every OFF-th pair of j's takes its reciprocals from rcp2_fma, which
+// moves work from the SFU (the binding pipe of this kernel) to the FMA pipe.
+template <int R_, int TJ_, int MODE, int OFF = 0>
 struct GravMixed {
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
   static constexpr bool MASK = false;
+  static_assert(OFF == 0 || (TJ / 2) % OFF == 0, "offload period must divide the tile");
   struct State {
     float2 x[R], y[R], fx[R], fy[R];
-    double accd[R][NACC];
+    CompSum cs[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -215,15 +264,14 @@ struct GravMixed {
       st.x[r] = f2(-m[0]);
       st.y[r] = f2(-m[2]);
       st.fx[r] = st.fy[r] = f2(0.f);
-      st.accd[r][0] = st.accd[r][1] = 0.0;
+      for (int d = 0; d < NACC; d++) st.cs[r][d] = CompSum{0.f, 0.f};
     }
   }
   template <bool DIAG>
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
-#pragma unroll 2
-    for (int k = 0; k < TJ / 2; k++) {
+    auto body = [&](int k, bool fma_rcp) {
       const float4 X = sm[k];
       const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
 #pragma unroll
@@ -231,15 +279,24 @@ struct GravMixed {
         float2 dx = __fadd2_rn(st.x[r], nx);
         float2 dy = __fadd2_rn(st.y[r], ny);
         float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
-        float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+        float2 inv = fma_rcp ? rcp2_fma(s) : make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
         st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
         st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+      }
+    };
+    if constexpr (OFF == 0) {
+#pragma unroll 2
+      for (int k = 0; k < TJ / 2; k++) body(k, false);
+    } else {
+      for (int k0 = 0; k0 < TJ / 2; k0 += OFF) {
+#pragma unroll
+        for (int kk = 0; kk < OFF; kk++) body(k0 + kk, kk == OFF - 1);
       }
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      st.accd[r][0] += (double)st.fx[r].x + (double)st.fx[r].y;
-      st.accd[r][1] += (double)st.fy[r].x + (double)st.fy[r].y;
+      csum_add2(st.cs[r][0], st.fx[r]);
+      csum_add2(st.cs[r][1], st.fy[r]);
       st.fx[r] = st.fy[r] = f2(0.f);
     }
   }
@@ -254,6 +311,10 @@ struct RingF64 {
     double s[R], c[R], a[R], g[R];
     double accd[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -293,6 +354,10 @@ struct GravF64 {
     double x[R], y[R];
     double accd[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -327,8 +392,12 @@ struct RingMixedAdj {
   static constexpr bool MASK = true;
   struct State {
     float2 s[R], c[R], a[R], g[R], ns[R], v[R], af[R], aj[R], ae[R];
-    double accd[R][NACC];
+    CompSum cs[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -341,7 +410,7 @@ struct RingMixedAdj {
       st.g[r] = f2(m[6]);
       st.v[r] = f2(-m[8]);
       st.af[r] = st.aj[r] = st.ae[r] = f2(0.f);
-      st.accd[r][0] = st.accd[r][1] = st.accd[r][2] = 0.0;
+      for (int d = 0; d < NACC; d++) st.cs[r][d] = CompSum{0.f, 0.f};
     }
   }
   template <bool DIAG>
@@ -377,9 +446,9 @@ struct RingMixedAdj {
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      st.accd[r][0] += (double)st.af[r].x + (double)st.af[r].y;
-      st.accd[r][1] += (double)st.aj[r].x + (double)st.aj[r].y;
-      st.accd[r][2] += (double)st.ae[r].x + (double)st.ae[r].y;
+      csum_add2(st.cs[r][0], st.af[r]);
+      csum_add2(st.cs[r][1], st.aj[r]);
+      csum_add2(st.cs[r][2], st.ae[r]);
       st.af[r] = st.aj[r] = st.ae[r] = f2(0.f);
     }
   }
@@ -393,8 +462,12 @@ struct GravMixedAdj {
   static constexpr bool MASK = false;
   struct State {
     float2 x[R], y[R], vx[R], vy[R], fx[R], fy[R], jx[R], jy[R], ex[R], ey[R];
-    double accd[R][NACC];
+    CompSum cs[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -406,7 +479,7 @@ struct GravMixedAdj {
       st.vy[r] = f2(-m[6]);
       st.fx[r] = st.fy[r] = st.jx[r] = st.jy[r] = st.ex[r] = st.ey[r] = f2(0.f);
 #pragma unroll
-      for (int d = 0; d < NACC; d++) st.accd[r][d] = 0.0;
+      for (int d = 0; d < NACC; d++) st.cs[r][d] = CompSum{0.f, 0.f};
     }
   }
   template <bool DIAG>
@@ -437,12 +510,12 @@ struct GravMixedAdj {
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      st.accd[r][0] += (double)st.fx[r].x + (double)st.fx[r].y;
-      st.accd[r][1] += (double)st.fy[r].x + (double)st.fy[r].y;
-      st.accd[r][2] += (double)st.jx[r].x + (double)st.jx[r].y;
-      st.accd[r][3] += (double)st.jy[r].x + (double)st.jy[r].y;
-      st.accd[r][4] += (double)st.ex[r].x + (double)st.ex[r].y;
-      st.accd[r][5] += (double)st.ey[r].x + (double)st.ey[r].y;
+      csum_add2(st.cs[r][0], st.fx[r]);
+      csum_add2(st.cs[r][1], st.fy[r]);
+      csum_add2(st.cs[r][2], st.jx[r]);
+      csum_add2(st.cs[r][3], st.jy[r]);
+      csum_add2(st.cs[r][4], st.ex[r]);
+      csum_add2(st.cs[r][5], st.ey[r]);
       st.fx[r] = st.fy[r] = st.jx[r] = st.jy[r] = st.ex[r] = st.ey[r] = f2(0.f);
     }
   }
@@ -457,6 +530,10 @@ struct RingF64Adj {
     double s[R], c[R], a[R], g[R], v[R];
     double accd[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -501,6 +578,10 @@ struct GravF64Adj {
     double x[R], y[R], vx[R], vy[R];
     double accd[R][NACC];
   };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {

@@ -49,7 +49,9 @@ __device__ __forceinline__ float cvt_roundtrip(float x) {
   return r;
 }
 
-enum Op { OP_FFMA = 0, OP_FFMA2, OP_RSQ, OP_RCP, OP_SIN, OP_LG2EX2, OP_DFMA, OP_CVT, OP_COUNT };
+// OP_MIX: half the chains packed FFMA2, half scalar FFMA (does the second FMA
+// pipe add throughput next to packed instructions?)
+enum Op { OP_FFMA = 0, OP_FFMA2, OP_RSQ, OP_RCP, OP_SIN, OP_LG2EX2, OP_DFMA, OP_CVT, OP_MIX, OP_COUNT };
 
 template <int OP>
 __global__ void __launch_bounds__(NT) pipe_kernel(const float *in, float *out, long long *cycles, int iters) {
@@ -78,6 +80,10 @@ __global__ void __launch_bounds__(NT) pipe_kernel(const float *in, float *out, l
       if (OP == OP_LG2EX2) a[c] = sfu_ex2(sfu_lg2(a[c]));
       if (OP == OP_DFMA) d[c] = fma(d[c], xd, yd);
       if (OP == OP_CVT) a[c] = cvt_roundtrip(a[c]);
+      if (OP == OP_MIX) {
+        if (c < CH / 2) b[c] = __ffma2_rn(b[c], x2, y2);
+        else a[c] = fmaf(a[c], x, y);
+      }
     }
   }
   __syncthreads();
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(NT) pipe_kernel(const float *in, float *out, l
 }
 
 // SFU / FMA operations counted per chain-iteration (the rcp chain's add is not counted)
-const double kOpsPerIter[OP_COUNT] = {1, 2, 1, 1, 1, 2, 1, 2};
+const double kOpsPerIter[OP_COUNT] = {1, 2, 1, 1, 1, 2, 1, 2, 1.5};
 
 template <int OP>
 int run(int nsm, const float *din, float *dout, long long *dcyc, long long *hcyc, int iters, double *rate,
@@ -155,6 +161,7 @@ extern "C" int mdp_pipe_rates(double *out, int nout) {
     case OP_LG2EX2: rc = run<OP_LG2EX2>(nsm, din, dout, dcyc, hcyc, iters, &r, &mhz); break;
     case OP_DFMA: rc = run<OP_DFMA>(nsm, din, dout, dcyc, hcyc, iters, &r, &mhz); break;
     case OP_CVT: rc = run<OP_CVT>(nsm, din, dout, dcyc, hcyc, iters, &r, &mhz); break;
+    case OP_MIX: rc = run<OP_MIX>(nsm, din, dout, dcyc, hcyc, iters, &r, &mhz); break;
     }
     out[1 + 2 * op] = r;
     out[2 + 2 * op] = mhz;
