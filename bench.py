@@ -38,6 +38,9 @@ WORKLOADS = {
                  name="Ring N=131,072 eps=0.01 dt=0.05 (all-pairs)"),
     "grav2d": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
                    name="2D self-gravitating N=262,144 eps=1e-4 dt=0.01 (all-pairs)"),
+    "adjoint": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
+                    name="2D N=262,144 eps=1e-4 dt=0.01: gradient of K(T) after 100 steps (forward + "
+                         "reversed adjoint, checkpoints every 20 steps)"),
     "ensemble": dict(model=-1, N=0, eps=0.0, dt=0.0, seed=1000, unit="pair-interactions/s",
                      name="ensemble: 128 Ring (eps=0.01, dt=0.05) + 128 2D (eps=1e-4, dt=0.01), "
                           "N log-uniform in [4096, 65536], one persistent launch per stage"),
@@ -62,7 +65,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
-    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "ensemble": (20, 3)}[a.workload]
+    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "ensemble": (20, 3), "adjoint": (1, 0)}[a.workload]
     if a.steps is None:
         a.steps = dflt[0]
     if a.warmup is None:
@@ -531,10 +534,63 @@ def run_ensemble(args, w):
     ens.close()
 
 
+def run_adjoint(args, w):
+    """md_grad on the 2D configuration: `steps` gradient evaluations of K(T) after
+    100 integrator steps; pair interactions counted for both passes (3 N^2 per
+    forward step, N^2 per reverse stage, 3 nsteps + 1 reverse stages).  The
+    mixed gradient's error is stated against the FP64 gradient at N = 16,384."""
+    import numpy as np
+    import torch
+
+    from paper_1212_0262_gb300 import System
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    N, nsteps, K = w["N"], 100, 20
+    s = System(2, N, w["eps"], w["dt"], w["seed"], precision=args.prec)
+    s.set_stream(stream)
+    for _ in range(args.warmup):
+        s.grad(2, 0, 1)
+    sampler = ClockSampler(device_uuid(local))
+    l0 = s.launch_count
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        val, gq, gp, ge = s.grad(nsteps, 0, K)
+    el = (time.perf_counter() - t0) / args.steps
+    launches = s.launch_count - l0
+    clocks = sampler.stop()
+    pairs = float(N) * N * (3 * nsteps + 3 * nsteps + 1)
+    # mixed vs FP64 gradient on a smaller system of the same recipe
+    n2 = 16384
+    out = {}
+    for prec in ("fp64", "mixed"):
+        with System(2, n2, w["eps"], w["dt"], w["seed"], precision=prec) as s2:
+            out[prec] = s2.grad(nsteps, 0, K)
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    err = {"grad_q": rel(out["mixed"][1], out["fp64"][1]), "grad_p": rel(out["mixed"][2], out["fp64"][2]),
+           "grad_eps": abs(out["mixed"][3] - out["fp64"][3]) / abs(out["fp64"][3]), "N": n2}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": pairs / el, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 state / f32 pair arithmetic" if args.prec == "mixed" else "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "precision": args.prec, "N": N,
+                                            "nsteps": nsteps, "checkpoint_every": K},
+            "gradient_seconds": el, "value_K_T": val, "grad_eps": ge,
+            "mixed_vs_fp64_gradient_rel_error": err, "gpu_launches": launches, "clocks": clocks,
+            "roofline": None, "cpu_baseline": None, "e2e": None}), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
     if args.workload == "ensemble" and args.impl == "ours":
         run_ensemble(args, WORKLOADS["ensemble"])
+        return
+    if args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args, WORKLOADS["adjoint"])
         return
     w = dict(WORKLOADS[args.workload])
     if args.n:
