@@ -251,6 +251,7 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   else if (k == "pair_ctas_per_sm" && value >= 0 && value <= 32) c->pt.ctas_per_sm = (int)value;
   else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
   else if (k == "rcp_offload" && (value == 0 || value == 8)) c->pt.rcp_off = (int)value;
+  else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
   else return set_err(c, MD_EINVAL, "unknown tuning key or value: %s=%lld", key, (long long)value);
   return MD_OK;
 }

@@ -94,7 +94,7 @@ __device__ __noinline__ void batch_part(const PartArgs &A, int64_t cta) {
 
   typename Pol::State st;
   PairArgs v = view(A, A.sys[s]);
-  int64_t i0 = it * TI + threadIdx.x;
+  int64_t i0 = it * TI;  // tile base; each thread's rows come from Pol::row_of
   Pol::load(st, v.mirror_in, i0);
   prefetch(0, s, jt);
 
@@ -126,20 +126,23 @@ __device__ __noinline__ void batch_part(const PartArgs &A, int64_t cta) {
       const int64_t row = A.sys[s].rbeg + it;
       if (row_end && row_from_start) {
 #pragma unroll
-        for (int r = 0; r < R; r++) {
+        for (int r = 0; r < Pol::NR; r++) {
           double ex[NACC];
           Pol::total(st, r, ex);
-          finish<Pol, MODEL, MIXED, MODE>(v, i0 + (int64_t)r * NT, ex);
+          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+          if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(v, i0 + lr, ex);
         }
       } else {
         const int slot = (row == first_row) ? 0 : 1;
         double *sp = A.slots + ((cta * 2 + slot) * NACC) * TI;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
+        for (int r = 0; r < Pol::NR; r++) {
           double ex[NACC];
           Pol::total(st, r, ex);
+          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+          if (lr >= 0)
 #pragma unroll
-          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = ex[d];
+            for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
         }
         __threadfence();
         __syncthreads();
@@ -153,21 +156,27 @@ __device__ __noinline__ void batch_part(const PartArgs &A, int64_t cta) {
         __syncthreads();
         if (s_last) {
           __threadfence();
-          double tot[R][NACC];
+          double tot[Pol::NR][NACC];
 #pragma unroll
-          for (int r = 0; r < R; r++)
+          for (int r = 0; r < Pol::NR; r++)
 #pragma unroll
             for (int d = 0; d < NACC; d++) tot[r][d] = 0.0;
           for (int64_t c2 = cf; c2 <= cl; c2++) {
             const int sl = (row == row_of_unit(A, unit_begin(A.U, A.P, c2))) ? 0 : 1;
             const double *src = A.slots + ((c2 * 2 + sl) * NACC) * TI;
 #pragma unroll
-            for (int r = 0; r < R; r++)
+            for (int r = 0; r < Pol::NR; r++) {
+              const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+              if (lr >= 0)
 #pragma unroll
-              for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + r * NT + threadIdx.x);
+                for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + lr);
+            }
           }
 #pragma unroll
-          for (int r = 0; r < R; r++) finish<Pol, MODEL, MIXED, MODE>(v, i0 + (int64_t)r * NT, tot[r]);
+          for (int r = 0; r < Pol::NR; r++) {
+            const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(v, i0 + lr, tot[r]);
+          }
           if (threadIdx.x == 0) A.tickets[row] = 0u;
         }
       }
@@ -180,7 +189,7 @@ __device__ __noinline__ void batch_part(const PartArgs &A, int64_t cta) {
           it = 0;
           v = view(A, A.sys[s]);
         }
-        i0 = it * TI + threadIdx.x;
+        i0 = it * TI;
         Pol::load(st, v.mirror_in, i0);
       }
     }
@@ -399,6 +408,7 @@ int refresh_mirrors(md_batch *b) {
   if (b->mirrors_valid) return MD_OK;
   for (md_ctx *c : b->ctx) {
     c->prec = b->prec;
+    c->pt.ring_tc = 0;  // the batched kernel reads the interleaved records
     c->mirror_cur = b->cur;
     int rc = mirror_refresh(c);
     if (rc) return berr(b, rc, "%s", c->err.c_str());

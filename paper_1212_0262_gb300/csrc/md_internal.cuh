@@ -21,6 +21,7 @@ struct PairTuning {
   int r_fp64 = 2;     // i-particles per thread, FP64 pair path
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
   int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
+  int ring_tc = 0;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
   int ctas_per_sm = 0;  // 0: occupancy-derived
 };
 
@@ -58,6 +59,7 @@ struct md_ctx {
   int mirror_cur = 0;
   bool mirror_valid = false;
   int mirror_prec = -1;
+  int mirror_fmt = -1;  // record format of the valid mirror (0 interleaved, 1 tensor-core fragments)
   double *sk_slots = nullptr;
   size_t sk_slots_bytes = 0;
   unsigned *sk_tickets = nullptr;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
   typename Pol::State st;
   int64_t it = u0 / a.n_jt, jt = u0 % a.n_jt;
   bool row_from_start = (jt == 0);
-  int64_t i0 = it * TI + threadIdx.x;
+  int64_t i0 = it * TI;  // tile base; each thread's rows come from Pol::row_of
   Pol::load(st, a.mirror_in, i0);
   prefetch(0, jt);
 
@@ -90,21 +90,24 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
       if (row_end && row_from_start) {
         // this CTA covered the whole i-tile: finish it directly
 #pragma unroll
-        for (int r = 0; r < R; r++) {
+        for (int r = 0; r < Pol::NR; r++) {
           double ex[NACC];
           Pol::total(st, r, ex);
-          finish<Pol, MODEL, MIXED, MODE>(a, i0 + (int64_t)r * NT, ex);
+          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+          if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(a, i0 + lr, ex);
         }
       } else {
         // partial coverage: publish, and let the last contributor finish
         const int slot = (it == first_row) ? 0 : 1;
         double *sp = a.slots + ((cta * 2 + slot) * NACC) * TI;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
+        for (int r = 0; r < Pol::NR; r++) {
           double ex[NACC];
           Pol::total(st, r, ex);
+          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+          if (lr >= 0)
 #pragma unroll
-          for (int d = 0; d < NACC; d++) sp[d * TI + r * NT + threadIdx.x] = ex[d];
+            for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
         }
         __threadfence();
         __syncthreads();
@@ -117,9 +120,9 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
         __syncthreads();
         if (s_last) {
           __threadfence();
-          double tot[R][NACC];
+          double tot[Pol::NR][NACC];
 #pragma unroll
-          for (int r = 0; r < R; r++)
+          for (int r = 0; r < Pol::NR; r++)
 #pragma unroll
             for (int d = 0; d < NACC; d++) tot[r][d] = 0.0;
           for (int64_t c2 = cf; c2 <= cl; c2++) {
@@ -127,12 +130,18 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
             const int sl = (it == fr) ? 0 : 1;
             const double *src = a.slots + ((c2 * 2 + sl) * NACC) * TI;
 #pragma unroll
-            for (int r = 0; r < R; r++)
+            for (int r = 0; r < Pol::NR; r++) {
+              const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+              if (lr >= 0)
 #pragma unroll
-              for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + r * NT + threadIdx.x);
+                for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + lr);
+            }
           }
 #pragma unroll
-          for (int r = 0; r < R; r++) finish<Pol, MODEL, MIXED, MODE>(a, i0 + (int64_t)r * NT, tot[r]);
+          for (int r = 0; r < Pol::NR; r++) {
+            const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(a, i0 + lr, tot[r]);
+          }
           if (threadIdx.x == 0) a.tickets[it] = 0u;
         }
       }
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
         it++;
         jt = 0;
         row_from_start = true;
-        i0 = it * TI + threadIdx.x;
+        i0 = it * TI;
         Pol::load(st, a.mirror_in, i0);
       }
     }
@@ -149,7 +158,7 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
 
 // Whole mirror from the FP64 state (and lambda_p for adjoint records), padding
 // records in both buffers.
-template <int MODEL, bool MIXED, bool ADJ>
+template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __global__ void mirror_kernel(const double *__restrict__ q, const double *__restrict__ lp, int64_t N, int64_t Npad,
                               void *m0, void *m1) {
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
@@ -157,16 +166,16 @@ __global__ void mirror_kernel(const double *__restrict__ q, const double *__rest
     if (i < N) {
       const double y = MODEL == MD_GRAV2D ? q[N + i] : 0.0;
       const double vx = ADJ ? lp[i] : 0.0, vy = (ADJ && MODEL == MD_GRAV2D) ? lp[N + i] : 0.0;
-      write_record<MODEL, MIXED, ADJ>(m0, i, q[i], y, vx, vy);
+      write_record_fmt<MODEL, MIXED, ADJ, FMT>(m0, i, q[i], y, vx, vy);
     } else {
-      write_pad<MODEL, MIXED, ADJ>(m0, i);
-      if (m1) write_pad<MODEL, MIXED, ADJ>(m1, i);
+      write_pad_fmt<MODEL, MIXED, ADJ, FMT>(m0, i);
+      if (m1) write_pad_fmt<MODEL, MIXED, ADJ, FMT>(m1, i);
     }
   }
 }
 
 // First stage from the cached force: p += kick f; q += drift p; new mirror.
-template <int MODEL, bool MIXED>
+template <int MODEL, bool MIXED, int FMT>
 __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restrict__ p,
                                          const double *__restrict__ f, int64_t N, double kick,
                                          double drift, void *mirror_out) {
@@ -181,11 +190,14 @@ __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restr
       x[d] = fma(drift, pp, q[d * N + i]);
       q[d * N + i] = x[d];
     }
-    write_record<MODEL, MIXED, false>(mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+    write_record_fmt<MODEL, MIXED, false, FMT>(mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
   }
 }
 
 // ------------------------------------------------------------ host side ---
+
+// The Ring FP32 forward path uses the tensor-core records and policy.
+bool ring_tc(const md_ctx *c) { return c->model == MD_RING && c->prec == MD_MIXED && c->pt.ring_tc; }
 
 int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadMultiple; }
 
@@ -217,7 +229,7 @@ int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc) {
 int ensure_mirrors(md_ctx *c, bool adj) {
   const int64_t Np = padded(c->N);
   // the FP64 record bounds the FP32 one
-  const size_t per = c->model == MD_RING ? (adj ? 48 : 32) : (adj ? 32 : 16);
+  const size_t per = c->model == MD_RING ? (adj ? 48 : 64) : (adj ? 32 : 16);  // Ring forward: tensor-core record
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
     for (int b = 0; b < 2; b++) {
@@ -270,8 +282,13 @@ int dispatch_forward(md_ctx *c, PairArgs a) {
       if constexpr (MODEL == MD_RING) return launch_streamk<RingMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
       else return launch_streamk<GravMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
     }
-    if constexpr (MODEL == MD_RING) return launch_streamk<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
-    else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
+    if constexpr (MODEL == MD_RING) {
+      if (ring_tc(c)) {
+        if (c->pt.ring_tc == 2) return launch_streamk<RingTC<2, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+        return launch_streamk<RingTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+      }
+      return launch_streamk<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    } else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
     else return launch_streamk<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
   } else {
     if (c->pt.r_fp64 == 4) {
@@ -302,11 +319,13 @@ int refresh(md_ctx *c, const double *lp) {
   void *m0 = c->mirror[c->mirror_cur], *m1 = c->mirror[1 - c->mirror_cur];
   const bool mixed = c->prec == MD_MIXED;
   if (c->model == MD_RING) {
-    if (mixed) mirror_kernel<MD_RING, true, ADJ><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
-    else mirror_kernel<MD_RING, false, ADJ><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    if (mixed && !ADJ && ring_tc(c))
+      mirror_kernel<MD_RING, true, false, 1><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else if (mixed) mirror_kernel<MD_RING, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else mirror_kernel<MD_RING, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   } else {
-    if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
-    else mirror_kernel<MD_GRAV2D, false, ADJ><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   }
   MD_LAUNCHED(c);
   return MD_OK;
@@ -319,6 +338,7 @@ int mirror_refresh(md_ctx *c) {
   if (rc) return rc;
   c->mirror_valid = true;
   c->mirror_prec = c->prec;
+  c->mirror_fmt = ring_tc(c) ? 1 : 0;
   return MD_OK;
 }
 
@@ -328,7 +348,7 @@ int adjoint_mirror_refresh(md_ctx *c, const double *lp) {
 }
 
 int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
-  if (!c->mirror_valid || c->mirror_prec != c->prec) {
+  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != (ring_tc(c) ? 1 : 0)) {
     int rc = mirror_refresh(c);
     if (rc) return rc;
   }
@@ -361,7 +381,7 @@ int pair_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, dou
 }
 
 int kick_drift_cached(md_ctx *c, double kick, double drift) {
-  if (!c->mirror_valid || c->mirror_prec != c->prec) {
+  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != (ring_tc(c) ? 1 : 0)) {
     int rc = mirror_refresh(c);
     if (rc) return rc;
   }
@@ -370,11 +390,13 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
   void *mo = c->mirror[1 - c->mirror_cur];
   const bool mixed = c->prec == MD_MIXED;
   if (c->model == MD_RING) {
-    if (mixed) kick_drift_cached_kernel<MD_RING, true><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
-    else kick_drift_cached_kernel<MD_RING, false><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    if (mixed && ring_tc(c))
+      kick_drift_cached_kernel<MD_RING, true, 1><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else if (mixed) kick_drift_cached_kernel<MD_RING, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else kick_drift_cached_kernel<MD_RING, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   } else {
-    if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
-    else kick_drift_cached_kernel<MD_GRAV2D, false><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else kick_drift_cached_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   }
   MD_LAUNCHED(c);
   c->mirror_cur = 1 - c->mirror_cur;

@@ -167,6 +167,9 @@ template <int R_, int TJ_, int MODE>
 struct RingMixed {
   static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_RING, true, false>::value;
   static constexpr bool MASK = true;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     float2 s[R], c[R], a[R], g[R], acc[R];
     CompSum cs[R][NACC];
@@ -178,7 +181,7 @@ struct RingMixed {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const int64_t i = i0 + (int64_t)r * NT;
+      const int64_t i = i0 + row_of(r);
       const float *m = (const float *)mirror + (i >> 1) * 8 + (i & 1);
       st.s[r] = f2(-m[0]);
       st.c[r] = f2(m[2]);
@@ -206,7 +209,7 @@ struct RingMixed {
         float2 y2 = __fmul2_rn(y, y);
         float2 qq = __fmul2_rn(S, y);
         if (DIAG) {
-          const int64_t i = i0 + (int64_t)r * NT, j = j0 + 2 * k;
+          const int64_t i = i0 + row_of(r), j = j0 + 2 * k;
           if (i == j) qq.x = 0.f;
           if (i == j + 1) qq.y = 0.f;
         }
@@ -247,6 +250,9 @@ template <int R_, int TJ_, int MODE, int OFF = 0>
 struct GravMixed {
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
   static constexpr bool MASK = false;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   static_assert(OFF == 0 || (TJ / 2) % OFF == 0, "offload period must divide the tile");
   struct State {
     float2 x[R], y[R], fx[R], fy[R];
@@ -259,7 +265,7 @@ struct GravMixed {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const int64_t i = i0 + (int64_t)r * NT;
+      const int64_t i = i0 + row_of(r);
       const float *m = (const float *)mirror + (i >> 1) * 4 + (i & 1);
       st.x[r] = f2(-m[0]);
       st.y[r] = f2(-m[2]);
@@ -307,6 +313,9 @@ template <int R_, int TJ_, int MODE>
 struct RingF64 {
   static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_RING, false, false>::value;
   static constexpr bool MASK = true;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     double s[R], c[R], a[R], g[R];
     double accd[R][NACC];
@@ -318,7 +327,7 @@ struct RingF64 {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 4;
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 4;
       st.s[r] = m[0];
       st.c[r] = m[1];
       st.a[r] = m[2];
@@ -338,7 +347,7 @@ struct RingF64 {
         double sh = fma(st.a[r], ag.y, -(st.g[r] * ag.x));
         double y = rsqrt_nr(fma(sh, sh, a.epsd));
         double qq = S * y;
-        if (DIAG && i0 + (int64_t)r * NT == j0 + k) qq = 0.0;
+        if (DIAG && i0 + row_of(r) == j0 + k) qq = 0.0;
         st.accd[r][0] = fma(qq, y * y, st.accd[r][0]);
       }
     }
@@ -350,6 +359,9 @@ template <int R_, int TJ_, int MODE>
 struct GravF64 {
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, false, false>::value;
   static constexpr bool MASK = false;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     double x[R], y[R];
     double accd[R][NACC];
@@ -361,7 +373,7 @@ struct GravF64 {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 2;
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 2;
       st.x[r] = m[0];
       st.y[r] = m[1];
       st.accd[r][0] = st.accd[r][1] = 0.0;
@@ -390,6 +402,9 @@ template <int R_, int TJ_, int MODE>
 struct RingMixedAdj {
   static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_RING, true, true>::value;
   static constexpr bool MASK = true;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     float2 s[R], c[R], a[R], g[R], ns[R], v[R], af[R], aj[R], ae[R];
     CompSum cs[R][NACC];
@@ -401,7 +416,7 @@ struct RingMixedAdj {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const int64_t i = i0 + (int64_t)r * NT;
+      const int64_t i = i0 + row_of(r);
       const float *m = (const float *)mirror + (i >> 1) * 12 + (i & 1);
       st.s[r] = f2(-m[0]);
       st.ns[r] = f2(m[0]);
@@ -434,7 +449,7 @@ struct RingMixedAdj {
         float2 r3 = __fmul2_rn(y2, y);
         float2 r5 = __fmul2_rn(r3, y2);
         if (DIAG) {
-          const int64_t i = i0 + (int64_t)r * NT, j = j0 + 2 * k;
+          const int64_t i = i0 + row_of(r), j = j0 + 2 * k;
           if (i == j) S.x = 0.f;
           if (i == j + 1) S.y = 0.f;
         }
@@ -460,6 +475,9 @@ template <int R_, int TJ_, int MODE>
 struct GravMixedAdj {
   static constexpr int R = R_, TJ = TJ_, NACC = 6, JB = RecordBytes<MD_GRAV2D, true, true>::value;
   static constexpr bool MASK = false;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     float2 x[R], y[R], vx[R], vy[R], fx[R], fy[R], jx[R], jy[R], ex[R], ey[R];
     CompSum cs[R][NACC];
@@ -471,7 +489,7 @@ struct GravMixedAdj {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const int64_t i = i0 + (int64_t)r * NT;
+      const int64_t i = i0 + row_of(r);
       const float *m = (const float *)mirror + (i >> 1) * 8 + (i & 1);
       st.x[r] = f2(-m[0]);
       st.y[r] = f2(-m[2]);
@@ -526,6 +544,9 @@ template <int R_, int TJ_, int MODE>
 struct RingF64Adj {
   static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_RING, false, true>::value;
   static constexpr bool MASK = true;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     double s[R], c[R], a[R], g[R], v[R];
     double accd[R][NACC];
@@ -537,7 +558,7 @@ struct RingF64Adj {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 6;
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 6;
       st.s[r] = m[0];
       st.c[r] = m[1];
       st.a[r] = m[2];
@@ -559,7 +580,7 @@ struct RingF64Adj {
         double sh = fma(st.a[r], ag.y, -(st.g[r] * ag.x));
         double y = rsqrt_nr(fma(sh, sh, a.epsd));
         double y2 = y * y, r3 = y2 * y, r5 = r3 * y2;
-        if (DIAG && i0 + (int64_t)r * NT == j0 + k) S = 0.0;
+        if (DIAG && i0 + row_of(r) == j0 + k) S = 0.0;
         st.accd[r][0] = fma(S, r3, st.accd[r][0]);
         st.accd[r][2] = fma(S, r5, st.accd[r][2]);
         double G = fma(-0.75 * S * S, r5, C * r3);
@@ -574,6 +595,9 @@ template <int R_, int TJ_, int MODE>
 struct GravF64Adj {
   static constexpr int R = R_, TJ = TJ_, NACC = 6, JB = RecordBytes<MD_GRAV2D, false, true>::value;
   static constexpr bool MASK = false;
+  static constexpr int NR = R;  // rows finished per thread
+  static constexpr int FMT = 0;  // mirror record format
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
     double x[R], y[R], vx[R], vy[R];
     double accd[R][NACC];
@@ -585,7 +609,7 @@ struct GravF64Adj {
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      const double *m = (const double *)mirror + (i0 + (int64_t)r * NT) * 4;
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 4;
       st.x[r] = m[0];
       st.y[r] = m[1];
       st.vx[r] = m[2];
@@ -618,10 +642,185 @@ struct GravF64Adj {
   }
 };
 
+// ------------------------------------------------ forward Ring, tensor cores
+//
+// sin(d) = s_i c_j - c_i s_j and sin(d/2) = a_i g_j - g_i a_j (a, g: sin, cos of
+// the half angle) are dot products of length 2, so for a 16 x 8 block of pairs
+// each is one warp-level matrix multiply.  The FP32 operands are split into
+// TF32 hi + lo parts (round to nearest) and the three significant products
+// hi.hi + hi.lo + lo.hi are laid along K (6 of the 8 K slots), which keeps the
+// result within a few FP32 ulps.  What is left per pair is 4 FP32 operations
+// and one rsqrt:  dd = sh^2 + eps/2,  acc += S * dd^(-3/2).
+//   A row i (S):  [s_h, c_h, s_h, c_h, s_l, c_l, 0, 0]
+//   B col j (S):  [c_h, -s_h, c_l, -s_l, c_h, -s_h, 0, 0]      (same with a, g for sh)
+// The mirror record of the 8 particles of an n-block holds, per lane (g, t) of
+// the m16n8k8 B fragment, the pair (B[t][g], B[t+4][g]) for S, then for sh:
+// 512 bytes per 8 particles.
+
+__device__ __forceinline__ unsigned tf32_rn(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// hi and lo TF32 parts of x (hi + lo = x to ~2^-22 relative)
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+  hi = __uint_as_float(tf32_rn(x));
+  lo = __uint_as_float(tf32_rn(x - hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%10,%10,%10};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+
+// TC record of particle i from FP32 (s, c, a, g); all-zero = padding
+__device__ __forceinline__ void write_tc_record(void *mirror, int64_t i, float s, float c, float a, float g) {
+  float *m = (float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
+  float sh, sl, ch, cl, ah, al, gh, gl;
+  tf32_split(s, sh, sl);
+  tf32_split(c, ch, cl);
+  tf32_split(a, ah, al);
+  tf32_split(g, gh, gl);
+  // lanes 4g+t of the S fragment, then of the sin(d/2) fragment (64 floats later)
+  float2 *S = (float2 *)m, *H = (float2 *)(m + 64);
+  S[0] = make_float2(ch, ch);
+  S[1] = make_float2(-sh, -sh);
+  S[2] = make_float2(cl, 0.f);
+  S[3] = make_float2(-sl, 0.f);
+  H[0] = make_float2(gh, gh);
+  H[1] = make_float2(-ah, -ah);
+  H[2] = make_float2(gl, 0.f);
+  H[3] = make_float2(-al, 0.f);
+}
+
+__device__ __forceinline__ void write_tc_pad(void *mirror, int64_t i) {
+  float *m = (float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
+#pragma unroll
+  for (int k = 0; k < 8; k++) m[k] = m[64 + k] = 0.f;
+}
+
+template <int RM_, int TJ_, int MODE>
+struct RingTC {
+  static constexpr int RM = RM_;              // 16-row m-blocks per warp
+  static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = NT * R = 64 RM rows per CTA
+  static constexpr int TJ = TJ_, NACC = 1, JB = 64;
+  static constexpr bool MASK = true;
+  static constexpr int NR = 2 * RM;           // rows g and g+8 of each m-block
+  static constexpr int FMT = 1;               // tensor-core fragment records
+  static_assert(NT * R == 64 * RM, "tile rows: 4 warps x RM m-blocks x 16");
+  __device__ static int mrow(int rr) {        // row offset in the tile of item rr = 2 r + h
+    const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+    return w * 16 * RM + 16 * (rr >> 1) + g + 8 * (rr & 1);
+  }
+  __device__ static int row_of(int rr) { return (threadIdx.x & 3) == 0 ? mrow(rr) : -1; }
+  struct State {
+    unsigned aS[RM][4], aH[RM][4];
+    float2 acc[RM][2];
+    CompSum cs[RM][2];
+  };
+  __device__ static void total(const State &st, int rr, double *out) {
+    double v = csum_total(st.cs[rr >> 1][rr & 1]);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    out[0] = v;
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+    const int t = threadIdx.x & 3;
+#pragma unroll
+    for (int r = 0; r < RM; r++) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int64_t i = i0 + mrow(2 * r + h);
+        const float *m = (const float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
+        // record lanes: 0 -> (c_h, c_h), 1 -> (-s_h, -s_h), 2 -> (c_l, 0), 3 -> (-s_l, 0)
+        const float ch = m[0], sh = -m[2], cl = m[4], sl = -m[6];
+        const float gh = m[64], ah = -m[66], gl = m[68], al = -m[70];
+        const float s_lo = (t == 0) ? sl : (t == 1) ? cl : 0.f;  // A[row][t+4]
+        const float h_lo = (t == 0) ? al : (t == 1) ? gl : 0.f;
+        st.aS[r][h] = __float_as_uint((t & 1) ? ch : sh);      // A[row][t]
+        st.aS[r][2 + h] = __float_as_uint(s_lo);
+        st.aH[r][h] = __float_as_uint((t & 1) ? gh : ah);
+        st.aH[r][2 + h] = __float_as_uint(h_lo);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        st.acc[r][h] = f2(0.f);
+        st.cs[r][h] = CompSum{0.f, 0.f};
+      }
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const float *sm = (const float *)smb;
+    const float2 he = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll 2
+    for (int k = 0; k < TJ / 8; k++) {
+      const float2 bs = *(const float2 *)(sm + k * 128 + lane * 2);
+      const float2 bh = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
+      const unsigned bs0 = __float_as_uint(bs.x), bs1 = __float_as_uint(bs.y);
+      const unsigned bh0 = __float_as_uint(bh.x), bh1 = __float_as_uint(bh.y);
+#pragma unroll
+      for (int r = 0; r < RM; r++) {
+        float dS[4], dH[4];
+        mma_tf32(dS, st.aS[r], bs0, bs1);
+        mma_tf32(dH, st.aH[r], bh0, bh1);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const float2 S = make_float2(dS[2 * h], dS[2 * h + 1]);   // row g + 8h, columns 2t, 2t+1
+          const float2 sh = make_float2(dH[2 * h], dH[2 * h + 1]);
+          const float2 d = __ffma2_rn(sh, sh, he);
+          const float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+          float2 qq = __fmul2_rn(S, y);
+          if (DIAG) {
+            const int64_t i = i0 + mrow(2 * r + h), j = j0 + 8 * k + 2 * t;
+            if (i == j) qq.x = 0.f;
+            if (i == j + 1) qq.y = 0.f;
+          }
+          st.acc[r][h] = __ffma2_rn(qq, __fmul2_rn(y, y), st.acc[r][h]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        csum_add2(st.cs[r][h], st.acc[r][h]);
+        st.acc[r][h] = f2(0.f);
+      }
+  }
+};
+
+// Record writers by format: FMT 0 = interleaved FP32 / FP64 records above,
+// FMT 1 = tensor-core fragment records (Ring FP32 forward only).
+template <int MODEL, bool MIXED, bool ADJ, int FMT>
+__device__ __forceinline__ void write_record_fmt(void *mirror, int64_t i, double x, double y, double vx, double vy) {
+  if constexpr (FMT == 1) {
+    const float r = (float)reduce_2pi(x);
+    float s, c, a, g;
+    sincos_small(r, &s, &c);
+    sincos_small(0.5f * r, &a, &g);
+    write_tc_record(mirror, i, s, c, a, g);
+  } else {
+    write_record<MODEL, MIXED, ADJ>(mirror, i, x, y, vx, vy);
+  }
+}
+template <int MODEL, bool MIXED, bool ADJ, int FMT>
+__device__ __forceinline__ void write_pad_fmt(void *mirror, int64_t i) {
+  if constexpr (FMT == 1)
+    write_tc_pad(mirror, i);
+  else
+    write_pad<MODEL, MIXED, ADJ>(mirror, i);
+}
+
 // ============================================================ epilogues ====
 
 // Forward stages: kick, drift, new mirror record (or the force alone).
-template <int MODEL, bool MIXED, int MODE>
+template <int MODEL, bool MIXED, int MODE, int FMT>
 __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, const double *acc) {
   constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
   if (i >= a.N) return;
@@ -645,7 +844,7 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
       a.fout[d * a.N + i] = f[d];
     }
   }
-  if (MODE == STAGE_KICK_DRIFT) write_record<MODEL, MIXED, false>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+  if (MODE == STAGE_KICK_DRIFT) write_record_fmt<MODEL, MIXED, false, FMT>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
 }
 
 // Reverse stages of md_grad, at the position q_s of one kick (b_adj = a.kick,
@@ -697,7 +896,7 @@ __device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const doubl
   if constexpr (MODE == STAGE_ADJOINT)
     finish_adjoint<MODEL, MIXED>(a, i, acc);
   else
-    finish_forward<MODEL, MIXED, MODE>(a, i, acc);
+    finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, acc);
 }
 
 }  // namespace

@@ -188,3 +188,34 @@ def test_mixed_2d_force_with_fma_pipe_reciprocals(N):
     f = s.force()
     err, scale, _ = _force_err(2, q, f)
     assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+
+
+@pytest.mark.parametrize("tc", [1, 2])
+@pytest.mark.parametrize("N", [1, 2, 33, 1000, 4097])
+def test_ring_tensor_core_force_error_bound(N, tc):
+    """Ring FP32 path with sin(d) and sin(d/2) from split-TF32 tensor-core MMAs."""
+    s, q, p = _sys(1, N, "mixed")
+    s.set_tuning("ring_tc", tc)
+    f = s.force()
+    err, scale, _ = _force_err(1, q, f)
+    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+    if N == 1:
+        assert f[0] == 0.0
+
+
+@pytest.mark.parametrize("tc", [1, 2])
+def test_ring_tensor_core_steps_match_fp32_kernel(tc):
+    """Ten steps with the tensor-core kernel stay as close to FP64 as the FP32
+    kernel, and the energy error keeps the mixed-vs-FP64 bound."""
+    N, dt = 3000, 0.05
+    ref, q0, p0 = _sys(1, N, "fp64", dt=dt)
+    tcs, _, _ = _sys(1, N, "mixed", dt=dt)
+    tcs.set_tuning("ring_tc", tc)
+    e0 = sum(ref.energy())
+    ref.step(10)
+    tcs.step(10)
+    (qr, pr), (qt, pt_) = ref.get_state(), tcs.get_state()
+    assert np.max(np.abs(qt - qr)) < 1e-5 and np.max(np.abs(pt_ - pr)) < 1e-5
+    d_ref = abs(sum(ref.energy()) - e0) / abs(e0)
+    d_tc = abs(sum(tcs.energy()) - e0) / abs(e0)
+    assert d_tc <= 2 * d_ref + 1e-9, (d_tc, d_ref)
