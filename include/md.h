@@ -164,6 +164,14 @@ int md_magnetization(md_ctx *ctx, double *mx, double *my);
 int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
             double *grad_q, double *grad_p, double *grad_eps, double *value);
 
+/* Advance the state nsteps steps exactly as md_step, together with a tangent
+ * vector (dq, dp) carried by the linearisation of the same discrete map
+ * (forward-mode derivative: dp += b dt J(q) dq at each kick, dq += d dt dp at
+ * each drift, J = df/dq).  The building block of largest-Lyapunov-exponent
+ * estimates (repeat, renormalising the tangent).  dq, dp: host arrays of dim*N,
+ * read and overwritten.  Uses the context's precision.  Synchronous. */
+int md_tangent_step(md_ctx *ctx, int64_t nsteps, double *dq, double *dp);
+
 /* Route the library's device allocations through alloc(bytes, user) and
  * free(ptr, user) (for example a caching allocator of the host framework).
  * alloc returns NULL on failure, which the library reports as MD_ENOMEM.

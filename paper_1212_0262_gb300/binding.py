@@ -57,6 +57,7 @@ _SIGS = {
     "md_energy": (_c.c_int, [_P, _D, _D]),
     "md_magnetization": (_c.c_int, [_P, _D, _D]),
     "md_grad": (_c.c_int, [_P, _c.c_int, _c.c_int64, _c.c_int, _P, _P, _D, _D]),
+    "md_tangent_step": (_c.c_int, [_P, _c.c_int64, _P, _P]),
     "md_set_allocator": (_c.c_int, [_P, _P, _P]),
     "md_potential_noalloc": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_double, _P, _P, _P]),
     "md_synchronize": (_c.c_int, [_P]),

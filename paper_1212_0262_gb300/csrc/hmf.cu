@@ -456,3 +456,73 @@ int hmf_magnetization_terminal(md_ctx *c, double cx, double cy, double *lq) {
   MD_LAUNCHED(c);
   return MD_OK;
 }
+
+// ---------------------------------------------------------------- tangent --
+//
+// Forward tangent (linearised) dynamics for HMF:  p += kick f, dp += kick J dq,
+// then theta += drift p, dq += drift dp, with (J dq)_i from the four sums of the
+// current (theta, dq) as in the adjoint above.
+
+namespace {
+
+template <bool MIXED>
+__global__ void __launch_bounds__(NT) hmf_tangent_stage_kernel(HmfAdjArgs a) {
+  const double mx = a.s_in[0] * a.invN, my = a.s_in[1] * a.invN;
+  const double A = a.s_in[2] * a.invN, B = a.s_in[3] * a.invN;
+  const float mxf = (float)mx, myf = (float)my;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int64_t G = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < a.N; i += G) {
+    double th = a.q[i], pp = a.p[i], dq = a.lq[i], dp = a.lp[i];
+    double s, c, f;
+    sc_of<MIXED>(th, s, c);
+    if (MIXED)
+      f = f2d_bits(__fsub_rn(__fmul_rn((float)c, myf), __fmul_rn((float)s, mxf)));
+    else
+      f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
+    const double jv = fma(-fma(s, my, c * mx), dq, fma(c, A, s * B));
+    pp = fma(a.b_adj, f, pp);
+    dp = fma(a.b_adj, jv, dp);
+    if (a.drift != 0.0) {
+      th = fma(a.drift, pp, th);
+      dq = fma(a.drift, dp, dq);
+      sc_of<MIXED>(th, s, c);
+      a0 += c;
+      a1 += s;
+      a2 = fma(c, dq, a2);
+      a3 = fma(s, dq, a3);
+      a.q[i] = th;
+      a.lq[i] = dq;
+    }
+    a.p[i] = pp;
+    a.lp[i] = dp;
+  }
+  if (a.drift != 0.0) grid_finish4(a0, a1, a2, a3, a.partials, a.s_out, a.ticket);
+}
+
+}  // namespace
+
+int hmf_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double *dp, const double *s_in,
+                      double *s_out) {
+  HmfAdjArgs a;
+  a.q = c->q;
+  a.p = c->p;
+  a.lq = dq;
+  a.lp = dp;
+  a.N = c->N;
+  a.invN = 1.0 / (double)c->N;
+  a.s_in = s_in;
+  a.b_adj = kick;
+  a.b_undo = 0.0;
+  a.drift = drift;
+  a.partials = c->hmf_partials;
+  a.s_out = s_out;
+  a.ticket = c->hmf_ticket;
+  const int g = grid_for(c, (const void *)hmf_tangent_stage_kernel<false>, c->N);
+  if (c->prec == MD_MIXED)
+    hmf_tangent_stage_kernel<true><<<g, NT, 0, c->stream>>>(a);
+  else
+    hmf_tangent_stage_kernel<false><<<g, NT, 0, c->stream>>>(a);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}

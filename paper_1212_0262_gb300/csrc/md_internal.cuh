@@ -108,7 +108,15 @@ enum StageMode {
   STAGE_KICK_ONLY = 1,   // f(q); p += kick f; store f in ctx->f (first-same-as-last cache)
   STAGE_FORCE_ONLY = 2,  // f(q) into an output array
   STAGE_ADJOINT = 3,     // reverse stage of md_grad (kick adjoint and undo, drift adjoint and undo)
+  STAGE_TANGENT = 4,     // forward stage of the tangent dynamics (state and tangent vector together)
 };
+
+// pairs.cu / hmf.cu: one forward stage of the tangent (linearised) dynamics,
+//   p += kick f(q);  dp += kick J(q) dq;  then, if drift != 0: q += drift p;  dq += drift dp.
+// The pair version reads adjoint-format records holding (q, dq).
+int pair_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double *dp);
+int hmf_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double *dp, const double *s_in,
+                      double *s_out);
 
 // api.cu: nsteps integrator steps of Sec. 3 on the context's state (md_step's body).
 int integrate(md_ctx *c, int64_t nsteps);

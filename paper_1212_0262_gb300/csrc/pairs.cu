@@ -271,7 +271,8 @@ int launch_streamk(md_ctx *c, PairArgs a) {
   a.tickets = c->sk_tickets;
   kern<<<a.P, NT, 0, c->stream>>>(a);
   MD_LAUNCHED(c);
-  if (MODE == STAGE_KICK_DRIFT || (MODE == STAGE_ADJOINT && a.drift != 0.0)) c->mirror_cur = 1 - c->mirror_cur;
+  if (MODE == STAGE_KICK_DRIFT || ((MODE == STAGE_ADJOINT || MODE == STAGE_TANGENT) && a.drift != 0.0))
+    c->mirror_cur = 1 - c->mirror_cur;
   return MD_OK;
 }
 
@@ -372,6 +373,21 @@ int pair_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, dou
   a.lp = lp;
   a.epsacc = epsacc;
   constexpr int M = STAGE_ADJOINT;
+  if (c->model == MD_RING) {
+    if (c->prec == MD_MIXED) return launch_streamk<RingMixedAdj<4, 256, M>, MD_RING, true, M>(c, a);
+    return launch_streamk<RingF64Adj<2, 128, M>, MD_RING, false, M>(c, a);
+  }
+  if (c->prec == MD_MIXED) return launch_streamk<GravMixedAdj<2, 256, M>, MD_GRAV2D, true, M>(c, a);
+  return launch_streamk<GravF64Adj<2, 128, M>, MD_GRAV2D, false, M>(c, a);
+}
+
+int pair_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double *dp) {
+  PairArgs a{};
+  a.kick = kick;
+  a.drift = drift;
+  a.lq = dq;
+  a.lp = dp;
+  constexpr int M = STAGE_TANGENT;
   if (c->model == MD_RING) {
     if (c->prec == MD_MIXED) return launch_streamk<RingMixedAdj<4, 256, M>, MD_RING, true, M>(c, a);
     return launch_streamk<RingF64Adj<2, 128, M>, MD_RING, false, M>(c, a);

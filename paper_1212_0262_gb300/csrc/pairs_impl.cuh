@@ -891,10 +891,41 @@ __device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, con
   if (a.drift != 0.0) write_record<MODEL, MIXED, true>(a.mirror_out, i, x[0], x[D - 1], lp[0], lp[D - 1]);
 }
 
+// Tangent stages (forward-mode derivative of the stage map), with a.lq = dq and
+// a.lp = dp: p += kick f; dp += kick J dq; then q += drift p; dq += drift dp and
+// a new adjoint-format record (q, dq) for the next stage.
+template <int MODEL, bool MIXED>
+__device__ __forceinline__ void finish_tangent(const PairArgs &a, int64_t i, const double *acc) {
+  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  if (i >= a.N) return;
+  const double n = (double)a.N;
+  double x[D], v[D];
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    const double f = MODEL == MD_RING ? -acc[0] / (8.0 * n) : -2.0 * acc[d] / n;
+    const double jv = MODEL == MD_RING ? -acc[1] / (8.0 * n) : -2.0 * acc[2 + d] / n;
+    const double pp = fma(a.kick, f, a.p[d * a.N + i]);
+    const double dpp = fma(a.kick, jv, a.lp[d * a.N + i]);
+    a.p[d * a.N + i] = pp;
+    a.lp[d * a.N + i] = dpp;
+    x[d] = a.q[d * a.N + i];
+    v[d] = a.lq[d * a.N + i];
+    if (a.drift != 0.0) {
+      x[d] = fma(a.drift, pp, x[d]);
+      v[d] = fma(a.drift, dpp, v[d]);
+      a.q[d * a.N + i] = x[d];
+      a.lq[d * a.N + i] = v[d];
+    }
+  }
+  if (a.drift != 0.0) write_record<MODEL, MIXED, true>(a.mirror_out, i, x[0], x[D - 1], v[0], v[D - 1]);
+}
+
 template <class Pol, int MODEL, bool MIXED, int MODE>
 __device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const double *acc) {
   if constexpr (MODE == STAGE_ADJOINT)
     finish_adjoint<MODEL, MIXED>(a, i, acc);
+  else if constexpr (MODE == STAGE_TANGENT)
+    finish_tangent<MODEL, MIXED>(a, i, acc);
   else
     finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, acc);
 }

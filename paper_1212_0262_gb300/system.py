@@ -57,6 +57,7 @@ class System:
         self.model = _model(model)
         self.N = int(N)
         self.dim = 2 if self.model == 2 else 1
+        self._dt = float(dt)
         h = lib.md_init(self.model, self.N, float(eps), float(dt), int(seed) & (2**64 - 1))
         if not h:
             raise B.MDError(B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
@@ -90,6 +91,7 @@ class System:
 
     def set_dt(self, dt: float) -> None:
         self._chk(B.load().md_set_dt(self._h, float(dt)))
+        self._dt = float(dt)
 
     def set_tuning(self, key: str, value: int) -> None:
         self._chk(B.load().md_set_tuning(self._h, key.encode(), int(value)))
@@ -161,6 +163,36 @@ class System:
         self._chk(B.load().md_grad(self._h, int(observable), int(nsteps), int(checkpoint_every),
                                    _ptr(gq), _ptr(gp), ctypes.byref(ge), ctypes.byref(val)))
         return val.value, gq, gp, ge.value
+
+    def set_eps(self, eps: float) -> None:
+        self._chk(B.load().md_set_eps(self._h, float(eps)))
+
+    def tangent_step(self, nsteps: int, dq, dp):
+        """Advance the state nsteps steps with a tangent vector; returns the new (dq, dp)."""
+        dq, dp = _f64(dq).copy(), _f64(dp).copy()
+        self._chk(B.load().md_tangent_step(self._h, int(nsteps), _ptr(dq), _ptr(dp)))
+        return dq, dp
+
+    def lyapunov(self, nsteps: int, renorm_every: int = 10, seed: int = 0, dt: float | None = None) -> float:
+        """Largest Lyapunov exponent estimate: a seeded random tangent vector carried
+        along nsteps steps (advancing the state), renormalised every renorm_every
+        steps; the mean log growth rate per unit time."""
+        from . import inputs
+
+        n = self.dim * self.N
+        d = inputs.uniform(seed, 0, 2 * n) - 0.5
+        d /= np.linalg.norm(d)
+        dq, dp = d[:n], d[n:]
+        total, done = 0.0, 0
+        while done < nsteps:
+            k = min(renorm_every, nsteps - done)
+            dq, dp = self.tangent_step(k, dq, dp)
+            norm = float(np.sqrt(np.dot(dq, dq) + np.dot(dp, dp)))
+            total += np.log(norm)
+            dq, dp = dq / norm, dp / norm
+            done += k
+        step_dt = dt if dt is not None else self._dt
+        return total / (nsteps * step_dt)
 
     @property
     def launch_count(self) -> int:
