@@ -49,6 +49,20 @@ WORKLOADS = {
 HMF_BYTES_PER_PARTICLE_STAGE = 32
 # FP32-pipe operations and SFU operations per pair in the mixed pair kernels
 PAIR_OPS = {1: (8, 1), 2: (6, 1)}
+# Per force-kernel variant (md_force_kernel): name, FP32 operations and SFU operations
+# per evaluated pair term, and whether each unordered pair is evaluated once.
+#   one-sided Ring: S and sin(d/2) (2 FMA + 2 MUL), dd (FMA), y^2, S y, acc (FMA) -> 8
+#   tensor-core Ring: S and sin(d/2) on the tensor cores -> 4
+#   one-sided 2D: dx, dy, |r|^2 + eps (2 FMA), fx, fy -> 6
+#   symmetric: + 1 (Ring) / 2 (2D) column accumulations per pair term, plus the
+#   butterfly adds (1/8 per term for Ring, 1/4 for 2D)
+PAIR_KERNELS = {
+    (1, 2): ("streamk_kernel<RingMixed<8,256>>", 8, 1, False),
+    (1, 3): ("streamk_kernel<RingTC<4,256>>", 4, 1, False),
+    (1, 5): ("sym_kernel<RingTC<4,256>>", 5.125, 1, True),
+    (2, 2): ("streamk_kernel<GravMixed<8,256>>", 6, 1, False),
+    (2, 4): ("sym_kernel<GravMixed<8,256>>", 8.25, 1, True),
+}
 
 
 def parse():
@@ -354,18 +368,23 @@ def run_ours(args, w):
         nsm = rates[0]
         fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
         sfu_rate = rates[5] if model == 1 else rates[7]
-        fops, sops = PAIR_OPS[model]
+        kcode = sysm.force_kernel
+        kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
         pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops)
         mhz = clocks.get("sm_mhz") or rates[2]
         peak = nsm * pairs_per_clk * mhz * 1e6
-        achieved = N * N / (avg_ms * 1e-3)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "pair-interactions/s",
+        # algorithmic pair terms per force pass: N^2 ordered pairs, or N (N - 1) / 2
+        # unordered pairs when each is evaluated once
+        terms = N * (N - 1) / 2 if sym else N * N
+        achieved = terms / (avg_ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                    "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": f"pair_stage_kernel<{'Ring' if model == 1 else '2D'}, {args.prec}>",
+                    "kernel": f"{kname}, {args.prec}",
                     "peak_derivation": {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
                                         "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
                                         "sfu_ops_per_pair": sops, "sm_mhz": mhz},
-                    "avg_launch_ms": avg_ms}
+                    "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
 
     # FP64 path on the same workload (few steps) and the matching mixed energy error
     extra = {}
@@ -375,6 +394,9 @@ def run_ours(args, w):
         for prec in ("fp64", "mixed"):
             with System(model, N, w["eps"], w["dt"], w["seed"], precision=prec) as s2:
                 s2.set_stream(stream)
+                for kv in args.tune:
+                    k, v = kv.split("=")
+                    s2.set_tuning(k, int(v))
                 e_a = sum(s2.energy())
                 s2.step(1)
                 torch.cuda.synchronize()

@@ -99,13 +99,34 @@ int md_set_dt(md_ctx *ctx, double dt);
 /* Change the softening eps of Eqs. 1 and 3 (> 0 for Ring/2D, >= 0 for HMF). */
 int md_set_eps(md_ctx *ctx, double eps);
 
-/* Tuning knobs of the kernels (used by the autotuner; defaults are sensible):
+/* Tuning knobs of the kernels (defaults: r_mixed 8, r_fp64 2, ring_tc 1, symmetric 1,
+ * step_graphs 1, the rest 0):
  *   "r_mixed"          i-particles per thread of the FP32 pair kernels (4 or 8)
  *   "r_fp64"           i-particles per thread of the FP64 pair kernels (2 or 4)
  *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
  *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = occupancy limit)
+ *   "rcp_offload"      2D FP32: every 8th pair of j's takes 1/x on the FMA pipe (0 or 8)
+ *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32
+ *                      tensor-core products (0 off; 1 or 2: 4 or 2 16-row blocks per warp)
+ *   "symmetric"        FP32 forward stages of Ring (with ring_tc 1) and 2D: every
+ *                      unordered pair evaluated once and added to both particles
+ *                      (Newton's third law; the paper evaluates both orders, Sec. 3.2).
+ *                      Needs column-partial storage of about N^2 / 2^16 floats (Ring)
+ *                      or N^2 / 2^18 (2D); above 4 GiB of it the one-sided kernel runs.
+ *   "step_graphs"      md_step replays its steps after the first from captured CUDA
+ *                      graphs of 8 steps (1, default) or launches every stage (0).
  * MD_EINVAL for an unknown key or value. */
 int md_set_tuning(md_ctx *ctx, const char *key, int64_t value);
+
+/* Which force kernel the context's next Ring / 2D stage runs (MD_KERNEL_*), from
+ * its model, precision and tuning; -1 for a NULL context. */
+#define MD_KERNEL_HMF 0          /* HMF mean-field stage (Sec. 3.1) */
+#define MD_KERNEL_PAIRS_FP64 1   /* FP64 all-pairs, every ordered pair */
+#define MD_KERNEL_PAIRS 2        /* FP32 all-pairs on the CUDA cores, every ordered pair */
+#define MD_KERNEL_PAIRS_TC 3     /* FP32 Ring with tensor-core products, every ordered pair */
+#define MD_KERNEL_PAIRS_SYM 4    /* FP32 2D, every unordered pair once */
+#define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 Ring with tensor-core products, every unordered pair once */
+int md_force_kernel(const md_ctx *ctx);
 
 /* Redraw the state with recipe `kind` (MD_IC_*) and `params` from `seed`.
  * Draw order: positions (counters 0..dim*N-1; the disk and annulus use two

@@ -44,6 +44,7 @@ _SIGS = {
     "md_set_dt": (_c.c_int, [_P, _c.c_double]),
     "md_set_eps": (_c.c_int, [_P, _c.c_double]),
     "md_set_tuning": (_c.c_int, [_P, _c.c_char_p, _c.c_int64]),
+    "md_force_kernel": (_c.c_int, [_P]),
     "md_set_ic": (_c.c_int, [_P, _c.c_int, _D, _c.c_uint64]),
     "md_set_state": (_c.c_int, [_P, _P, _P]),
     "md_get_state": (_c.c_int, [_P, _P, _P]),

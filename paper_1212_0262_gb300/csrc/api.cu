@@ -10,6 +10,7 @@
 // the step boundary and keeps that force for the next call.
 #include <stdarg.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <mutex>
 #include <new>
@@ -136,6 +137,10 @@ void md_free(md_ctx *c) {
   dev_free(c->mirror[1]);
   dev_free(c->sk_slots);
   dev_free(c->sk_tickets);
+  dev_free(c->sym_rowfull);
+  dev_free(c->sym_colslot);
+  dev_free(c->sym_chunks);
+  destroy_step_graphs(c);
   dev_free(c->red);
   dev_free(c->gw);
   if (c->host_scalars) cudaFreeHost(c->host_scalars);
@@ -252,6 +257,8 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
   else if (k == "rcp_offload" && (value == 0 || value == 8)) c->pt.rcp_off = (int)value;
   else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
+  else if (k == "symmetric" && (value == 0 || value == 1)) c->pt.symmetric = (int)value;
+  else if (k == "step_graphs" && (value == 0 || value == 1)) c->use_graphs = value != 0;
   else return set_err(c, MD_EINVAL, "unknown tuning key or value: %s=%lld", key, (long long)value);
   return MD_OK;
 }
@@ -312,6 +319,94 @@ int md_step(md_ctx *c, int64_t nsteps) {
 
 }  // extern "C"
 
+namespace {
+
+constexpr int kStepGraphSteps = 8;  // even: every stage flips the ping-pong parity, 3 per step
+
+// One step after the first: (2 B0, D0) (B1, D1) (B1, D0), kick-drift stages.
+int middle_step(md_ctx *c, const double *k, double h) {
+  int rc;
+  if (c->model == MD_HMF) {
+    if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, 2.0 * k[0] * h, k[2] * h, nullptr))) return rc;
+    if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, k[1] * h, k[3] * h, nullptr))) return rc;
+    return hmf_stage(c, STAGE_KICK_DRIFT, k[1] * h, k[2] * h, nullptr);
+  }
+  if ((rc = pair_stage(c, STAGE_KICK_DRIFT, 2.0 * k[0] * h, k[2] * h, nullptr))) return rc;
+  if ((rc = pair_stage(c, STAGE_KICK_DRIFT, k[1] * h, k[3] * h, nullptr))) return rc;
+  return pair_stage(c, STAGE_KICK_DRIFT, k[1] * h, k[2] * h, nullptr);
+}
+
+StepGraphKey step_key_of(const md_ctx *c, double h) {
+  StepGraphKey key;
+  memset(&key, 0, sizeof key);
+  key.model = c->model;
+  key.prec = c->prec;
+  key.N = c->N;
+  key.h = h;
+  key.eps = c->eps;
+  key.stream = (void *)c->stream;
+  key.pt = c->pt;
+  key.ht = c->ht;
+  key.mirror_fmt = c->mirror_fmt;
+  const void *b[13] = {c->q, c->p, c->mirror[0], c->mirror[1], c->sk_slots, c->sk_tickets, c->sym_rowfull,
+                       c->sym_colslot, c->sym_chunks, c->hmf_partials, c->hmf_m, c->hmf_ticket, c->f};
+  memcpy(key.bufs, b, sizeof b);
+  return key;
+}
+
+int parity_of(const md_ctx *c) { return c->model == MD_HMF ? c->hmf_cur : c->mirror_cur; }
+
+// kStepGraphSteps middle steps from the graph of the current parity, captured on
+// first use and again whenever anything the launches depend on has changed.
+// Every kernel it holds has already run once in this call (the first step), so
+// capture loads no module and allocates nothing.
+int replay_steps(md_ctx *c, const double *k, double h) {
+  const int par = parity_of(c);
+  const StepGraphKey key = step_key_of(c, h);
+  if (c->step_graph[par] && memcmp(&key, &c->step_key[par], sizeof key) != 0) {
+    cudaGraphExecDestroy(c->step_graph[par]);
+    c->step_graph[par] = nullptr;
+  }
+  if (!c->step_graph[par]) {
+    MD_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    const int64_t l0 = c->launches;
+    int rc = MD_OK;
+    for (int g = 0; g < kStepGraphSteps && rc == MD_OK; g++) rc = middle_step(c, k, h);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->step_graph_launches[par] = c->launches - l0;
+    c->launches = l0;
+    if (rc != MD_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      c->mirror_valid = c->hmf_m_valid = false;  // host-side parity no longer matches the device
+      return rc != MD_OK ? rc : cuda_err(c, e, "md_step: graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->step_graph[par], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      c->step_graph[par] = nullptr;
+      return cuda_err(c, ei, "md_step: graph instantiate");
+    }
+    c->step_key[par] = key;
+  }
+  MD_CUDA(c, cudaGraphLaunch(c->step_graph[par], c->stream));
+  c->launches += c->step_graph_launches[par];
+  return MD_OK;
+}
+
+}  // namespace
+
+void destroy_step_graphs(md_ctx *c) {
+  for (int k = 0; k < 2; k++)
+    if (c->step_graph[k]) {
+      cudaGraphExecDestroy(c->step_graph[k]);
+      c->step_graph[k] = nullptr;
+    }
+}
+
+// md_step's body: step 1 (whose first kick is B0, or comes from the cached
+// force), steps 2..n with the merged 2 B0 kicks (blocks of kStepGraphSteps from
+// CUDA graphs), and the closing B0 kick whose force is kept (first-same-as-last).
 int integrate(md_ctx *c, int64_t nsteps) {
   if (nsteps == 0) return MD_OK;
   double k[4];
@@ -319,24 +414,23 @@ int integrate(md_ctx *c, int64_t nsteps) {
   const double h = c->dt, B0 = k[0], B1 = k[1], D0 = k[2], D1 = k[3];
   int rc;
   if (c->model == MD_HMF) {
-    for (int64_t s = 0; s < nsteps; s++) {
-      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, (s == 0 ? B0 : 2.0 * B0) * h, D0 * h, nullptr))) return rc;
-      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D1 * h, nullptr))) return rc;
-      if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
-    }
-    return hmf_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, nullptr);
-  }
-  const bool cached = c->fsal_valid && c->fsal_prec == c->prec && c->mirror_valid && c->mirror_prec == c->prec;
-  c->fsal_valid = false;
-  for (int64_t s = 0; s < nsteps; s++) {
-    if (s == 0 && cached)
-      rc = kick_drift_cached(c, B0 * h, D0 * h);
-    else
-      rc = pair_stage(c, STAGE_KICK_DRIFT, (s == 0 ? B0 : 2.0 * B0) * h, D0 * h, nullptr);
+    if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B0 * h, D0 * h, nullptr))) return rc;
+    if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D1 * h, nullptr))) return rc;
+    if ((rc = hmf_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
+  } else {
+    const bool cached = c->fsal_valid && c->fsal_prec == c->prec && c->mirror_valid && c->mirror_prec == c->prec;
+    c->fsal_valid = false;
+    rc = cached ? kick_drift_cached(c, B0 * h, D0 * h) : pair_stage(c, STAGE_KICK_DRIFT, B0 * h, D0 * h, nullptr);
     if (rc) return rc;
     if ((rc = pair_stage(c, STAGE_KICK_DRIFT, B1 * h, D1 * h, nullptr))) return rc;
     if ((rc = pair_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
   }
+  int64_t rest = nsteps - 1;
+  for (; c->use_graphs && rest >= kStepGraphSteps; rest -= kStepGraphSteps)
+    if ((rc = replay_steps(c, k, h))) return rc;
+  for (; rest > 0; rest--)
+    if ((rc = middle_step(c, k, h))) return rc;
+  if (c->model == MD_HMF) return hmf_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, nullptr);
   if ((rc = pair_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, c->f))) return rc;
   c->fsal_valid = true;
   c->fsal_prec = c->prec;

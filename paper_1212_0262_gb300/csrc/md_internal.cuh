@@ -21,7 +21,8 @@ struct PairTuning {
   int r_fp64 = 2;     // i-particles per thread, FP64 pair path
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
   int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
-  int ring_tc = 0;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
+  int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
+  int symmetric = 1;  // FP32 forward stages: each unordered pair once (Newton's third law)
   int ctas_per_sm = 0;  // 0: occupancy-derived
 };
 
@@ -30,6 +31,19 @@ struct HmfTuning {
 };
 
 // ----------------------------------------------------------------- context --
+
+// Everything the launches of a captured block of md_step's steps depend on,
+// besides the ping-pong parity (one graph per parity).  Compared bytewise.
+struct StepGraphKey {
+  int model, prec;
+  int64_t N;
+  double h, eps;
+  void *stream;
+  PairTuning pt;
+  HmfTuning ht;
+  int mirror_fmt;
+  const void *bufs[13];
+};
 
 struct md_ctx {
   int model = 0, dim = 1, prec = MD_FP64;
@@ -64,6 +78,12 @@ struct md_ctx {
   size_t sk_slots_bytes = 0;
   unsigned *sk_tickets = nullptr;
   size_t sk_tickets_count = 0;
+  double *sym_rowfull = nullptr;  // Newton's-third-law variant: row partials of whole rows
+  size_t sym_rowfull_bytes = 0;
+  float *sym_colslot = nullptr;   // and column partials per unit
+  size_t sym_colslot_bytes = 0;
+  double *sym_chunks = nullptr;   // and chunk sums of the column partials
+  size_t sym_chunk_bytes = 0;
 
   // reductions (energies)
   double *red = nullptr;
@@ -77,6 +97,12 @@ struct md_ctx {
   HmfTuning ht;
   int64_t launches = 0;
   std::string err;
+
+  // md_step: steps 2.. replayed from CUDA graphs of kStepGraphSteps steps, one per parity
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  StepGraphKey step_key[2];
+  int64_t step_graph_launches[2] = {0, 0};
+  bool use_graphs = true;
 };
 
 // ------------------------------------------------------------ host helpers --
@@ -96,6 +122,8 @@ void dev_free(void *p);
     cudaError_t e_ = cudaGetLastError();                                      \
     if (e_ != cudaSuccess) return cuda_err((ctx), e_, "kernel launch");       \
   } while (0)
+
+void destroy_step_graphs(md_ctx *c);
 
 // Yoshida coefficients of Eq. 4 (B0, B1, D0, D1), from the triple-jump closed form.
 void yoshida_coefficients(double c[4]);
@@ -145,6 +173,11 @@ int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2);
 int mirror_refresh(md_ctx *c);                                    // mirror[mirror_cur] from q
 int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
 int kick_drift_cached(md_ctx *c, double kick, double drift);      // first stage from the cached force
+int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc);       // stream-K slots and tickets
+
+// sym.cu (Newton's-third-law variant of the FP32 forward stages)
+bool sym_applies(const md_ctx *c);
+int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
 
 // energy.cu
 int kinetic_fp64(md_ctx *c, double *d_out);                       // (1/2) sum p^2 into device out

@@ -201,31 +201,6 @@ bool ring_tc(const md_ctx *c) { return c->model == MD_RING && c->prec == MD_MIXE
 
 int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadMultiple; }
 
-int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc) {
-  size_t need_slots = (size_t)P * 2 * nacc * TI * sizeof(double);
-  if (need_slots > c->sk_slots_bytes) {
-    dev_free(c->sk_slots);
-    c->sk_slots = (double *)dev_alloc(need_slots);
-    if (!c->sk_slots) {
-      c->sk_slots_bytes = 0;
-      return set_err(c, MD_ENOMEM, "stream-K slots: %zu bytes", need_slots);
-    }
-    c->sk_slots_bytes = need_slots;
-  }
-  size_t n_it = (size_t)((c->N + TI - 1) / TI);
-  if (n_it > c->sk_tickets_count) {
-    dev_free(c->sk_tickets);
-    c->sk_tickets = (unsigned *)dev_alloc(n_it * sizeof(unsigned));
-    if (!c->sk_tickets) {
-      c->sk_tickets_count = 0;
-      return set_err(c, MD_ENOMEM, "stream-K tickets");
-    }
-    c->sk_tickets_count = n_it;
-    MD_CUDA(c, cudaMemsetAsync(c->sk_tickets, 0, n_it * sizeof(unsigned), c->stream));
-  }
-  return MD_OK;
-}
-
 int ensure_mirrors(md_ctx *c, bool adj) {
   const int64_t Np = padded(c->N);
   // the FP64 record bounds the FP32 one
@@ -334,6 +309,31 @@ int refresh(md_ctx *c, const double *lp) {
 
 }  // namespace
 
+int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc) {
+  size_t need_slots = (size_t)P * 2 * nacc * TI * sizeof(double);
+  if (need_slots > c->sk_slots_bytes) {
+    dev_free(c->sk_slots);
+    c->sk_slots = (double *)dev_alloc(need_slots);
+    if (!c->sk_slots) {
+      c->sk_slots_bytes = 0;
+      return set_err(c, MD_ENOMEM, "stream-K slots: %zu bytes", need_slots);
+    }
+    c->sk_slots_bytes = need_slots;
+  }
+  size_t n_it = (size_t)((c->N + TI - 1) / TI);
+  if (n_it > c->sk_tickets_count) {
+    dev_free(c->sk_tickets);
+    c->sk_tickets = (unsigned *)dev_alloc(n_it * sizeof(unsigned));
+    if (!c->sk_tickets) {
+      c->sk_tickets_count = 0;
+      return set_err(c, MD_ENOMEM, "stream-K tickets");
+    }
+    c->sk_tickets_count = n_it;
+    MD_CUDA(c, cudaMemsetAsync(c->sk_tickets, 0, n_it * sizeof(unsigned), c->stream));
+  }
+  return MD_OK;
+}
+
 int mirror_refresh(md_ctx *c) {
   int rc = refresh<false>(c, nullptr);
   if (rc) return rc;
@@ -353,6 +353,7 @@ int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
     int rc = mirror_refresh(c);
     if (rc) return rc;
   }
+  if (sym_applies(c)) return sym_pair_stage(c, mode, kick, drift, fout);
   PairArgs a{};
   a.kick = kick;
   a.drift = drift;
@@ -417,4 +418,13 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
   MD_LAUNCHED(c);
   c->mirror_cur = 1 - c->mirror_cur;
   return MD_OK;
+}
+
+extern "C" int md_force_kernel(const md_ctx *c) {
+  if (!c) return -1;
+  if (c->model == MD_HMF) return MD_KERNEL_HMF;
+  if (c->prec != MD_MIXED) return MD_KERNEL_PAIRS_FP64;
+  const bool tc = ring_tc(c) && c->pt.r_mixed != 4;
+  if (sym_applies(c)) return tc ? MD_KERNEL_PAIRS_TC_SYM : MD_KERNEL_PAIRS_SYM;
+  return tc ? MD_KERNEL_PAIRS_TC : MD_KERNEL_PAIRS;
 }

@@ -71,6 +71,26 @@ __device__ __forceinline__ void csum_add2(CompSum &c, float2 x) {
 }
 __device__ __forceinline__ double csum_total(const CompSum &c) { return (double)c.hi + (double)c.lo; }
 
+// Reduce-scatter of V values per lane over the lanes spanned by the xor masks
+// MASK0, MASK0/2, ..., MASK0*2/V: each round halves the values a lane keeps
+// (lanes with the mask bit set keep the upper half) and adds the partner's copy
+// of them.  Returns the sum over those lanes of value number
+// sum_r (bit MASK_r of the lane ? V/2^(r+1) : 0).
+template <int V, int MASK0>
+__device__ __forceinline__ float butterfly_sum(float (&v)[V], int lane) {
+#pragma unroll
+  for (int h = V / 2, mask = MASK0; h >= 1; h /= 2, mask /= 2) {
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int i = 0; i < h; i++) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+  }
+  return v[0];
+}
+
 // ============================================================ records ======
 
 // Mirror record of particle i at FP64 position(s) (x, y) and, for adjoint
@@ -297,6 +317,55 @@ struct GravMixed {
       for (int k0 = 0; k0 < TJ / 2; k0 += OFF) {
 #pragma unroll
         for (int kk = 0; kk < OFF; kk++) body(k0 + kk, kk == OFF - 1);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      csum_add2(st.cs[r][0], st.fx[r]);
+      csum_add2(st.cs[r][1], st.fy[r]);
+      st.fx[r] = st.fy[r] = f2(0.f);
+    }
+  }
+  // Off-diagonal block of the Newton's-third-law variant: the i-rows as in tile<>,
+  // and for every j the sum over this warp's 32 R rows of the same terms
+  // r_ij / s_ij, into colsm[(warp TJ + j) 2 + component] (the j-side term is
+  // minus that sum).  Eight j's at a time: per lane 16 partial sums (4 j-pairs x
+  // 2 components), reduced over the warp by a butterfly.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    static_assert(OFF == 0, "the symmetric variant keeps every reciprocal on the SFU");
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k8 = 0; k8 < TJ / 8; k8++) {
+      float v[16];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const float4 X = sm[4 * k8 + kk];
+        const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
+        float2 cx = f2(0.f), cy = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          float2 dx = __fadd2_rn(st.x[r], nx);
+          float2 dy = __fadd2_rn(st.y[r], ny);
+          float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+          float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+          st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
+          st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+          cx = __ffma2_rn(dx, inv, cx);
+          cy = __ffma2_rn(dy, inv, cy);
+        }
+        v[4 * kk + 0] = cx.x;
+        v[4 * kk + 1] = cx.y;
+        v[4 * kk + 2] = cy.x;
+        v[4 * kk + 3] = cy.y;
+      }
+      float sum = butterfly_sum<16, 16>(v, lane);  // over lane bits 4..1
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      if ((lane & 1) == 0) {
+        const int vi = lane >> 1;  // value number: 4 kk + 2 component + (j parity)
+        const int j = 8 * k8 + 2 * (vi >> 2) + (vi & 1);
+        colsm[(w * TJ + j) * 2 + ((vi >> 1) & 1)] = sum;
       }
     }
 #pragma unroll
@@ -784,6 +853,59 @@ struct RingTC {
           st.acc[r][h] = __ffma2_rn(qq, __fmul2_rn(y, y), st.acc[r][h]);
         }
       }
+    }
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        csum_add2(st.cs[r][h], st.acc[r][h]);
+        st.acc[r][h] = f2(0.f);
+      }
+  }
+  // Off-diagonal block of the Newton's-third-law variant: the i-rows as in tile<>,
+  // and for every j the sum over this warp's 16 RM rows of the same terms
+  // S dd^(-3/2), into colsm[warp TJ + j] (the j-side term is minus that sum, as
+  // sin(theta_j - theta_i) = -sin(theta_i - theta_j)).  Per lane and n-block the
+  // two columns 2t, 2t+1 are summed over the lane's rows; four n-blocks at a
+  // time are then reduced over the 8 lanes g by a butterfly.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    const float *sm = (const float *)smb;
+    const float2 he = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, t = lane & 3, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k4 = 0; k4 < TJ / 32; k4++) {
+      float v[8];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const int k = 4 * k4 + kk;
+        const float2 bs = *(const float2 *)(sm + k * 128 + lane * 2);
+        const float2 bh = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
+        const unsigned bs0 = __float_as_uint(bs.x), bs1 = __float_as_uint(bs.y);
+        const unsigned bh0 = __float_as_uint(bh.x), bh1 = __float_as_uint(bh.y);
+        float2 col = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < RM; r++) {
+          float dS[4], dH[4];
+          mma_tf32(dS, st.aS[r], bs0, bs1);
+          mma_tf32(dH, st.aH[r], bh0, bh1);
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const float2 S = make_float2(dS[2 * h], dS[2 * h + 1]);
+            const float2 sh = make_float2(dH[2 * h], dH[2 * h + 1]);
+            const float2 d = __ffma2_rn(sh, sh, he);
+            const float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+            const float2 qq = __fmul2_rn(S, y);
+            const float2 y2 = __fmul2_rn(y, y);
+            st.acc[r][h] = __ffma2_rn(qq, y2, st.acc[r][h]);
+            col = __ffma2_rn(qq, y2, col);
+          }
+        }
+        v[2 * kk] = col.x;
+        v[2 * kk + 1] = col.y;
+      }
+      // lane (g, t) ends with n-block 4 k4 + (g >> 1), column 2t + (g & 1)
+      const float sum = butterfly_sum<8, 16>(v, lane);
+      colsm[w * TJ + 8 * (4 * k4 + (lane >> 3)) + 2 * t + ((lane >> 2) & 1)] = sum;
     }
 #pragma unroll
     for (int r = 0; r < RM; r++)

@@ -96,6 +96,11 @@ class System:
     def set_tuning(self, key: str, value: int) -> None:
         self._chk(B.load().md_set_tuning(self._h, key.encode(), int(value)))
 
+    @property
+    def force_kernel(self) -> int:
+        """MD_KERNEL_* code of the force kernel the next stage runs."""
+        return int(B.load().md_force_kernel(self._h))
+
     def set_stream(self, stream) -> None:
         """A cudaStream_t as int, or a torch.cuda.Stream."""
         handle = getattr(stream, "cuda_stream", stream)

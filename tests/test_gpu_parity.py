@@ -66,11 +66,25 @@ def test_fp64_force_parity(model, N):
         assert np.all(f == 0.0)
 
 
+# FP32 pair-kernel variants: (ring_tc, symmetric); the default is (1, 1)
+VARIANTS = {"default": None, "one_sided_cuda_cores": (0, 0), "one_sided_tensor_cores": (1, 0)}
+
+
+def _variant(s, name):
+    if VARIANTS[name] is not None:
+        s.set_tuning("ring_tc", VARIANTS[name][0])
+        s.set_tuning("symmetric", VARIANTS[name][1])
+    return s
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("N", SIZES)
 @pytest.mark.parametrize("model", [0, 1, 2])
-def test_mixed_force_error_bound(model, N):
+def test_mixed_force_error_bound(model, N, variant):
+    if model == 0 and variant != "default":
+        pytest.skip("HMF has no pair kernel")
     s, q, p = _sys(model, N, "mixed")
-    f = s.force()
+    f = _variant(s, variant).force()
     err, scale, _ = _force_err(model, q, f)
     assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
 
@@ -164,12 +178,16 @@ def test_mixed_energy_error_within_twice_fp64():
 
 # ------------------------------------------------ full-size sampled checks --
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "mixed_one_sided"])
 @pytest.mark.parametrize("model,N,eps", [(0, 50_000_000, 0.0), (1, 131072, 0.01), (2, 262144, 1e-4)])
 def test_full_size_sampled_force_parity(model, N, eps, prec):
     """Bench-size systems in the bench's launch configuration: forces on 64
     sampled particles against the oracle's direct sums."""
-    s = System(model, N, eps, 0.05, 42 + model, precision=prec)
+    if model == 0 and prec == "mixed_one_sided":
+        pytest.skip("HMF has no pair kernel")
+    s = System(model, N, eps, 0.05, 42 + model, precision=prec.split("_")[0])
+    if prec == "mixed_one_sided":
+        _variant(s, "one_sided_cuda_cores")
     q, _ = s.get_state()
     f = s.force().reshape(2 if model == 2 else 1, N)
     rows = np.unique(np.concatenate([[0, N - 1], inputs.splitmix64(9, np.arange(62)) % np.uint64(N)]).astype(np.int64))
@@ -196,6 +214,7 @@ def test_ring_tensor_core_force_error_bound(N, tc):
     """Ring FP32 path with sin(d) and sin(d/2) from split-TF32 tensor-core MMAs."""
     s, q, p = _sys(1, N, "mixed")
     s.set_tuning("ring_tc", tc)
+    s.set_tuning("symmetric", 0)
     f = s.force()
     err, scale, _ = _force_err(1, q, f)
     assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
@@ -211,6 +230,7 @@ def test_ring_tensor_core_steps_match_fp32_kernel(tc):
     ref, q0, p0 = _sys(1, N, "fp64", dt=dt)
     tcs, _, _ = _sys(1, N, "mixed", dt=dt)
     tcs.set_tuning("ring_tc", tc)
+    tcs.set_tuning("symmetric", 0)
     e0 = sum(ref.energy())
     ref.step(10)
     tcs.step(10)
@@ -219,3 +239,27 @@ def test_ring_tensor_core_steps_match_fp32_kernel(tc):
     d_ref = abs(sum(ref.energy()) - e0) / abs(e0)
     d_tc = abs(sum(tcs.energy()) - e0) / abs(e0)
     assert d_tc <= 2 * d_ref + 1e-9, (d_tc, d_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_step_graphs_match_stage_by_stage(model, prec):
+    """md_step replays its steps 2.. from captured CUDA graphs (blocks of 8); the
+    result is bitwise that of the same stage schedule launched one md_stage at a
+    time, for both ping-pong parities (odd step counts alternate them between
+    calls).  md_step launches no more kernels than the stage-by-stage run (its
+    first stage reuses the cached force of the previous call)."""
+    from paper_1212_0262_gb300.system import stage_schedule
+
+    N = 3000
+    a, _, _ = _sys(model, N, prec)
+    b, _, _ = _sys(model, N, prec)
+    la, lb = a.launch_count, b.launch_count
+    for n in (17, 17, 9, 25, 1):
+        a.step(n)
+        for bb, dd in stage_schedule(n):
+            b.stage(bb, dd)
+        qa, pa = a.get_state()
+        qb, pb = b.get_state()
+        assert np.array_equal(qa, qb) and np.array_equal(pa, pb), n
+    assert a.launch_count - la <= b.launch_count - lb
