@@ -242,13 +242,19 @@ void md_batch_free(md_batch *b);
 int md_batch_set_precision(md_batch *b, int precision);
 int md_batch_set_stream(md_batch *b, void *stream);
 /* Advance every system by nsteps steps of Sec. 3 (asynchronous).  Three fused
- * force + kick + drift launches per step cover all systems; blocks of steps are
- * replayed from a captured CUDA graph. */
+ * force + kick + drift stages per step cover all systems (one launch per stage,
+ * two in the Newton's-third-law form: pair phase and finish phase); blocks of
+ * steps are replayed from a captured CUDA graph. */
 int md_batch_step(md_batch *b, int64_t nsteps);
-/* Kernel shape of the batched launches: r i-particles per thread (4 or 8),
- * fraction `split` (0, 1) of the CTAs given to the Ring systems, CTAs per SM
- * (0 = occupancy limit). */
+/* Kernel shape of the batched launches: r = 0 (default) runs the mixed-precision
+ * Newton's-third-law kernels (every unordered pair of a system once; tensor-core
+ * Ring products), r = 4 or 8 the one-sided kernels with r i-particles per thread
+ * (FP64 ensembles always run the one-sided FP64 kernel); fraction `split` (0, 1)
+ * of the CTAs given to the Ring systems; CTAs per SM (0 = occupancy limit). */
 int md_batch_set_tuning(md_batch *b, int r, double split, int ctas_per_sm);
+/* The current shape (after md_batch_autotune: the one it picked); NULL outputs
+ * are skipped. */
+int md_batch_get_tuning(const md_batch *b, int *r, double *split, int *ctas_per_sm);
 /* Time candidate shapes (r, split, CTAs per SM) on force-only launches, which
  * leave every state unchanged, and keep the fastest.  *best_ms (may be NULL)
  * receives the fastest launch time.  Synchronous. */

@@ -258,6 +258,7 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   else if (k == "rcp_offload" && (value == 0 || value == 8)) c->pt.rcp_off = (int)value;
   else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
   else if (k == "symmetric" && (value == 0 || value == 1)) c->pt.symmetric = (int)value;
+  else if (k == "sym_threads" && (value == 128 || value == 256 || value == 768)) c->pt.sym_threads = (int)value;
   else if (k == "step_graphs" && (value == 0 || value == 1)) c->use_graphs = value != 0;
   else return set_err(c, MD_EINVAL, "unknown tuning key or value: %s=%lld", key, (long long)value);
   return MD_OK;
@@ -356,6 +357,20 @@ StepGraphKey step_key_of(const md_ctx *c, double h) {
 
 int parity_of(const md_ctx *c) { return c->model == MD_HMF ? c->hmf_cur : c->mirror_cur; }
 
+// Graphs are captured only on a stream of our own choosing that is not already
+// being captured: the legacy and per-thread default streams cannot be captured,
+// and inside a caller's capture the stages are simply recorded into it.
+bool graphs_usable(md_ctx *c) {
+  if (!c->use_graphs || c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+    return false;
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st == cudaStreamCaptureStatusNone;
+}
+
 // kStepGraphSteps middle steps from the graph of the current parity, captured on
 // first use and again whenever anything the launches depend on has changed.
 // Every kernel it holds has already run once in this call (the first step), so
@@ -426,8 +441,9 @@ int integrate(md_ctx *c, int64_t nsteps) {
     if ((rc = pair_stage(c, STAGE_KICK_DRIFT, B1 * h, D0 * h, nullptr))) return rc;
   }
   int64_t rest = nsteps - 1;
-  for (; c->use_graphs && rest >= kStepGraphSteps; rest -= kStepGraphSteps)
-    if ((rc = replay_steps(c, k, h))) return rc;
+  if (rest >= kStepGraphSteps && graphs_usable(c))
+    for (; rest >= kStepGraphSteps; rest -= kStepGraphSteps)
+      if ((rc = replay_steps(c, k, h))) return rc;
   for (; rest > 0; rest--)
     if ((rc = middle_step(c, k, h))) return rc;
   if (c->model == MD_HMF) return hmf_stage(c, STAGE_KICK_ONLY, B0 * h, 0.0, nullptr);

@@ -11,6 +11,14 @@
 // the CTAs per SM are chosen by md_batch_autotune, which times candidate
 // configurations on force-only launches (state untouched).  md_batch_step
 // replays a CUDA graph holding a block of steps.
+//
+// Mixed precision runs, by default, the Newton's-third-law form of each part
+// (every unordered pair of a system once, as the single-system stages in
+// sym.cu): a pair launch whose parts walk the triangular (system, i-tile,
+// j-tile) units of their systems stream-K style and write row and column
+// partials, then a finish launch with one CTA per (system, tile, chunk of 16
+// column-partial rows) that sums them in a fixed order and runs the epilogue.
+#include <algorithm>
 #include <vector>
 
 #include "pairs_impl.cuh"
@@ -25,6 +33,8 @@ struct SysDesc {
   int64_t N, n_it, n_jt;
   int64_t ubeg;  // first unit of the system in its part
   int64_t rbeg;  // first row (i-tile) of the system in its part
+  int64_t fbeg;  // symmetric form: first finish CTA of the system in its part
+  int nc;        // symmetric form: chunk slots per tile
   double epsd, dt;
 };
 
@@ -37,6 +47,12 @@ struct PartArgs {
   double b, d;
   double *slots;
   unsigned *tickets;
+  // symmetric form
+  int m;             // TI / TJ of the part
+  int64_t nfin;      // finish CTAs of the part
+  double *rowfull;   // [rows][NACC][TI]
+  float *colslot;    // [U][TJ][NACC]
+  double *chunks;    // [nfin][TI][NACC]
 };
 
 // index of the system whose unit range holds u (binary search on ubeg)
@@ -204,8 +220,207 @@ __global__ void __launch_bounds__(NT) batch_kernel(PartArgs ring, PartArgs grav)
     batch_part<PolG, MD_GRAV2D, MIXED, MODE>(grav, (int64_t)blockIdx.x - ring.P);
 }
 
+// ------------------------------------------------- Newton's-third-law form --
+
+constexpr int kSymChunkB = 16;     // column-partial rows per finish CTA
+constexpr int kFinishThreadsB = 256;
+
+// (system, local row) of part-local unit u in the triangular layout
+__device__ __forceinline__ void sym_locate(const PartArgs &A, int64_t u, int &s, int64_t &it, int64_t &jt) {
+  s = sys_of_unit(A, u);
+  const SysDesc &S = A.sys[s];
+  const int64_t lu = u - S.ubeg;
+  it = sym_row_of_unit(lu, S.n_it, S.n_jt, A.m);
+  jt = (int64_t)A.m * it + (lu - sym_rowstart(it, S.n_jt, A.m));
+}
+
+// Pair phase of one part: the part's CTAs walk its triangular units (systems
+// one after the other), write the row partials of the rows they cover and the
+// column partial of every off-diagonal unit.  smem: the j-tile double buffer,
+// then the per-warp column sums.
+template <class Pol>
+__device__ __noinline__ void batch_sym_pairs(const PartArgs &A, int64_t cta, unsigned char *smem) {
+  constexpr int TJ = Pol::TJ, NACC = Pol::NACC, NW = NT / 32;
+  constexpr int TILE_BYTES = TJ * Pol::JB;
+  constexpr int CHUNKS = TILE_BYTES / 16;
+  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  unsigned char *sbuf0 = smem, *sbuf1 = smem + TILE_BYTES;
+  float *colsm = (float *)(smem + 2 * TILE_BYTES);
+  const int64_t u0 = unit_begin(A.U, A.P, cta), u1 = unit_begin(A.U, A.P, cta + 1);
+  if (u0 >= u1) return;
+  const int m = A.m;
+  int s;
+  int64_t it, jt;
+  sym_locate(A, u0, s, it, jt);
+  const int64_t first_row = A.sys[s].rbeg + it;
+  bool row_from_start = (jt == (int64_t)m * it);
+  auto prefetch = [&](unsigned char *buf, int sp, int64_t jtp) {
+    const unsigned char *src = A.sys[sp].mir[A.cur] + jtp * (int64_t)TILE_BYTES;
+    for (int ch = threadIdx.x; ch < CHUNKS; ch += NT) cp_async16(buf + ch * 16, src + ch * 16);
+    cp_async_commit();
+  };
+  typename Pol::State st;
+  PairArgs v = view(A, A.sys[s]);
+  int64_t i0 = it * TI;
+  Pol::load(st, v.mirror_in, i0);
+  prefetch(sbuf0, s, jt);
+  for (int64_t u = u0; u < u1; u++) {
+    unsigned char *buf = ((u - u0) & 1) ? sbuf1 : sbuf0;
+    const SysDesc &S = A.sys[s];
+    const bool row_end = (jt + 1 == S.n_jt);
+    const bool sys_end = row_end && (it + 1 == S.n_it);
+    const int s_next = sys_end ? s + 1 : s;
+    const int64_t jt_next = sys_end ? 0 : row_end ? (int64_t)m * (it + 1) : jt + 1;
+    if (u + 1 < u1) {
+      prefetch(((u - u0) & 1) ? sbuf0 : sbuf1, s_next, jt_next);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const bool diag = jt < (int64_t)m * (it + 1);
+    if (diag) Pol::template tile<true>(st, buf, v, i0, jt * TJ);
+    else Pol::tile_sym(st, buf, v, colsm);
+    __syncthreads();
+    if (!diag) {
+      float *dst = A.colslot + u * (int64_t)(TJ * NACC);
+      for (int idx = threadIdx.x; idx < TJ * NACC; idx += NT) {
+        float x = colsm[idx];
+#pragma unroll
+        for (int w = 1; w < NW; w++) x += colsm[w * TJ * NACC + idx];
+        dst[idx] = x;
+      }
+    }
+    if (row_end || u + 1 == u1) {
+      const int64_t row = S.rbeg + it;
+      double *sp = (row_end && row_from_start) ? A.rowfull + row * NACC * TI
+                                               : A.slots + ((cta * 2 + (row == first_row ? 0 : 1)) * NACC) * TI;
+#pragma unroll
+      for (int r = 0; r < Pol::NR; r++) {
+        double ex[NACC];
+        Pol::total(st, r, ex);
+        const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+        if (lr >= 0)
+#pragma unroll
+          for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
+      }
+      if (row_end && u + 1 < u1) {
+        row_from_start = true;
+        if (sys_end) {
+          s++;
+          it = 0;
+          v = view(A, A.sys[s]);
+        } else {
+          it++;
+        }
+        i0 = it * TI;
+        Pol::load(st, v.mirror_in, i0);
+      }
+    }
+    jt = jt_next;
+  }
+}
+
+// index of the system whose finish-CTA range holds f (binary search on fbeg)
+__device__ __forceinline__ int sys_of_fin(const PartArgs &A, int64_t f) {
+  int lo = 0, hi = A.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (A.sys[mid].fbeg <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Finish phase of one part, CTA f: chunk c of tile T of system s (as in sym.cu).
+template <class Pol, int MODEL, int MODE>
+__device__ __noinline__ void batch_sym_finish(const PartArgs &A, int64_t f) {
+  constexpr int NACC = Pol::NACC, TJ = Pol::TJ;
+  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  constexpr int OUT = (int)TI * NACC;
+  __shared__ bool s_last;
+  const int s = sys_of_fin(A, f);
+  const SysDesc &S = A.sys[s];
+  const int64_t lf = f - S.fbeg, T = lf / S.nc;
+  const int c = (int)(lf % S.nc);
+  const int nch = T == 0 ? 1 : (int)((T + kSymChunkB - 1) / kSymChunkB);
+  if (c >= nch) return;
+  const int m = A.m;
+  const int64_t I_lo = (int64_t)c * kSymChunkB, I_hi = min(T, I_lo + kSymChunkB);
+  double *chunk = A.chunks + (S.fbeg + T * S.nc) * OUT;
+  for (int o = threadIdx.x; o < OUT; o += kFinishThreadsB) {
+    const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);
+    CompSum cs{0.f, 0.f};
+#pragma unroll 8
+    for (int64_t I2 = I_lo; I2 < I_hi; I2++) {
+      const int64_t u = S.ubeg + sym_rowstart(I2, S.n_jt, m) + (T * m + jsub - (int64_t)m * I2);
+      csum_add(cs, __ldcg(A.colslot + u * (TJ * NACC) + rest));
+    }
+    chunk[(int64_t)c * OUT + o] = csum_total(cs);
+  }
+  __threadfence();
+  __syncthreads();
+  const int64_t row = S.rbeg + T;
+  if (threadIdx.x == 0) s_last = atomicAdd(&A.tickets[row], 1u) + 1u == (unsigned)nch;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int64_t cf = cta_of_unit(A.U, A.P, S.ubeg + sym_rowstart(T, S.n_jt, m));
+  const int64_t cl = cta_of_unit(A.U, A.P, S.ubeg + sym_rowstart(T + 1, S.n_jt, m) - 1);
+  const PairArgs v = view(A, S);
+  for (int lr = threadIdx.x; lr < TI; lr += kFinishThreadsB) {
+    const int64_t i = T * TI + lr;
+    if (i >= S.N) break;
+    double tot[NACC];
+    if (cf == cl) {
+#pragma unroll
+      for (int d = 0; d < NACC; d++) tot[d] = __ldcg(A.rowfull + (row * NACC + d) * TI + lr);
+    } else {
+#pragma unroll
+      for (int d = 0; d < NACC; d++) tot[d] = 0.0;
+      for (int64_t c2 = cf; c2 <= cl; c2++) {
+        int s2;
+        int64_t it2, jt2;
+        sym_locate(A, unit_begin(A.U, A.P, c2), s2, it2, jt2);
+        const double *src = A.slots + ((c2 * 2 + (row == A.sys[s2].rbeg + it2 ? 0 : 1)) * NACC) * TI;
+#pragma unroll
+        for (int d = 0; d < NACC; d++) tot[d] += __ldcg(src + d * TI + lr);
+      }
+    }
+    for (int c2 = 0; c2 < nch; c2++)
+#pragma unroll
+      for (int d = 0; d < NACC; d++) tot[d] -= __ldcg(chunk + (int64_t)c2 * OUT + lr * NACC + d);
+    finish<Pol, MODEL, true, MODE>(v, i, tot);
+  }
+  if (threadIdx.x == 0) A.tickets[row] = 0u;
+}
+
+template <class Pol>
+constexpr int sym_smem_bytes() {
+  return 2 * Pol::TJ * Pol::JB + (NT / 32) * Pol::TJ * Pol::NACC * 4;
+}
+
+template <class PolR, class PolG>
+__global__ void __launch_bounds__(NT) batch_sym_pairs_kernel(PartArgs ring, PartArgs grav) {
+  constexpr int BYTES = sym_smem_bytes<PolR>() > sym_smem_bytes<PolG>() ? sym_smem_bytes<PolR>() : sym_smem_bytes<PolG>();
+  __shared__ __align__(16) unsigned char smem[BYTES];
+  if ((int)blockIdx.x < ring.P)
+    batch_sym_pairs<PolR>(ring, blockIdx.x, smem);
+  else
+    batch_sym_pairs<PolG>(grav, (int64_t)blockIdx.x - ring.P, smem);
+}
+
+template <class PolR, class PolG, int MODE>
+__global__ void __launch_bounds__(kFinishThreadsB) batch_sym_finish_kernel(PartArgs ring, PartArgs grav) {
+  if ((int64_t)blockIdx.x < ring.nfin)
+    batch_sym_finish<PolR, MD_RING, MODE>(ring, blockIdx.x);
+  else
+    batch_sym_finish<PolG, MD_GRAV2D, MODE>(grav, (int64_t)blockIdx.x - ring.nfin);
+}
+
 struct Config {
-  int r = 8;            // i-particles per thread (mixed: 4 or 8; FP64: 2)
+  int r = 0;            // i-particles per thread of the one-sided kernels (mixed: 4 or 8;
+                        // FP64: 2); 0: Newton's-third-law kernels (mixed only)
   double split = 0.5;   // fraction of CTAs given to the Ring part
   int ctas_per_sm = 0;  // 0: occupancy limit
 };
@@ -229,10 +444,18 @@ struct md_batch {
   size_t tickets_count = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_key[2] = {-1, -1};
-  // unit / row layout uploaded for tile shape (layout_ti, layout_tj)
-  int64_t layout_ti = -1, layout_tj = -1;
-  int64_t Ur = 0, Ug = 0, rows_r = 0, rows_g = 0;
+  int64_t graph_launches[2] = {0, 0};
+  // unit / row layout uploaded for tile shapes and form (layout_key)
+  int64_t layout_key[5] = {-1, -1, -1, -1, -1};
+  int64_t Ur = 0, Ug = 0, rows_r = 0, rows_g = 0, nfin_r = 0, nfin_g = 0;
   int nr = 0;
+  int mirror_sym = -1;  // form the mirrors were written for (Ring records differ)
+  double *rowfull = nullptr;  // Newton's-third-law form: row partials, column partials, chunk sums
+  size_t rowfull_bytes = 0;
+  float *colslot = nullptr;
+  size_t colslot_bytes = 0;
+  double *chunks = nullptr;
+  size_t chunks_bytes = 0;
   std::vector<std::pair<const void *, int>> occ_cache;  // occupancy per kernel, queried outside captures
   int64_t launches = 0;
   std::string err;
@@ -262,14 +485,16 @@ void drop_graphs(md_batch *b) {
   }
 }
 
-// Descriptors and the unit / row layout of both parts for tile sizes (TI, TJ).
-int build_layout(md_batch *b, int64_t TI, int64_t TJ, std::vector<SysDesc> &hs, int64_t &Ur, int64_t &Ug,
-                 int64_t &rows_r, int64_t &rows_g, int &nr) {
+// Descriptors and the unit / row layout of both parts: tile sizes (TI, TJ) per
+// part, and the one-sided (rectangular unit table) or symmetric (triangular,
+// n_jt = m n_it) form.
+int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym, std::vector<SysDesc> &hs) {
   hs.clear();
-  Ur = Ug = rows_r = rows_g = 0;
-  nr = 0;
+  b->Ur = b->Ug = b->rows_r = b->rows_g = b->nfin_r = b->nfin_g = 0;
+  b->nr = 0;
   for (int pass = 0; pass < 2; pass++) {
     const int want = pass == 0 ? MD_RING : MD_GRAV2D;
+    const int64_t ti = TI[pass], tj = TJ[pass], m = ti / tj;
     for (int s = 0; s < b->nsys; s++) {
       if (b->model[s] != want) continue;
       md_ctx *c = b->ctx[s];
@@ -280,57 +505,86 @@ int build_layout(md_batch *b, int64_t TI, int64_t TJ, std::vector<SysDesc> &hs, 
       d.mir[0] = (const unsigned char *)c->mirror[0];
       d.mir[1] = (const unsigned char *)c->mirror[1];
       d.N = c->N;
-      d.n_it = (c->N + TI - 1) / TI;
-      d.n_jt = (c->N + TJ - 1) / TJ;
+      d.n_it = (c->N + ti - 1) / ti;
+      d.n_jt = sym ? m * d.n_it : (c->N + tj - 1) / tj;
       d.epsd = want == MD_RING ? 0.5 * c->eps : c->eps;
       d.dt = c->dt;
-      int64_t &U = pass == 0 ? Ur : Ug;
-      int64_t &rows = pass == 0 ? rows_r : rows_g;
+      d.nc = (int)std::max<int64_t>(1, (d.n_it - 1 + kSymChunkB - 1) / kSymChunkB);
+      int64_t &U = pass == 0 ? b->Ur : b->Ug;
+      int64_t &rows = pass == 0 ? b->rows_r : b->rows_g;
+      int64_t &nfin = pass == 0 ? b->nfin_r : b->nfin_g;
       d.ubeg = U;
       d.rbeg = rows;
-      U += d.n_it * d.n_jt;
+      d.fbeg = nfin;
+      U += sym ? sym_rowstart(d.n_it, d.n_jt, (int)m) : d.n_it * d.n_jt;
       rows += d.n_it;
+      nfin += d.n_it * d.nc;
       hs.push_back(d);
-      if (pass == 0) nr++;
+      if (pass == 0) b->nr++;
     }
   }
   return MD_OK;
 }
 
-template <class PolR, class PolG, bool MIXED, int MODE>
-int launch_batch(md_batch *b, double bc, double dc) {
-  constexpr int64_t TI = (int64_t)NT * PolR::R, TJ = PolR::TJ;
-  static_assert(PolR::R == PolG::R && PolR::TJ == PolG::TJ, "parts share the tile shape");
-  if (b->layout_ti != TI || b->layout_tj != TJ) {
-    // (re)build and upload the layout; never inside a stream capture, because the
-    // first step of md_batch_step and every autotune trial run uncaptured first
-    std::vector<SysDesc> hs;
-    build_layout(b, TI, TJ, hs, b->Ur, b->Ug, b->rows_r, b->rows_g, b->nr);
-    if (hs.size() > b->d_sys_count) {
-      dev_free(b->d_sys);
-      b->d_sys = (SysDesc *)dev_alloc(hs.size() * sizeof(SysDesc));
-      if (!b->d_sys) return berr(b, MD_ENOMEM, "%s", "batch descriptors");
-      b->d_sys_count = hs.size();
-    }
-    B_CUDA(b, cudaStreamSynchronize(b->stream));  // no launch may still read the old layout
-    B_CUDA(b, cudaMemcpy(b->d_sys, hs.data(), hs.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
-    b->layout_ti = TI;
-    b->layout_tj = TJ;
+// Upload the layout for (TI, TJ, form) unless it is the current one.  Never runs
+// inside a stream capture: the first step of md_batch_step and every autotune
+// trial run uncaptured first.
+int ensure_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym) {
+  const int64_t key[5] = {TI[0], TJ[0], TI[1], TJ[1], sym ? 1 : 0};
+  if (std::equal(key, key + 5, b->layout_key)) return MD_OK;
+  std::vector<SysDesc> hs;
+  build_layout(b, TI, TJ, sym, hs);
+  if (hs.size() > b->d_sys_count) {
+    dev_free(b->d_sys);
+    b->d_sys = (SysDesc *)dev_alloc(hs.size() * sizeof(SysDesc));
+    if (!b->d_sys) return berr(b, MD_ENOMEM, "%s", "batch descriptors");
+    b->d_sys_count = hs.size();
   }
-  const int64_t Ur = b->Ur, Ug = b->Ug, rows_r = b->rows_r, rows_g = b->rows_g;
-  const int nr = b->nr;
-  auto kern = batch_kernel<PolR, PolG, MIXED, MODE>;
+  B_CUDA(b, cudaStreamSynchronize(b->stream));  // no launch may still read the old layout
+  B_CUDA(b, cudaMemcpy(b->d_sys, hs.data(), hs.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
+  std::copy(key, key + 5, b->layout_key);
+  return MD_OK;
+}
+
+template <class T>
+int grow(md_batch *b, T *&ptr, size_t &have, size_t need, const char *what) {
+  if (need <= have) return MD_OK;
+  dev_free(ptr);
+  ptr = (T *)dev_alloc(need);
+  have = ptr ? need : 0;
+  return ptr ? MD_OK : berr(b, MD_ENOMEM, "%s", what);
+}
+
+int ensure_tickets(md_batch *b) {
+  const size_t nt = (size_t)(b->rows_r + b->rows_g);
+  if (nt > b->tickets_count) {
+    dev_free(b->tickets);
+    b->tickets = (unsigned *)dev_alloc(nt * sizeof(unsigned));
+    if (!b->tickets) return berr(b, MD_ENOMEM, "%s", "batch tickets");
+    b->tickets_count = nt;
+    B_CUDA(b, cudaMemsetAsync(b->tickets, 0, nt * sizeof(unsigned), b->stream));
+  }
+  return MD_OK;
+}
+
+int occupancy(md_batch *b, const void *kern) {
   int occ = 0;
   for (const auto &kv : b->occ_cache)
-    if (kv.first == (const void *)kern) occ = kv.second;
+    if (kv.first == kern) occ = kv.second;
   if (occ == 0) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
     if (occ < 1) occ = 1;
-    b->occ_cache.push_back({(const void *)kern, occ});
+    b->occ_cache.push_back({kern, occ});
   }
   if (b->cfg.ctas_per_sm > 0 && b->cfg.ctas_per_sm < occ) occ = b->cfg.ctas_per_sm;
-  const int64_t P = (int64_t)b->nsm * occ;
-  int64_t Pr = 0, Pg = 0;
+  return occ;
+}
+
+// CTAs of the Ring and 2D parts out of P, by the configured split
+void split_ctas(const md_batch *b, int64_t P, int64_t &Pr, int64_t &Pg) {
+  const int64_t Ur = b->Ur, Ug = b->Ug;
+  Pr = Pg = 0;
   if (Ur > 0 && Ug > 0) {
     Pr = (int64_t)(b->cfg.split * (double)P + 0.5);
     if (Pr < 1) Pr = 1;
@@ -343,31 +597,88 @@ int launch_batch(md_batch *b, double bc, double dc) {
   }
   if (Pr > Ur) Pr = Ur;
   if (Pg > Ug) Pg = Ug;
-  // device buffers: slots of both parts, tickets of both parts
-  const size_t slot_r = (size_t)Pr * 2 * PolR::NACC * TI, slot_g = (size_t)Pg * 2 * PolG::NACC * TI;
-  const size_t need = (slot_r + slot_g) * sizeof(double);
-  if (need > b->slots_bytes) {
-    dev_free(b->slots);
-    b->slots = (double *)dev_alloc(need);
-    if (!b->slots) return berr(b, MD_ENOMEM, "%s", "batch slots");
-    b->slots_bytes = need;
-  }
-  const size_t nt = (size_t)(rows_r + rows_g);
-  if (nt > b->tickets_count) {
-    dev_free(b->tickets);
-    b->tickets = (unsigned *)dev_alloc(nt * sizeof(unsigned));
-    if (!b->tickets) return berr(b, MD_ENOMEM, "%s", "batch tickets");
-    b->tickets_count = nt;
-    B_CUDA(b, cudaMemsetAsync(b->tickets, 0, nt * sizeof(unsigned), b->stream));
-  }
+}
+
+template <class PolR, class PolG, int MODE>
+int launch_batch_sym(md_batch *b, double bc, double dc) {
+  constexpr int64_t TIr = (int64_t)NT * PolR::R, TIg = (int64_t)NT * PolG::R;
+  constexpr int NAr = PolR::NACC, NAg = PolG::NACC;
+  const int64_t TI[2] = {TIr, TIg}, TJ[2] = {PolR::TJ, PolG::TJ};
+  int rc = ensure_layout(b, TI, TJ, true);
+  if (rc) return rc;
+  auto kern = batch_sym_pairs_kernel<PolR, PolG>;
+  const int occ = occupancy(b, (const void *)kern);
+  int64_t Pr, Pg;
+  split_ctas(b, (int64_t)b->nsm * occ, Pr, Pg);
+  const size_t slot_r = (size_t)Pr * 2 * NAr * TIr, slot_g = (size_t)Pg * 2 * NAg * TIg;
+  const size_t row_r = (size_t)b->rows_r * NAr * TIr, row_g = (size_t)b->rows_g * NAg * TIg;
+  const size_t col_r = (size_t)b->Ur * PolR::TJ * NAr, col_g = (size_t)b->Ug * PolG::TJ * NAg;
+  const size_t ch_r = (size_t)b->nfin_r * TIr * NAr, ch_g = (size_t)b->nfin_g * TIg * NAg;
+  if ((rc = grow(b, b->slots, b->slots_bytes, (slot_r + slot_g) * sizeof(double), "batch slots")) ||
+      (rc = grow(b, b->rowfull, b->rowfull_bytes, (row_r + row_g) * sizeof(double), "batch row partials")) ||
+      (rc = grow(b, b->colslot, b->colslot_bytes, (col_r + col_g) * sizeof(float), "batch column partials")) ||
+      (rc = grow(b, b->chunks, b->chunks_bytes, (ch_r + ch_g) * sizeof(double), "batch chunk sums")) ||
+      (rc = ensure_tickets(b)))
+    return rc;
   PartArgs ar{}, ag{};
   ar.sys = b->d_sys;
-  ar.nsys = nr;
-  ar.U = Ur;
+  ar.nsys = b->nr;
+  ar.U = b->Ur;
   ar.P = (int)Pr;
-  ag.sys = b->d_sys + nr;
-  ag.nsys = b->nsys - nr;
-  ag.U = Ug;
+  ar.m = (int)(TIr / PolR::TJ);
+  ar.nfin = b->nfin_r;
+  ar.slots = b->slots;
+  ar.rowfull = b->rowfull;
+  ar.colslot = b->colslot;
+  ar.chunks = b->chunks;
+  ar.tickets = b->tickets;
+  ag.sys = b->d_sys + b->nr;
+  ag.nsys = b->nsys - b->nr;
+  ag.U = b->Ug;
+  ag.P = (int)Pg;
+  ag.m = (int)(TIg / PolG::TJ);
+  ag.nfin = b->nfin_g;
+  ag.slots = b->slots + slot_r;
+  ag.rowfull = b->rowfull + row_r;
+  ag.colslot = b->colslot + col_r;
+  ag.chunks = b->chunks + ch_r;
+  ag.tickets = b->tickets + b->rows_r;
+  ar.cur = ag.cur = b->cur;
+  ar.b = ag.b = bc;
+  ar.d = ag.d = dc;
+  kern<<<(int)(Pr + Pg), NT, 0, b->stream>>>(ar, ag);
+  b->launches++;
+  batch_sym_finish_kernel<PolR, PolG, MODE><<<(unsigned)(b->nfin_r + b->nfin_g), kFinishThreadsB, 0, b->stream>>>(ar, ag);
+  b->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return berr(b, MD_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+  if (MODE == STAGE_KICK_DRIFT) b->cur = 1 - b->cur;
+  return MD_OK;
+}
+
+template <class PolR, class PolG, bool MIXED, int MODE>
+int launch_batch(md_batch *b, double bc, double dc) {
+  constexpr int64_t TI = (int64_t)NT * PolR::R;
+  static_assert(PolR::R == PolG::R && PolR::TJ == PolG::TJ, "parts share the tile shape");
+  const int64_t TIs[2] = {TI, TI}, TJs[2] = {PolR::TJ, PolG::TJ};
+  int rc = ensure_layout(b, TIs, TJs, false);
+  if (rc) return rc;
+  auto kern = batch_kernel<PolR, PolG, MIXED, MODE>;
+  const int occ = occupancy(b, (const void *)kern);
+  int64_t Pr, Pg;
+  split_ctas(b, (int64_t)b->nsm * occ, Pr, Pg);
+  const size_t slot_r = (size_t)Pr * 2 * PolR::NACC * TI, slot_g = (size_t)Pg * 2 * PolG::NACC * TI;
+  if ((rc = grow(b, b->slots, b->slots_bytes, (slot_r + slot_g) * sizeof(double), "batch slots")) ||
+      (rc = ensure_tickets(b)))
+    return rc;
+  PartArgs ar{}, ag{};
+  ar.sys = b->d_sys;
+  ar.nsys = b->nr;
+  ar.U = b->Ur;
+  ar.P = (int)Pr;
+  ag.sys = b->d_sys + b->nr;
+  ag.nsys = b->nsys - b->nr;
+  ag.U = b->Ug;
   ag.P = (int)Pg;
   ar.cur = ag.cur = b->cur;
   ar.b = ag.b = bc;
@@ -375,7 +686,7 @@ int launch_batch(md_batch *b, double bc, double dc) {
   ar.slots = b->slots;
   ag.slots = b->slots + slot_r;
   ar.tickets = b->tickets;
-  ag.tickets = b->tickets + rows_r;
+  ag.tickets = b->tickets + b->rows_r;
   kern<<<(int)(Pr + Pg), NT, 0, b->stream>>>(ar, ag);
   b->launches++;
   cudaError_t e = cudaGetLastError();
@@ -384,9 +695,12 @@ int launch_batch(md_batch *b, double bc, double dc) {
   return MD_OK;
 }
 
+bool sym_form(const md_batch *b) { return b->prec == MD_MIXED && b->cfg.r == 0; }
+
 template <bool MIXED, int MODE>
 int dispatch(md_batch *b, double bc, double dc) {
   if constexpr (MIXED) {
+    if (b->cfg.r == 0) return launch_batch_sym<RingTC<4, 256, MODE>, GravMixed<8, 256, MODE>, MODE>(b, bc, dc);
     if (b->cfg.r == 4)
       return launch_batch<RingMixed<4, 256, MODE>, GravMixed<4, 256, MODE>, true, MODE>(b, bc, dc);
     return launch_batch<RingMixed<8, 256, MODE>, GravMixed<8, 256, MODE>, true, MODE>(b, bc, dc);
@@ -395,7 +709,14 @@ int dispatch(md_batch *b, double bc, double dc) {
   }
 }
 
+int refresh_mirrors(md_batch *b);
+
 int stage(md_batch *b, int mode, double bc, double dc) {
+  if (!b->mirrors_valid || b->mirror_sym != (sym_form(b) ? 1 : 0)) {
+    b->mirrors_valid = false;
+    int rc = refresh_mirrors(b);
+    if (rc) return rc;
+  }
   const bool mixed = b->prec == MD_MIXED;
   switch (mode) {
   case STAGE_KICK_DRIFT: return mixed ? dispatch<true, STAGE_KICK_DRIFT>(b, bc, dc) : dispatch<false, STAGE_KICK_DRIFT>(b, bc, dc);
@@ -405,15 +726,17 @@ int stage(md_batch *b, int mode, double bc, double dc) {
 }
 
 int refresh_mirrors(md_batch *b) {
-  if (b->mirrors_valid) return MD_OK;
+  const int sym = sym_form(b) ? 1 : 0;
+  if (b->mirrors_valid && b->mirror_sym == sym) return MD_OK;
   for (md_ctx *c : b->ctx) {
     c->prec = b->prec;
-    c->pt.ring_tc = 0;  // the batched kernel reads the interleaved records
+    c->pt.ring_tc = sym;  // symmetric form: tensor-core Ring records; one-sided: interleaved
     c->mirror_cur = b->cur;
     int rc = mirror_refresh(c);
     if (rc) return berr(b, rc, "%s", c->err.c_str());
   }
   b->mirrors_valid = true;
+  b->mirror_sym = sym;
   return MD_OK;
 }
 
@@ -485,6 +808,9 @@ void md_batch_free(md_batch *b) {
   dev_free(b->d_sys);
   dev_free(b->slots);
   dev_free(b->tickets);
+  dev_free(b->rowfull);
+  dev_free(b->colslot);
+  dev_free(b->chunks);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -522,12 +848,20 @@ int md_batch_set_stream(md_batch *b, void *stream) {
 
 int md_batch_set_tuning(md_batch *b, int r, double split, int ctas_per_sm) {
   if (!b) return set_err(nullptr, MD_EINVAL, "NULL batch");
-  if ((r != 4 && r != 8) || !(split > 0.0 && split < 1.0) || ctas_per_sm < 0 || ctas_per_sm > 16)
-    return berr(b, MD_EINVAL, "%s", "md_batch_set_tuning: need r in {4, 8}, 0 < split < 1, 0 <= ctas_per_sm <= 16");
+  if ((r != 0 && r != 4 && r != 8) || !(split > 0.0 && split < 1.0) || ctas_per_sm < 0 || ctas_per_sm > 16)
+    return berr(b, MD_EINVAL, "%s", "md_batch_set_tuning: need r in {0, 4, 8}, 0 < split < 1, 0 <= ctas_per_sm <= 16");
   b->cfg.r = r;
   b->cfg.split = split;
   b->cfg.ctas_per_sm = ctas_per_sm;
   drop_graphs(b);
+  return MD_OK;
+}
+
+int md_batch_get_tuning(const md_batch *b, int *r, double *split, int *ctas_per_sm) {
+  if (!b) return set_err(nullptr, MD_EINVAL, "NULL batch");
+  if (r) *r = b->cfg.r;
+  if (split) *split = b->cfg.split;
+  if (ctas_per_sm) *ctas_per_sm = b->cfg.ctas_per_sm;
   return MD_OK;
 }
 
@@ -537,12 +871,13 @@ int md_batch_autotune(md_batch *b, double *best_ms) {
   if (rc) return rc;
   const Config base = b->cfg;
   std::vector<Config> cand;
-  const int rs[2] = {8, 4};
+  const int rs[3] = {0, 8, 4};
   const double fs[5] = {0.90, 0.95, 1.0, 1.05, 1.10};
   const int cps[2] = {0, 3};
   for (int r : rs)
     for (double f : fs)
       for (int cp : cps) {
+        if (b->prec != MD_MIXED && r != rs[0]) continue;
         Config c = base;
         c.r = b->prec == MD_MIXED ? r : base.r;
         c.split = base.split * f > 0.98 ? 0.98 : base.split * f;
@@ -590,11 +925,19 @@ int md_batch_step(md_batch *b, int64_t nsteps) {
       (rc = stage(b, STAGE_KICK_DRIFT, B1, D0)))
     return rc;
   int64_t left = nsteps - 1;
-  while (left >= kGraphSteps) {
+  // capture only on a capturable stream that is not being captured already
+  bool graphs = b->stream != nullptr && b->stream != cudaStreamLegacy && b->stream != cudaStreamPerThread;
+  if (graphs) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    graphs = cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    cudaGetLastError();
+  }
+  while (graphs && left >= kGraphSteps) {
     const int key = b->cur;
     if (b->graph_key[key] != key || !b->graph[key]) {
       cudaGraph_t g;
       B_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      const int64_t l0 = b->launches;
       for (int s = 0; s < kGraphSteps && !rc; s++) {
         if (!rc) rc = stage(b, STAGE_KICK_DRIFT, 2.0 * B0, D0);
         if (!rc) rc = stage(b, STAGE_KICK_DRIFT, B1, D1);
@@ -603,13 +946,14 @@ int md_batch_step(md_batch *b, int64_t nsteps) {
       cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
       if (rc) return rc;
       if (ee != cudaSuccess) return berr(b, MD_ECUDA, "graph capture: %s", cudaGetErrorString(ee));
-      b->launches -= 3 * kGraphSteps;  // captured, not launched
+      b->graph_launches[key] = b->launches - l0;
+      b->launches = l0;  // captured, not launched
       B_CUDA(b, cudaGraphInstantiate(&b->graph[key], g, 0));
       cudaGraphDestroy(g);
       b->graph_key[key] = key;
     }
     B_CUDA(b, cudaGraphLaunch(b->graph[key], b->stream));
-    b->launches += 3 * kGraphSteps;
+    b->launches += b->graph_launches[key];
     left -= kGraphSteps;
   }
   for (; left > 0; left--) {

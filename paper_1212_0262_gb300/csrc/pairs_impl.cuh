@@ -50,6 +50,23 @@ __host__ __device__ __forceinline__ int64_t unit_begin(int64_t U, int P, int64_t
 // CTA whose range holds unit u: max c with U c / P <= u.
 __device__ __forceinline__ int64_t cta_of_unit(int64_t U, int P, int64_t u) { return ((u + 1) * P - 1) / U; }
 
+// Triangular unit table of the Newton's-third-law form: row I (i-tile of m
+// j-tiles) holds the j-tiles J = m I .. n_jt - 1.
+__host__ __device__ __forceinline__ int64_t sym_rowstart(int64_t I, int64_t n_jt, int m) {
+  return I * n_jt - (int64_t)m * I * (I - 1) / 2;
+}
+
+// The row holding unit u: the largest I < n_it with rowstart(I) <= u.
+__device__ int64_t sym_row_of_unit(int64_t u, int64_t n_it, int64_t n_jt, int m) {
+  int64_t lo = 0, hi = n_it - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (sym_rowstart(mid, n_jt, m) <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // Compensated FP32 running sum (Knuth's TwoSum: hi + lo carries the exact sum of
@@ -268,6 +285,7 @@ __device__ __forceinline__ float2 rcp2_fma(float2 s) {
 // moves work from the SFU (the binding pipe of this kernel) to the FMA pipe.
 template <int R_, int TJ_, int MODE, int OFF = 0>
 struct GravMixed {
+  static constexpr int THREADS = NT, MINB = 4;  // CTA size and CTAs per SM of the register budget
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;  // rows finished per thread
@@ -772,15 +790,17 @@ __device__ __forceinline__ void write_tc_pad(void *mirror, int64_t i) {
   for (int k = 0; k < 8; k++) m[k] = m[64 + k] = 0.f;
 }
 
-template <int RM_, int TJ_, int MODE>
+template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 3>
 struct RingTC {
+  static constexpr int THREADS = THREADS_;    // CTA size (the one-sided skeletons use NT)
+  static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget is set for
   static constexpr int RM = RM_;              // 16-row m-blocks per warp
-  static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = NT * R = 64 RM rows per CTA
+  static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = THREADS * R = 16 RM rows per warp
   static constexpr int TJ = TJ_, NACC = 1, JB = 64;
   static constexpr bool MASK = true;
   static constexpr int NR = 2 * RM;           // rows g and g+8 of each m-block
   static constexpr int FMT = 1;               // tensor-core fragment records
-  static_assert(NT * R == 64 * RM, "tile rows: 4 warps x RM m-blocks x 16");
+  static_assert(THREADS * R == 16 * RM * (THREADS / 32), "tile rows: warps x RM m-blocks x 16");
   __device__ static int mrow(int rr) {        // row offset in the tile of item rr = 2 r + h
     const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
     return w * 16 * RM + 16 * (rr >> 1) + g + 8 * (rr & 1);

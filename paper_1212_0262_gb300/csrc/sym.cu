@@ -41,7 +41,6 @@
 
 namespace {
 
-constexpr int NW = NT / 32;
 constexpr size_t kSymMaxColBytes = (size_t)4 << 30;
 
 struct SymArgs {
@@ -52,21 +51,6 @@ struct SymArgs {
   double *chunks;    // [n_it][nc][TI][NACC] chunk sums of the column partials
 };
 
-__host__ __device__ __forceinline__ int64_t sym_rowstart(int64_t I, int64_t n_jt, int m) {
-  return I * n_jt - (int64_t)m * I * (I - 1) / 2;
-}
-
-// The row holding unit u: the largest I < n_it with rowstart(I) <= u.
-__device__ int64_t sym_row_of_unit(int64_t u, int64_t n_it, int64_t n_jt, int m) {
-  int64_t lo = 0, hi = n_it - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) / 2;
-    if (sym_rowstart(mid, n_jt, m) <= u) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 // CTAs of the pair kernel that cover part of row T: [cf, cl].
 __device__ __forceinline__ void sym_row_ctas(const PairArgs &a, const SymArgs &s, int64_t T, int64_t &cf,
                                              int64_t &cl) {
@@ -76,11 +60,12 @@ __device__ __forceinline__ void sym_row_ctas(const PairArgs &a, const SymArgs &s
 
 // Pair phase: every unit's block, row partials per CTA segment, column partials per unit.
 template <class Pol>
-__global__ void __launch_bounds__(NT) sym_pairs_kernel(PairArgs a, SymArgs s) {
+__global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(PairArgs a, SymArgs s) {
+  constexpr int THR = Pol::THREADS, NW = THR / 32;
   constexpr int TJ = Pol::TJ, NACC = Pol::NACC;
   constexpr int TILE_BYTES = TJ * Pol::JB;
   constexpr int CHUNKS = TILE_BYTES / 16;
-  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  constexpr int64_t TI = (int64_t)THR * Pol::R;
   static_assert(TILE_BYTES % 16 == 0, "tile must be a whole number of 16-byte chunks");
   static_assert(TI % TJ == 0, "i-tiles must be whole numbers of j-tiles");
   __shared__ __align__(16) unsigned char sbuf[2][TILE_BYTES];
@@ -93,7 +78,7 @@ __global__ void __launch_bounds__(NT) sym_pairs_kernel(PairArgs a, SymArgs s) {
   const unsigned char *mir = (const unsigned char *)a.mirror_in;
   auto prefetch = [&](int buf, int64_t jt) {
     const unsigned char *src = mir + jt * (int64_t)TILE_BYTES;
-    for (int ch = threadIdx.x; ch < CHUNKS; ch += NT) cp_async16(&sbuf[buf][ch * 16], src + ch * 16);
+    for (int ch = threadIdx.x; ch < CHUNKS; ch += THR) cp_async16(&sbuf[buf][ch * 16], src + ch * 16);
     cp_async_commit();
   };
 
@@ -125,7 +110,7 @@ __global__ void __launch_bounds__(NT) sym_pairs_kernel(PairArgs a, SymArgs s) {
       // column partial of this unit: the warps' sums in a fixed order (colsm is
       // rewritten only after the next unit's first barrier)
       float *dst = s.colslot + u * (int64_t)(TJ * NACC);
-      for (int idx = threadIdx.x; idx < TJ * NACC; idx += NT) {
+      for (int idx = threadIdx.x; idx < TJ * NACC; idx += THR) {
         float v = colsm[idx];
 #pragma unroll
         for (int w = 1; w < NW; w++) v += colsm[w * TJ * NACC + idx];
@@ -168,7 +153,7 @@ constexpr int kFinishThreads = 256;
 template <class Pol, int MODEL, int MODE>
 __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, SymArgs s) {
   constexpr int NACC = Pol::NACC, TJ = Pol::TJ;
-  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  constexpr int64_t TI = (int64_t)Pol::THREADS * Pol::R;
   constexpr int OUT = (int)TI * NACC;  // outputs of a tile: (particle, component)
   __shared__ bool s_last;
   const int64_t T = blockIdx.x / s.nc;
@@ -226,7 +211,8 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
 
 template <class Pol, int MODEL, int MODE>
 int launch_sym(md_ctx *c, PairArgs a) {
-  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  constexpr int THR = Pol::THREADS;
+  constexpr int64_t TI = (int64_t)THR * Pol::R;
   constexpr int TJ = Pol::TJ, NACC = Pol::NACC;
   auto kern = sym_pairs_kernel<Pol>;
   static bool carveout_set = false;  // once per kernel, before any stream capture
@@ -236,7 +222,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
     carveout_set = true;
   }
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THR, 0);
   if (occ < 1) occ = 1;
   if (c->pt.ctas_per_sm > 0 && c->pt.ctas_per_sm < occ) occ = c->pt.ctas_per_sm;
   SymArgs s{};
@@ -282,7 +268,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
-  kern<<<a.P, NT, 0, c->stream>>>(a, s);
+  kern<<<a.P, THR, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
   sym_finish_kernel<Pol, MODEL, MODE><<<a.n_it * s.nc, kFinishThreads, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
@@ -292,7 +278,11 @@ int launch_sym(md_ctx *c, PairArgs a) {
 
 template <int MODEL, int MODE>
 int sym_dispatch(md_ctx *c, PairArgs a) {
-  if constexpr (MODEL == MD_RING) return launch_sym<RingTC<4, 256, MODE>, MODEL, MODE>(c, a);
+  if constexpr (MODEL == MD_RING) {
+    if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, MODE>(c, a);
+    if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, MODE>(c, a);
+    return launch_sym<RingTC<4, 256, MODE>, MODEL, MODE>(c, a);
+  }
   else return launch_sym<GravMixed<8, 256, MODE>, MODEL, MODE>(c, a);
 }
 

@@ -247,7 +247,16 @@ class Ensemble:
         self._chk(B.load().md_batch_step(self._h, int(nsteps)))
 
     def set_tuning(self, r: int, split: float, ctas_per_sm: int = 0) -> None:
+        """r = 0: Newton's-third-law kernels (mixed default); r = 4 or 8: one-sided."""
         self._chk(B.load().md_batch_set_tuning(self._h, int(r), float(split), int(ctas_per_sm)))
+
+    @property
+    def tuning(self):
+        """(r, split, ctas_per_sm) of the batched launches."""
+        r, cps = ctypes.c_int(), ctypes.c_int()
+        split = ctypes.c_double()
+        self._chk(B.load().md_batch_get_tuning(self._h, ctypes.byref(r), ctypes.byref(split), ctypes.byref(cps)))
+        return r.value, split.value, cps.value
 
     def autotune(self) -> float:
         """Pick the fastest kernel shape; returns its force-launch time in ms."""

@@ -1,7 +1,9 @@
 """Batched ensembles (md_batch_*): every system of an uneven ensemble, advanced in
 shared persistent launches and replayed CUDA graphs, must match the same system
-advanced alone by md_step (same kernels and precision; only the stream-K split of
-the FP64 per-particle sums differs, so agreement is to rounding)."""
+advanced alone by md_step (same pair arithmetic and precision; only the stream-K
+split of the FP64 per-particle sums differs, so agreement is to rounding).  Mixed
+ensembles run the Newton's-third-law kernels by default (r = 0) and the one-sided
+CUDA-core kernels with r = 4 or 8; the lone systems take the matching form."""
 import numpy as np
 import pytest
 
@@ -17,26 +19,28 @@ SEEDS = [1000 + s for s in range(6)]
 
 
 def _one_sided(sy):
-    # the batched kernel is the one-sided CUDA-core kernel of the single-system path
+    # the one-sided batched kernel is the one-sided CUDA-core kernel of the single-system path
     sy.set_tuning("ring_tc", 0)
     sy.set_tuning("symmetric", 0)
     return sy
 
 
-def _alone(s, nsteps, prec):
+def _alone(s, nsteps, prec, sym=False):
     with System(MODELS[s], NS[s], EPS[s], DTS[s], SEEDS[s], precision=prec) as sy:
-        _one_sided(sy).step(nsteps)
+        (sy if sym else _one_sided(sy)).step(nsteps)
         return sy.get_state(), sy.energy()
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "mixed_one_sided", "fp64"])
 @pytest.mark.parametrize("nsteps", [1, 25])
 def test_ensemble_matches_individual_runs(prec, nsteps):
-    ens = Ensemble(MODELS, NS, EPS, DTS, SEEDS, precision=prec)
+    ens = Ensemble(MODELS, NS, EPS, DTS, SEEDS, precision=prec.split("_")[0])
+    if prec == "mixed_one_sided":
+        ens.set_tuning(8, 0.5, 0)
     ens.step(nsteps)
     K, V = ens.energy()
     for s in range(len(NS)):
-        (q, p), (k, v) = _alone(s, nsteps, prec)
+        (q, p), (k, v) = _alone(s, nsteps, prec.split("_")[0], sym=(prec == "mixed"))
         qb, pb = ens.get_state(s)
         tol = 1e-12 if prec == "fp64" else 1e-9
         assert np.max(np.abs(qb - q)) <= tol * max(1.0, np.abs(q).max()), s
@@ -55,7 +59,8 @@ def test_autotune_leaves_states_unchanged_and_shapes_agree():
         assert np.array_equal(q, before[s][0]) and np.array_equal(p, before[s][1])
     ens.step(12)
     ref = [ens.get_state(s) for s in range(len(NS))]
-    for r, split, cps in ((4, 0.3, 0), (8, 0.7, 2)):
+    r = ens.tuning[0]  # the form autotune picked; other splits and CTA counts must agree with it
+    for split, cps in ((0.3, 0), (0.7, 2)):
         e2 = Ensemble(MODELS, NS, EPS, DTS, SEEDS)
         e2.set_tuning(r, split, cps)
         e2.step(12)
@@ -72,9 +77,26 @@ def test_set_state_is_used_by_the_next_step():
     ens.set_state(1, q, p)
     ens.step(3)
     with System(MODELS[1], NS[1], EPS[1], DTS[1], 0, precision="mixed") as sy:
-        _one_sided(sy).set_state(q, p)
+        sy.set_state(q, p)
         sy.step(3)
         qa, pa = sy.get_state()
     qb, pb = ens.get_state(1)
     assert np.max(np.abs(qb - qa)) <= 1e-9 * max(1.0, np.abs(qa).max())
     ens.close()
+
+
+def test_one_sided_tunings_agree_with_the_symmetric_default():
+    """r = 4 and r = 8 (one-sided) and r = 0 (symmetric) give the same trajectories
+    to the FP32 pair-arithmetic level."""
+    ref = Ensemble(MODELS, NS, EPS, DTS, SEEDS)
+    ref.step(5)
+    for r in (4, 8):
+        e2 = Ensemble(MODELS, NS, EPS, DTS, SEEDS)
+        e2.set_tuning(r, 0.5, 0)
+        e2.step(5)
+        for s in range(len(NS)):
+            q, p = e2.get_state(s)
+            qr, pr = ref.get_state(s)
+            assert np.max(np.abs(q - qr)) <= 1e-5 * max(1.0, np.abs(qr).max()), (r, s)
+        e2.close()
+    ref.close()

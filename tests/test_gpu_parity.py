@@ -263,3 +263,17 @@ def test_step_graphs_match_stage_by_stage(model, prec):
         qb, pb = b.get_state()
         assert np.array_equal(qa, qb) and np.array_equal(pa, pb), n
     assert a.launch_count - la <= b.launch_count - lb
+
+
+@pytest.mark.parametrize("model", [0, 1, 2])
+def test_step_on_the_legacy_default_stream(model):
+    """The legacy default stream cannot be captured: md_step then launches every
+    stage itself, with the same result."""
+    a, _, _ = _sys(model, 2000, "mixed")
+    b, _, _ = _sys(model, 2000, "mixed")
+    b.set_stream(0)
+    a.step(20)
+    b.step(20)
+    qa, pa = a.get_state()
+    qb, pb = b.get_state()
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
