@@ -108,11 +108,13 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "rcp_offload"      2D FP32: every 8th pair of j's takes 1/x on the FMA pipe (0 or 8)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32
  *                      tensor-core products (0 off; 1 or 2: 4 or 2 16-row blocks per warp)
- *   "symmetric"        FP32 forward stages of Ring (with ring_tc 1) and 2D: every
- *                      unordered pair evaluated once and added to both particles
- *                      (Newton's third law; the paper evaluates both orders, Sec. 3.2).
- *                      Needs column-partial storage of about N^2 / 2^16 floats (Ring)
- *                      or N^2 / 2^18 (2D); above 4 GiB of it the one-sided kernel runs.
+ *   "symmetric"        forward stages of Ring (FP32: with ring_tc 1) and 2D, FP32 and
+ *                      FP64 (r_fp64 2): every unordered pair evaluated once and added to
+ *                      both particles (Newton's third law; the paper evaluates both
+ *                      orders, Sec. 3.2).  Needs column-partial storage of about
+ *                      N^2 / 2^16 floats (FP32 Ring), N^2 / 2^18 floats (FP32 2D) or
+ *                      N^2 / 2^16 doubles (FP64); above 4 GiB of it the one-sided kernel
+ *                      runs.
  *   "step_graphs"      md_step replays its steps after the first from captured CUDA
  *                      graphs of 8 steps (1, default) or launches every stage (0).
  * MD_EINVAL for an unknown key or value. */
@@ -126,6 +128,7 @@ int md_set_tuning(md_ctx *ctx, const char *key, int64_t value);
 #define MD_KERNEL_PAIRS_TC 3     /* FP32 Ring with tensor-core products, every ordered pair */
 #define MD_KERNEL_PAIRS_SYM 4    /* FP32 2D, every unordered pair once */
 #define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 Ring with tensor-core products, every unordered pair once */
+#define MD_KERNEL_PAIRS_FP64_SYM 6 /* FP64 all-pairs, every unordered pair once */
 int md_force_kernel(const md_ctx *ctx);
 
 /* Redraw the state with recipe `kind` (MD_IC_*) and `params` from `seed`.

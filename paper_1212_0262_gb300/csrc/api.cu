@@ -133,6 +133,7 @@ void md_free(md_ctx *c) {
   dev_free(c->hmf_partials);
   dev_free(c->hmf_m);
   dev_free(c->hmf_ticket);
+  dev_free(c->hmf_cs);
   dev_free(c->mirror[0]);
   dev_free(c->mirror[1]);
   dev_free(c->sk_slots);
@@ -349,8 +350,9 @@ StepGraphKey step_key_of(const md_ctx *c, double h) {
   key.pt = c->pt;
   key.ht = c->ht;
   key.mirror_fmt = c->mirror_fmt;
-  const void *b[13] = {c->q, c->p, c->mirror[0], c->mirror[1], c->sk_slots, c->sk_tickets, c->sym_rowfull,
-                       c->sym_colslot, c->sym_chunks, c->hmf_partials, c->hmf_m, c->hmf_ticket, c->f};
+  const void *b[14] = {c->q,           c->p,          c->mirror[0],    c->mirror[1], c->sk_slots,
+                       c->sk_tickets,  c->sym_rowfull, c->sym_colslot, c->sym_chunks, c->hmf_partials,
+                       c->hmf_m,       c->hmf_ticket, c->f,            c->hmf_cs};
   memcpy(key.bufs, b, sizeof b);
   return key;
 }

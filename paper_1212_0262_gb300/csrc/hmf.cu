@@ -7,8 +7,12 @@
 //     p += kick * f ;  theta += drift * p                (Sec. 3 step list)
 //     accumulate cos(theta_new), sin(theta_new)          (Eq. 7 for the next stage)
 // so the state is read once and written once per stage (32 B per particle).
-// The paper instead stores sin and cos in global memory and reloads them; here
-// they are recomputed, which is cheaper than the extra 16 B of traffic.
+// The paper stores sin and cos in global memory and reloads them.  The mixed
+// path recomputes them instead (FP32 polynomials are cheaper than 32 B more
+// traffic); the FP64 path is bound by the FP64 pipe (an FP64 sincos is tens of
+// DFMA at 2.3 per SM per clock), so it keeps (cos, sin) of the current angles in
+// a buffer, as the paper does, and computes one FP64 sincos per particle-stage
+// instead of two.
 //
 // Reduction: per-thread sums, warp shuffles and a block tree give one FP64
 // partial per CTA; the last CTA to finish (atomic ticket, no waiting) adds the
@@ -30,6 +34,7 @@ struct HmfArgs {
   double *m_out;     // (sum cos, sum sin) of the new angles
   unsigned *ticket;
   double *fout;  // STAGE_FORCE_ONLY output
+  double2 *cs;   // FP64 path: (cos, sin) of the current angles, rewritten by drifts
 };
 
 // One particle of a stage.  MIXED: FP64 state update, FP32 sine/cosine of the
@@ -59,9 +64,8 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
       asf += s;
     }
   } else {
-    double s, c;
-    sincos(th, &s, &c);
-    double f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
+    const double2 cs = a.cs[i];
+    double f = __dsub_rn(__dmul_rn(cs.x, my), __dmul_rn(cs.y, mx));
     if (MODE == STAGE_FORCE_ONLY) {
       a.fout[i] = f;
       return;
@@ -69,7 +73,9 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
     pp = fma(a.kick, f, pp);
     if (MODE == STAGE_KICK_DRIFT) {
       th = fma(a.drift, pp, th);
+      double s, c;
       sincos(th, &s, &c);
+      a.cs[i] = make_double2(c, s);
       acd += c;
       asd += s;
     }
@@ -158,7 +164,8 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
 // range reduction, FP32 per-thread sums; otherwise FP64 throughout.
 template <bool MIXED>
 __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__ q, int64_t N,
-                                                      double *partials, double *m_out, unsigned *ticket) {
+                                                      double *partials, double *m_out, unsigned *ticket,
+                                                      double2 *cs_out) {
   float acf = 0.f, asf = 0.f;
   double acd = 0.0, asd = 0.0;
   const int64_t G = (int64_t)gridDim.x * NT;
@@ -172,6 +179,7 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
     } else {
       double s, c;
       sincos(th, &s, &c);
+      if (cs_out) cs_out[i] = make_double2(c, s);
       acd += c;
       asd += s;
     }
@@ -209,6 +217,7 @@ int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
   a.m_out = c->hmf_m + 2 * (1 - c->hmf_cur);
   a.ticket = c->hmf_ticket;
   a.fout = fout;
+  a.cs = (double2 *)c->hmf_cs;
   auto kern = hmf_stage_kernel<MIXED, MODE>;
   int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1);
   kern<<<g, NT, 0, c->stream>>>(a);
@@ -230,13 +239,13 @@ void hmf_sums_raw(cudaStream_t st, int nsm, int grid_cap, const double *q, int64
   if (g > need) g = need;
   if (g > grid_cap) g = grid_cap;
   if (g < 1) g = 1;
-  hmf_sums_kernel<false><<<(int)g, NT, 0, st>>>(q, N, partials, out2, ticket);
+  hmf_sums_kernel<false><<<(int)g, NT, 0, st>>>(q, N, partials, out2, ticket, nullptr);
 }
 
 int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2) {
   auto kern = hmf_sums_kernel<false>;
   int g = grid_for(c, (const void *)kern, c->N);
-  kern<<<g, NT, 0, c->stream>>>(q, c->N, c->hmf_partials, d_out2, c->hmf_ticket);
+  kern<<<g, NT, 0, c->stream>>>(q, c->N, c->hmf_partials, d_out2, c->hmf_ticket, nullptr);
   MD_LAUNCHED(c);
   return MD_OK;
 }
@@ -249,11 +258,21 @@ int hmf_prime(md_ctx *c) {
   if (c->prec == MD_MIXED) {
     auto kern = hmf_sums_kernel<true>;
     int g = grid_for(c, (const void *)kern, c->N);
-    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr);
     MD_LAUNCHED(c);
   } else {
-    int rc = hmf_sums_fp64_of(c, c->q, out);
-    if (rc) return rc;
+    // FP64: the sums and the (cos, sin) buffer the FP64 stages read
+    const size_t need = sizeof(double2) * (size_t)c->N;
+    if (need > c->hmf_cs_bytes) {
+      dev_free(c->hmf_cs);
+      c->hmf_cs = (double *)dev_alloc(need);
+      c->hmf_cs_bytes = c->hmf_cs ? need : 0;
+      if (!c->hmf_cs) return set_err(c, MD_ENOMEM, "HMF (cos, sin) buffer: %zu bytes", need);
+    }
+    auto kern = hmf_sums_kernel<false>;
+    int g = grid_for(c, (const void *)kern, c->N);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs);
+    MD_LAUNCHED(c);
   }
   c->hmf_m_valid = true;
   c->hmf_m_prec = c->prec;

@@ -22,7 +22,7 @@ struct PairTuning {
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
   int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
   int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
-  int symmetric = 1;  // FP32 forward stages: each unordered pair once (Newton's third law)
+  int symmetric = 1;  // forward stages: each unordered pair once (Newton's third law)
   int sym_threads = 128;  // symmetric Ring kernel: 128 threads, 4 m-blocks per warp; 256: 2 m-blocks;
                           // 768: 256 threads with registers capped for 3 CTAs per SM
   int ctas_per_sm = 0;  // 0: occupancy-derived
@@ -44,7 +44,7 @@ struct StepGraphKey {
   PairTuning pt;
   HmfTuning ht;
   int mirror_fmt;
-  const void *bufs[13];
+  const void *bufs[14];
 };
 
 struct md_ctx {
@@ -66,7 +66,9 @@ struct md_ctx {
   unsigned *hmf_ticket = nullptr;
   int hmf_grid_max = 0;
   int hmf_cur = 0;
-  bool hmf_m_valid = false;
+  bool hmf_m_valid = false;           // FP64: the (cos, sin) buffer is valid with the sums
+  double *hmf_cs = nullptr;           // FP64 path: (cos, sin) of the current angles, N double2
+  size_t hmf_cs_bytes = 0;
   int hmf_m_prec = -1;
 
   // Ring / 2D: position mirrors (ping-pong), stream-K partial slots and tickets
@@ -82,7 +84,7 @@ struct md_ctx {
   size_t sk_tickets_count = 0;
   double *sym_rowfull = nullptr;  // Newton's-third-law variant: row partials of whole rows
   size_t sym_rowfull_bytes = 0;
-  float *sym_colslot = nullptr;   // and column partials per unit
+  void *sym_colslot = nullptr;    // and column partials per unit (FP32 or FP64)
   size_t sym_colslot_bytes = 0;
   double *sym_chunks = nullptr;   // and chunk sums of the column partials
   size_t sym_chunk_bytes = 0;

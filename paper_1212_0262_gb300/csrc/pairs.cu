@@ -423,7 +423,7 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
 extern "C" int md_force_kernel(const md_ctx *c) {
   if (!c) return -1;
   if (c->model == MD_HMF) return MD_KERNEL_HMF;
-  if (c->prec != MD_MIXED) return MD_KERNEL_PAIRS_FP64;
+  if (c->prec != MD_MIXED) return sym_applies(c) ? MD_KERNEL_PAIRS_FP64_SYM : MD_KERNEL_PAIRS_FP64;
   const bool tc = ring_tc(c) && c->pt.r_mixed != 4;
   if (sym_applies(c)) return tc ? MD_KERNEL_PAIRS_TC_SYM : MD_KERNEL_PAIRS_SYM;
   return tc ? MD_KERNEL_PAIRS_TC : MD_KERNEL_PAIRS;

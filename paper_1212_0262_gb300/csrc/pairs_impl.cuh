@@ -93,15 +93,15 @@ __device__ __forceinline__ double csum_total(const CompSum &c) { return (double)
 // (lanes with the mask bit set keep the upper half) and adds the partner's copy
 // of them.  Returns the sum over those lanes of value number
 // sum_r (bit MASK_r of the lane ? V/2^(r+1) : 0).
-template <int V, int MASK0>
-__device__ __forceinline__ float butterfly_sum(float (&v)[V], int lane) {
+template <int V, int MASK0, class T>
+__device__ __forceinline__ T butterfly_sum(T (&v)[V], int lane) {
 #pragma unroll
   for (int h = V / 2, mask = MASK0; h >= 1; h /= 2, mask /= 2) {
     const bool up = (lane & mask) != 0;
 #pragma unroll
     for (int i = 0; i < h; i++) {
-      const float send = up ? v[i] : v[i + h];
-      const float keep = up ? v[i + h] : v[i];
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
     }
   }
@@ -286,6 +286,7 @@ __device__ __forceinline__ float2 rcp2_fma(float2 s) {
 template <int R_, int TJ_, int MODE, int OFF = 0>
 struct GravMixed {
   static constexpr int THREADS = NT, MINB = 4;  // CTA size and CTAs per SM of the register budget
+  using ColT = float;                           // column partials of the symmetric form
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;  // rows finished per thread
@@ -398,6 +399,8 @@ struct GravMixed {
 // ------------------------------------------------------------ forward Ring FP64
 template <int R_, int TJ_, int MODE>
 struct RingF64 {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = double;
   static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_RING, false, false>::value;
   static constexpr bool MASK = true;
   static constexpr int NR = R;  // rows finished per thread
@@ -439,11 +442,43 @@ struct RingF64 {
       }
     }
   }
+  // Off-diagonal block of the Newton's-third-law variant (FP64): the i-rows as in
+  // tile<>, and per j the sum over this warp's 32 R rows of the same terms, into
+  // colsm[warp TJ + j]; sixteen j's at a time reduced over the warp by a butterfly.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
+    const double2 *sm = (const double2 *)smb;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k16 = 0; k16 < TJ / 16; k16++) {
+      double v[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; kk++) {
+        const int k = 16 * k16 + kk;
+        const double2 sc = sm[2 * k], ag = sm[2 * k + 1];
+        double col = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          double S = fma(st.s[r], sc.y, -(st.c[r] * sc.x));
+          double sh = fma(st.a[r], ag.y, -(st.g[r] * ag.x));
+          double y = rsqrt_nr(fma(sh, sh, a.epsd));
+          double t = S * y * (y * y);
+          st.accd[r][0] += t;
+          col += t;
+        }
+        v[kk] = col;
+      }
+      double sum = butterfly_sum<16, 16>(v, lane);  // over lane bits 4..1
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      if ((lane & 1) == 0) colsm[w * TJ + 16 * k16 + (lane >> 1)] = sum;
+    }
+  }
 };
 
 // ------------------------------------------------------------ forward 2D FP64
 template <int R_, int TJ_, int MODE>
 struct GravF64 {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = double;
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, false, false>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;  // rows finished per thread
@@ -478,6 +513,40 @@ struct GravF64 {
         double inv = rcp_nr(fma(dx, dx, fma(dy, dy, a.epsd)));
         st.accd[r][0] = fma(dx, inv, st.accd[r][0]);
         st.accd[r][1] = fma(dy, inv, st.accd[r][1]);
+      }
+    }
+  }
+  // Off-diagonal block of the Newton's-third-law variant (FP64): per j the sums
+  // over this warp's rows of the x and y terms into colsm[(warp TJ + j) 2 + d];
+  // eight j's (16 values) at a time reduced over the warp by a butterfly.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
+    const double2 *sm = (const double2 *)smb;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k8 = 0; k8 < TJ / 8; k8++) {
+      double v[16];
+#pragma unroll
+      for (int kk = 0; kk < 8; kk++) {
+        const double2 xy = sm[8 * k8 + kk];
+        double cx = 0.0, cy = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          double dx = st.x[r] - xy.x, dy = st.y[r] - xy.y;
+          double inv = rcp_nr(fma(dx, dx, fma(dy, dy, a.epsd)));
+          double tx = dx * inv, ty = dy * inv;
+          st.accd[r][0] += tx;
+          st.accd[r][1] += ty;
+          cx += tx;
+          cy += ty;
+        }
+        v[2 * kk] = cx;
+        v[2 * kk + 1] = cy;
+      }
+      double sum = butterfly_sum<16, 16>(v, lane);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      if ((lane & 1) == 0) {
+        const int vi = lane >> 1;  // 2 kk + component
+        colsm[(w * TJ + 8 * k8 + (vi >> 1)) * 2 + (vi & 1)] = sum;
       }
     }
   }
@@ -794,6 +863,7 @@ template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 3>
 struct RingTC {
   static constexpr int THREADS = THREADS_;    // CTA size (the one-sided skeletons use NT)
   static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget is set for
+  using ColT = float;                         // column partials of the symmetric form
   static constexpr int RM = RM_;              // 16-row m-blocks per warp
   static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = THREADS * R = 16 RM rows per warp
   static constexpr int TJ = TJ_, NACC = 1, JB = 64;

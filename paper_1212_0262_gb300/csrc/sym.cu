@@ -1,4 +1,4 @@
-// Newton's-third-law variant of the FP32 Ring and 2D force stages: every
+// Newton's-third-law variant of the Ring and 2D force stages: every
 // unordered pair is evaluated once and its term added to both particles.  The
 // paper evaluates every ordered pair (Sec. 3.2, tile algorithm) and leaves this
 // variant out; it is one of the extensions its conclusion names.
@@ -47,7 +47,8 @@ struct SymArgs {
   int m;             // TI / TJ
   int nc;            // chunk slots per tile in the finish phase
   double *rowfull;   // [n_it][NACC][TI] row partials of rows covered by one CTA
-  float *colslot;    // [U][TJ][NACC] column partials of the off-diagonal units
+  void *colslot;     // [U][TJ][NACC] column partials of the off-diagonal units (Pol::ColT:
+                     // FP32 for the mixed policies, FP64 for the FP64 ones)
   double *chunks;    // [n_it][nc][TI][NACC] chunk sums of the column partials
 };
 
@@ -68,8 +69,10 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
   constexpr int64_t TI = (int64_t)THR * Pol::R;
   static_assert(TILE_BYTES % 16 == 0, "tile must be a whole number of 16-byte chunks");
   static_assert(TI % TJ == 0, "i-tiles must be whole numbers of j-tiles");
+  using ColT = typename Pol::ColT;
   __shared__ __align__(16) unsigned char sbuf[2][TILE_BYTES];
-  __shared__ float colsm[NW * TJ * NACC];
+  __shared__ __align__(16) unsigned char colraw[NW * TJ * NACC * sizeof(ColT)];
+  ColT *colsm = (ColT *)colraw;
 
   const int64_t cta = blockIdx.x;
   const int64_t u0 = unit_begin(a.U, a.P, cta), u1 = unit_begin(a.U, a.P, cta + 1);
@@ -109,9 +112,9 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
     if (!diag) {
       // column partial of this unit: the warps' sums in a fixed order (colsm is
       // rewritten only after the next unit's first barrier)
-      float *dst = s.colslot + u * (int64_t)(TJ * NACC);
+      ColT *dst = (ColT *)s.colslot + u * (int64_t)(TJ * NACC);
       for (int idx = threadIdx.x; idx < TJ * NACC; idx += THR) {
-        float v = colsm[idx];
+        ColT v = colsm[idx];
 #pragma unroll
         for (int w = 1; w < NW; w++) v += colsm[w * TJ * NACC + idx];
         dst[idx] = v;
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
 constexpr int kSymChunk = 16;
 constexpr int kFinishThreads = 256;
 
-template <class Pol, int MODEL, int MODE>
+template <class Pol, int MODEL, bool MIXED, int MODE>
 __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, SymArgs s) {
   constexpr int NACC = Pol::NACC, TJ = Pol::TJ;
   constexpr int64_t TI = (int64_t)Pol::THREADS * Pol::R;
@@ -163,15 +166,19 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
   const int m = s.m;
   const int64_t I_lo = (int64_t)c * kSymChunk, I_hi = min(T, I_lo + kSymChunk);
   double *chunk = s.chunks + (T * s.nc) * OUT;
+  using ColT = typename Pol::ColT;
+  const ColT *col = (const ColT *)s.colslot;
   for (int o = threadIdx.x; o < OUT; o += kFinishThreads) {
     const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);
-    CompSum cs{0.f, 0.f};
+    CompSum cs{0.f, 0.f};  // FP32 column partials: compensated FP32 sum
+    double sd = 0.0;       // FP64 column partials
 #pragma unroll 8
     for (int64_t I2 = I_lo; I2 < I_hi; I2++) {
       const int64_t u = sym_rowstart(I2, a.n_jt, m) + (T * m + jsub - (int64_t)m * I2);
-      csum_add(cs, __ldcg(s.colslot + u * (TJ * NACC) + rest));
+      if constexpr (sizeof(ColT) == 4) csum_add(cs, __ldcg(col + u * (TJ * NACC) + rest));
+      else sd += __ldcg(col + u * (TJ * NACC) + rest);
     }
-    chunk[(int64_t)c * OUT + o] = csum_total(cs);
+    chunk[(int64_t)c * OUT + o] = sizeof(ColT) == 4 ? csum_total(cs) : sd;
   }
   __threadfence();
   __syncthreads();
@@ -202,14 +209,14 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
     for (int c2 = 0; c2 < nch; c2++)
 #pragma unroll
       for (int d = 0; d < NACC; d++) tot[d] -= __ldcg(chunk + (int64_t)c2 * OUT + lr * NACC + d);
-    finish<Pol, MODEL, true, MODE>(a, i, tot);
+    finish<Pol, MODEL, MIXED, MODE>(a, i, tot);
   }
   if (threadIdx.x == 0) a.tickets[T] = 0u;
 }
 
 // ------------------------------------------------------------ host side ---
 
-template <class Pol, int MODEL, int MODE>
+template <class Pol, int MODEL, bool MIXED, int MODE>
 int launch_sym(md_ctx *c, PairArgs a) {
   constexpr int THR = Pol::THREADS;
   constexpr int64_t TI = (int64_t)THR * Pol::R;
@@ -238,7 +245,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   if (rc) return rc;
   s.nc = (int)std::max<int64_t>(1, (a.n_it - 1 + kSymChunk - 1) / kSymChunk);
   const size_t need_row = (size_t)a.n_it * NACC * TI * sizeof(double);
-  const size_t need_col = (size_t)a.U * TJ * NACC * sizeof(float);
+  const size_t need_col = (size_t)a.U * TJ * NACC * sizeof(typename Pol::ColT);
   const size_t need_chunk = (size_t)a.n_it * s.nc * NACC * TI * sizeof(double);
   if (need_row > c->sym_rowfull_bytes) {
     dev_free(c->sym_rowfull);
@@ -248,7 +255,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   }
   if (need_col > c->sym_colslot_bytes) {
     dev_free(c->sym_colslot);
-    c->sym_colslot = (float *)dev_alloc(need_col);
+    c->sym_colslot = dev_alloc(need_col);
     c->sym_colslot_bytes = c->sym_colslot ? need_col : 0;
     if (!c->sym_colslot) return set_err(c, MD_ENOMEM, "symmetric column partials: %zu bytes", need_col);
   }
@@ -270,28 +277,32 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.tickets = c->sk_tickets;
   kern<<<a.P, THR, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
-  sym_finish_kernel<Pol, MODEL, MODE><<<a.n_it * s.nc, kFinishThreads, 0, c->stream>>>(a, s);
+  sym_finish_kernel<Pol, MODEL, MIXED, MODE><<<a.n_it * s.nc, kFinishThreads, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
   if (MODE == STAGE_KICK_DRIFT) c->mirror_cur = 1 - c->mirror_cur;
   return MD_OK;
 }
 
-template <int MODEL, int MODE>
+template <int MODEL, bool MIXED, int MODE>
 int sym_dispatch(md_ctx *c, PairArgs a) {
-  if constexpr (MODEL == MD_RING) {
-    if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, MODE>(c, a);
-    if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, MODE>(c, a);
-    return launch_sym<RingTC<4, 256, MODE>, MODEL, MODE>(c, a);
+  if constexpr (!MIXED) {
+    if constexpr (MODEL == MD_RING) return launch_sym<RingF64<2, 128, MODE>, MODEL, false, MODE>(c, a);
+    else return launch_sym<GravF64<2, 128, MODE>, MODEL, false, MODE>(c, a);
+  } else if constexpr (MODEL == MD_RING) {
+    if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, true, MODE>(c, a);
+    if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, true, MODE>(c, a);
+    return launch_sym<RingTC<4, 256, MODE>, MODEL, true, MODE>(c, a);
+  } else {
+    return launch_sym<GravMixed<8, 256, MODE>, MODEL, true, MODE>(c, a);
   }
-  else return launch_sym<GravMixed<8, 256, MODE>, MODEL, MODE>(c, a);
 }
 
-template <int MODEL>
+template <int MODEL, bool MIXED>
 int sym_mode(md_ctx *c, int mode, PairArgs a) {
   switch (mode) {
-  case STAGE_KICK_DRIFT: return sym_dispatch<MODEL, STAGE_KICK_DRIFT>(c, a);
-  case STAGE_KICK_ONLY: return sym_dispatch<MODEL, STAGE_KICK_ONLY>(c, a);
-  default: return sym_dispatch<MODEL, STAGE_FORCE_ONLY>(c, a);
+  case STAGE_KICK_DRIFT: return sym_dispatch<MODEL, MIXED, STAGE_KICK_DRIFT>(c, a);
+  case STAGE_KICK_ONLY: return sym_dispatch<MODEL, MIXED, STAGE_KICK_ONLY>(c, a);
+  default: return sym_dispatch<MODEL, MIXED, STAGE_FORCE_ONLY>(c, a);
   }
 }
 
@@ -300,22 +311,23 @@ int sym_mode(md_ctx *c, int mode, PairArgs a) {
 // Column partials need U TJ NACC floats, U ~ N^2 / (2 TI TJ): the variant runs
 // while they fit in kSymMaxColBytes.
 bool sym_applies(const md_ctx *c) {
-  if (!c->pt.symmetric || c->prec != MD_MIXED) return false;
-  int64_t TI, TJ = 256, nacc;
-  if (c->model == MD_RING) {
+  if (!c->pt.symmetric) return false;
+  int64_t TI, TJ, nacc = c->model == MD_GRAV2D ? 2 : 1, colbytes;
+  if (c->prec == MD_FP64) {
+    if (c->pt.r_fp64 != 2 || (c->model != MD_RING && c->model != MD_GRAV2D)) return false;
+    TI = 256, TJ = 128, colbytes = 8;
+  } else if (c->model == MD_RING) {
     if (!c->pt.ring_tc || c->pt.ring_tc == 2 || c->pt.r_mixed == 4) return false;
-    TI = 256;
-    nacc = 1;
+    TI = 256, TJ = 256, colbytes = 4;
   } else if (c->model == MD_GRAV2D) {
     if (c->pt.rcp_off || c->pt.r_mixed == 4) return false;
-    TI = 1024;
-    nacc = 2;
+    TI = 1024, TJ = 256, colbytes = 4;
   } else {
     return false;
   }
   const int64_t m = TI / TJ, n_it = (c->N + TI - 1) / TI, n_jt = m * n_it;
   const int64_t U = n_it * n_jt - m * n_it * (n_it - 1) / 2;
-  return (size_t)U * TJ * nacc * sizeof(float) <= kSymMaxColBytes;
+  return (size_t)U * TJ * nacc * colbytes <= kSymMaxColBytes;
 }
 
 int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
@@ -323,6 +335,7 @@ int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout)
   a.kick = kick;
   a.drift = drift;
   a.fout = fout;
-  if (c->model == MD_RING) return sym_mode<MD_RING>(c, mode, a);
-  return sym_mode<MD_GRAV2D>(c, mode, a);
+  const bool mixed = c->prec == MD_MIXED;
+  if (c->model == MD_RING) return mixed ? sym_mode<MD_RING, true>(c, mode, a) : sym_mode<MD_RING, false>(c, mode, a);
+  return mixed ? sym_mode<MD_GRAV2D, true>(c, mode, a) : sym_mode<MD_GRAV2D, false>(c, mode, a);
 }

@@ -55,10 +55,18 @@ def test_device_initial_state_matches_input_generator(model):
 
 # --------------------------------------------------------------- forces ---
 
+@pytest.mark.parametrize("symmetric", [1, 0])
 @pytest.mark.parametrize("N", SIZES)
 @pytest.mark.parametrize("model", [0, 1, 2])
-def test_fp64_force_parity(model, N):
+def test_fp64_force_parity(model, N, symmetric):
+    """FP64 forces; Ring and 2D both with every unordered pair once (default) and
+    with every ordered pair (the one-sided kernel)."""
+    if model == 0 and symmetric == 0:
+        pytest.skip("HMF has no pair kernel")
     s, q, p = _sys(model, N)
+    s.set_tuning("symmetric", symmetric)
+    if model:
+        assert s.force_kernel == (6 if symmetric else 1)
     f = s.force()
     err, scale, f_ora = _force_err(model, q, f)
     assert np.all(err <= 1e-12 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
@@ -178,21 +186,21 @@ def test_mixed_energy_error_within_twice_fp64():
 
 # ------------------------------------------------ full-size sampled checks --
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64", "mixed_one_sided"])
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "mixed_one_sided", "fp64_one_sided"])
 @pytest.mark.parametrize("model,N,eps", [(0, 50_000_000, 0.0), (1, 131072, 0.01), (2, 262144, 1e-4)])
 def test_full_size_sampled_force_parity(model, N, eps, prec):
     """Bench-size systems in the bench's launch configuration: forces on 64
     sampled particles against the oracle's direct sums."""
-    if model == 0 and prec == "mixed_one_sided":
+    if model == 0 and prec.endswith("one_sided"):
         pytest.skip("HMF has no pair kernel")
     s = System(model, N, eps, 0.05, 42 + model, precision=prec.split("_")[0])
-    if prec == "mixed_one_sided":
+    if prec.endswith("one_sided"):
         _variant(s, "one_sided_cuda_cores")
     q, _ = s.get_state()
     f = s.force().reshape(2 if model == 2 else 1, N)
     rows = np.unique(np.concatenate([[0, N - 1], inputs.splitmix64(9, np.arange(62)) % np.uint64(N)]).astype(np.int64))
     fo, scale = ora.force_rows(model, q, rows, eps, with_abs=True)
-    tol = 1e-12 if prec == "fp64" else 2e-5
+    tol = 1e-12 if prec.startswith("fp64") else 2e-5
     assert np.all(np.abs(f[:, rows] - fo) <= tol * scale), (np.abs(f[:, rows] - fo) / scale).max()
     s.close()
 

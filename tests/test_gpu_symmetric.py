@@ -118,3 +118,17 @@ def test_symmetric_full_size_sampled_force_parity(model, N, eps):
     fo, scale = ora.force_rows(model, q, rows, eps, with_abs=True)
     assert np.all(np.abs(f[:, rows] - fo) <= 2e-5 * scale), (np.abs(f[:, rows] - fo) / scale).max()
     s.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256, 768])
+@pytest.mark.parametrize("N", [1, 255, 257, 1000, 4097])
+def test_symmetric_ring_cta_shapes(N, threads):
+    """The symmetric Ring kernel with 128-thread CTAs (4 m-blocks per warp) and
+    256-thread CTAs (2 m-blocks per warp; registers for 2 or 3 CTAs per SM)."""
+    s, q, _ = _sym(1, N)
+    s.set_tuning("sym_threads", threads)
+    f = s.force()
+    fo = ora.force(1, q, EPS[1])
+    scale = ora.force_abs(1, q, EPS[1])
+    err = np.abs(f - fo)
+    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
