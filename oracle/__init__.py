@@ -18,7 +18,7 @@ import threading
 
 import numpy as np
 
-HMF, RING, GRAV2D, HARMONIC = 0, 1, 2, 9
+HMF, RING, GRAV2D, GRAV3D, HARMONIC = 0, 1, 2, 3, 9
 OBS_KINETIC, OBS_MAGNETIZATION = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -82,7 +82,7 @@ def _arr(a) -> np.ndarray:
 
 
 def dim(model: int) -> int:
-    return 2 if model == GRAV2D else 1
+    return 2 if model == GRAV2D else 3 if model == GRAV3D else 1
 
 
 def yoshida() -> np.ndarray:
@@ -101,7 +101,8 @@ def magnetization(q) -> tuple[float, float]:
 
 
 def force(model: int, q, eps: float = 0.0) -> np.ndarray:
-    """Forces at q: Eq. 6 (HMF), minus the gradient of Eq. 1 (Ring) or Eq. 3 (2D)."""
+    """Forces at q: Eq. 6 (HMF), minus the gradient of Eq. 1 (Ring), Eq. 3 (2D) or of
+    the softened 3D gravitational potential (GRAV3D)."""
     q = _arr(q)
     f = np.empty_like(q)
     _load().ora_force(model, q.size // dim(model), eps, _p(q), _p(f))
@@ -117,7 +118,8 @@ def force_hmf_pairwise(q) -> np.ndarray:
 
 
 def potential(model: int, q, eps: float = 0.0) -> float:
-    """V of Eq. 5 (HMF), Eq. 1 (Ring), Eq. 3 (2D), with i<j pair sums."""
+    """V of Eq. 5 (HMF), Eq. 1 (Ring), Eq. 3 (2D) or the 3D gravitational potential,
+    with i<j pair sums."""
     q = _arr(q)
     return _load().ora_potential(model, q.size // dim(model), eps, _p(q))
 

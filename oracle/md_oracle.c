@@ -15,8 +15,9 @@
  *
  * Layout: positions q and momenta p are arrays of dim*N doubles.  dim = 1 for
  * HMF and Ring (q = theta), dim = 2 for the 2D model (q = [x_0..x_{N-1},
- * y_0..y_{N-1}], p = [px..., py...]).  A "harmonic" test model (f = -q) is
- * included only to pin the integrator's order.
+ * y_0..y_{N-1}], p = [px..., py...]), dim = 3 for 3D gravity (x block, y block,
+ * z block).  A "harmonic" test model (f = -q) is included only to pin the
+ * integrator's order.
  *
  * Readings of the paper taken here (each is pinned by a test):
  *  - Yoshida constants (Sec. 3, Eq. 4): the paper does not print B0, B1, D0,
@@ -33,6 +34,12 @@
  *  - 2D force (not printed): f_i = -(2/N) sum_j r_ij / (|r_ij|^2 + eps), from
  *    Eq. 3 with the natural log.
  *  - Energies use i<j pair sums (Eqs. 1-3); self terms are excluded.
+ *  - 3D self-gravitating particles (not in the paper; its introduction lists
+ *    self-gravitating systems among the long-range models and its conclusion
+ *    calls other N-particle systems a direct extension): unit masses with the
+ *    Kac 1/N coupling and the additive softening of Eqs. 1-3,
+ *    V = -(1/N) sum_{i<j} (|r_ij|^2 + eps)^(-1/2),
+ *    f_i = -(1/N) sum_j r_ij (|r_ij|^2 + eps)^(-3/2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -42,12 +49,13 @@
 #define ORA_HMF 0
 #define ORA_RING 1
 #define ORA_GRAV2D 2
+#define ORA_GRAV3D 3
 #define ORA_HARMONIC 9
 
 #define ORA_OBS_KINETIC 0
 #define ORA_OBS_MAGNETIZATION 1
 
-int ora_dim(int model) { return model == ORA_GRAV2D ? 2 : 1; }
+int ora_dim(int model) { return model == ORA_GRAV2D ? 2 : model == ORA_GRAV3D ? 3 : 1; }
 
 /* Sec. 3, Eq. 4: B0, B1, D0, D1 from the closed form of the triple jump. */
 void ora_yoshida(double c[4]) {
@@ -163,6 +171,40 @@ double ora_potential_2d(int64_t N, double eps, const double *q) {
   return v / (double)N;
 }
 
+/* ----------------------------------------------------------------- 3D ---- */
+
+/* Minus the gradient of V below: f_i = -(1/N) sum_{j != i} r_ij / (|r_ij|^2 + eps)^(3/2). */
+void ora_force_3d(int64_t N, double eps, const double *q, double *f) {
+  const double *x = q, *y = q + N, *z = q + 2 * N;
+  for (int64_t i = 0; i < N; i++) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t j = 0; j < N; j++) {
+      if (j == i) continue;
+      double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+      double s = dx * dx + dy * dy + dz * dz + eps;
+      double w = 1.0 / (s * sqrt(s));
+      sx += dx * w;
+      sy += dy * w;
+      sz += dz * w;
+    }
+    f[i] = -sx / (double)N;
+    f[N + i] = -sy / (double)N;
+    f[2 * N + i] = -sz / (double)N;
+  }
+}
+
+/* V = -(1/N) sum_{i<j} (|r_ij|^2 + eps)^(-1/2). */
+double ora_potential_3d(int64_t N, double eps, const double *q) {
+  const double *x = q, *y = q + N, *z = q + 2 * N;
+  double v = 0.0;
+  for (int64_t i = 0; i < N; i++)
+    for (int64_t j = i + 1; j < N; j++) {
+      double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+      v += 1.0 / sqrt(dx * dx + dy * dy + dz * dz + eps);
+    }
+  return -v / (double)N;
+}
+
 /* ------------------------------------------------------------ generic ---- */
 
 void ora_force(int model, int64_t N, double eps, const double *q, double *f) {
@@ -170,6 +212,7 @@ void ora_force(int model, int64_t N, double eps, const double *q, double *f) {
   case ORA_HMF: ora_force_hmf(N, q, f); break;
   case ORA_RING: ora_force_ring(N, eps, q, f); break;
   case ORA_GRAV2D: ora_force_2d(N, eps, q, f); break;
+  case ORA_GRAV3D: ora_force_3d(N, eps, q, f); break;
   case ORA_HARMONIC:
     for (int64_t i = 0; i < N; i++) f[i] = -q[i];
     break;
@@ -181,6 +224,7 @@ double ora_potential(int model, int64_t N, double eps, const double *q) {
   case ORA_HMF: return ora_potential_hmf(N, q);
   case ORA_RING: return ora_potential_ring(N, eps, q);
   case ORA_GRAV2D: return ora_potential_2d(N, eps, q);
+  case ORA_GRAV3D: return ora_potential_3d(N, eps, q);
   case ORA_HARMONIC: {
     double v = 0.0;
     for (int64_t i = 0; i < N; i++) v += 0.5 * q[i] * q[i];
@@ -233,6 +277,23 @@ void ora_force_abs(int model, int64_t N, double eps, const double *q, double *ou
       }
       out[i] = 2.0 * sx / (double)N;
       out[N + i] = 2.0 * sy / (double)N;
+    }
+  } else if (model == ORA_GRAV3D) {
+    const double *x = q, *y = q + N, *z = q + 2 * N;
+    for (int64_t i = 0; i < N; i++) {
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+        double s = dx * dx + dy * dy + dz * dz + eps;
+        double w = 1.0 / (s * sqrt(s));
+        sx += fabs(dx) * w;
+        sy += fabs(dy) * w;
+        sz += fabs(dz) * w;
+      }
+      out[i] = sx / (double)N;
+      out[N + i] = sy / (double)N;
+      out[2 * N + i] = sz / (double)N;
     }
   } else {
     for (int64_t i = 0; i < N; i++) out[i] = fabs(q[i]);
@@ -291,6 +352,32 @@ void ora_force_rows(int model, int64_t N, double eps, const double *q, const int
       if (out_abs) {
         out_abs[r] = 2.0 * ax / (double)N;
         out_abs[nrows + r] = 2.0 * ay / (double)N;
+      }
+    }
+  } else if (model == ORA_GRAV3D) {
+    const double *x = q, *y = q + N, *z = q + 2 * N;
+    for (int64_t r = 0; r < nrows; r++) {
+      int64_t i = rows[r];
+      double sx = 0.0, sy = 0.0, sz = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+        double s = dx * dx + dy * dy + dz * dz + eps;
+        double w = 1.0 / (s * sqrt(s));
+        sx += dx * w;
+        sy += dy * w;
+        sz += dz * w;
+        ax += fabs(dx) * w;
+        ay += fabs(dy) * w;
+        az += fabs(dz) * w;
+      }
+      out[r] = -sx / (double)N;
+      out[nrows + r] = -sy / (double)N;
+      out[2 * nrows + r] = -sz / (double)N;
+      if (out_abs) {
+        out_abs[r] = ax / (double)N;
+        out_abs[nrows + r] = ay / (double)N;
+        out_abs[2 * nrows + r] = az / (double)N;
       }
     }
   }

@@ -13,7 +13,7 @@ A uniform is (x >> 11) * 2^-53 in [0, 1).  A Gaussian uses two consecutive
 uniforms u1, u2 (Box-Muller 1958): sqrt(-2 log(1 - u1)) cos(2 pi u2).
 
 Draw order: all positions first (counters 0 .. dim*N - 1; the disk uses two
-counters per particle), then all momenta.  Affine maps are evaluated as
+counters per particle, the ball three), then all momenta.  Affine maps are evaluated as
 (hi - lo) * u + lo with two separate roundings.
 """
 from __future__ import annotations
@@ -31,6 +31,7 @@ IC_RING = 1       # Ring: theta ~ U[-pi, pi), p ~ N(0, sigma^2)
 IC_DISK = 2       # 2D: uniform unit disk, p ~ N(0, sigma^2) per component
 IC_ANNULUS = 3    # 2D: uniform annulus R1 <= r < R2, at rest
 IC_UNIFORM_REST = 4  # angle models: theta ~ U[-pi, pi), at rest
+IC_BALL = 5       # 3D: uniform unit ball, p ~ N(0, sigma^2) per component
 
 
 def splitmix64(seed: int, counters: np.ndarray) -> np.ndarray:
@@ -94,19 +95,35 @@ def annulus_state(N: int, seed: int, r1=1.0, r2=1.5):
     return q, np.zeros(2 * N)
 
 
+def ball_state(N: int, seed: int, sigma=0.3):
+    """3D: uniform in the unit ball (r = u1^(1/3), cos(polar angle) = 1 - 2 u2,
+    azimuth = 2 pi u3, counters 3i .. 3i + 2), p ~ N(0, sigma^2) per component
+    (x block, then y, then z)."""
+    u = uniform(seed, 0, 3 * N)
+    r = np.cbrt(u[0::3])
+    ct = 1.0 - 2.0 * u[1::3]
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    phi = _TWO_PI * u[2::3]
+    q = np.concatenate([r * st * np.cos(phi), r * st * np.sin(phi), r * ct])
+    p = sigma * gaussian(seed, 3 * N, 3 * N)
+    return q, p
+
+
 def uniform_rest(N: int, seed: int):
     """Angle models at rest: theta ~ U[-pi, pi), p = 0."""
     return _affine(uniform(seed, 0, N), -np.pi, np.pi), np.zeros(N)
 
 
 def default_state(model: int, N: int, seed: int):
-    """Per-model default initial state: water-bag (HMF), ring_state, disk_state."""
+    """Per-model default initial state: water-bag (HMF), ring_state, disk_state, ball_state."""
     if model == 0:
         return waterbag(N, seed)
     if model == 1:
         return ring_state(N, seed)
     if model == 2:
         return disk_state(N, seed)
+    if model == 3:
+        return ball_state(N, seed)
     raise ValueError(f"unknown model {model}")
 
 

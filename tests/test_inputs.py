@@ -50,3 +50,20 @@ def test_counter_based_draws_are_prefix_stable():
     a = inputs.uniform(9, 0, 100)
     b = inputs.uniform(9, 40, 20)
     assert np.array_equal(a[40:60], b)
+
+
+def test_ball_state_recipe():
+    """3D ball: deterministic, inside the unit ball, uniform in volume (mean r^3 = 1/2,
+    mean z = 0), counters 3i..3i+2 per particle, then Gaussian momenta."""
+    q, p = inputs.ball_state(20000, 5)
+    q2, p2 = inputs.ball_state(20000, 5)
+    assert np.array_equal(q, q2) and np.array_equal(p, p2)
+    r = np.sqrt(q[:20000] ** 2 + q[20000:40000] ** 2 + q[40000:] ** 2)
+    assert r.max() <= 1.0 + 1e-15
+    assert abs(np.mean(r ** 3) - 0.5) < 0.01
+    assert abs(np.mean(q[40000:])) < 0.01
+    u = inputs.uniform(5, 0, 3)
+    assert abs(r[0] - np.cbrt(u[0])) < 1e-15 and abs(q[40000] - np.cbrt(u[0]) * (1 - 2 * u[1])) < 1e-15
+    assert abs(np.std(p) - 0.3) < 0.01
+    q3, p3 = inputs.default_state(3, 10, 2)
+    assert q3.size == 30 and p3.size == 30

@@ -24,6 +24,8 @@ def _state(model, N, seed):
         return inputs.waterbag(N, seed)
     if model == 1:
         return inputs.ring_state(N, seed)
+    if model == 3:
+        return inputs.ball_state(N, seed)
     return inputs.disk_state(N, seed)
 
 
@@ -115,7 +117,7 @@ def test_hmf_meanfield_equals_pairwise(ora, N):
     assert abs(v_mf - v_pw) <= 1e-13 * max(1.0, N)
 
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5), (3, 1e-3), (3, 0.5)])
 def test_force_is_minus_gradient_of_potential(ora, model, eps):
     N = 12
     q, _ = _state(model, N, 21)
@@ -131,12 +133,12 @@ def test_force_is_minus_gradient_of_potential(ora, model, eps):
     assert np.max(np.abs(fd - f)) < 2e-7 * scale, np.max(np.abs(fd - f)) / scale
 
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3), (3, 1e-3)])
 def test_total_momentum_conserved(ora, model, eps):
     N = 40
     q0, p0 = _state(model, N, 31)
     q, p = ora.step(model, q0, p0, eps, 0.05, 20)
-    d = 2 if model == 2 else 1
+    d = {2: 2, 3: 3}.get(model, 1)
     for c in range(d):
         tot0 = p0[c * N:(c + 1) * N].sum()
         tot = p[c * N:(c + 1) * N].sum()
@@ -154,6 +156,66 @@ def test_angular_momentum_conserved_2d(ora):
     assert abs(lz(q, p) - lz(q0, p0)) < 1e-12 * np.sum(np.abs(q0) * np.abs(p0).max()) * 20
 
 
+def test_angular_momentum_conserved_3d(ora):
+    N = 40
+    q0, p0 = inputs.ball_state(N, 43)
+
+    def L(q, p):
+        r, v = q.reshape(3, N).T, p.reshape(3, N).T
+        return np.cross(r, v).sum(axis=0)
+
+    q, p = ora.step(3, q0, p0, 1e-3, 0.05, 20)
+    scale = np.sum(np.abs(q0)) * np.abs(p0).max()
+    assert np.max(np.abs(L(q, p) - L(q0, p0))) < 1e-12 * scale * 20
+
+
+def test_3d_shell_theorem(ora):
+    """Newton's shell theorem: 12 unit masses on the vertices of an icosahedron of
+    radius a (a spherical 5-design: its multipole moments of orders 1 to 5 vanish)
+    act on a distant test mass like 12 masses at the centre, up to O((a/D)^6)."""
+    phi = (1 + math.sqrt(5)) / 2
+    verts = []
+    for s1 in (-1, 1):
+        for s2 in (-1, 1):
+            verts += [(0, s1, s2 * phi), (s1, s2 * phi, 0), (s2 * phi, 0, s1)]
+    v = np.array(verts, dtype=float)
+    a, D = 0.05, 1.0
+    v *= a / np.linalg.norm(v[0])
+    test = np.array([[0.6, -0.48, 0.64]]) * D  # |test| = D, a generic direction
+    r = np.vstack([v, test])
+    N = r.shape[0]
+    q = r.T.reshape(-1)
+    f = ora.force(3, q, 0.0).reshape(3, N)[:, -1]
+    f_point = -(12.0 / N) * test[0] / D ** 3
+    assert np.max(np.abs(f - f_point)) < 1e-6 * np.linalg.norm(f_point)
+    # and the potential energy of the test mass, to the same order
+    V_all = ora.potential(3, q, 0.0)
+    V_shell = ora.potential(3, v.T.reshape(-1), 0.0) * 12 / N  # same 1/N coupling
+    assert abs((V_all - V_shell) - (-12.0 / (N * D))) < 1e-6 * 12.0 / (N * D)
+
+
+def test_3d_two_body_circular_orbit(ora):
+    """Two unit masses at separation d with speeds v = 1/(2 sqrt(d)) (eps = 0, N = 2:
+    coupling 1/2) move on a circle: the separation stays d and they are back at the
+    start after one period 2 pi (d/2) / v."""
+    d = 1.0
+    v = 1.0 / (2.0 * math.sqrt(d))
+    T = 2 * math.pi * (d / 2) / v
+    q0 = np.array([d / 2, -d / 2, 0.0, 0.0, 0.0, 0.0])
+    p0 = np.array([0.0, 0.0, v, -v, 0.0, 0.0])
+    n = 800
+    q, p = q0.copy(), p0.copy()
+    for _ in range(4):
+        q, p = ora.step(3, q, p, 0.0, T / n, n // 4)
+        sep = np.linalg.norm(q.reshape(3, 2)[:, 0] - q.reshape(3, 2)[:, 1])
+        assert abs(sep - d) < 2e-8
+    err = np.max(np.abs(q - q0))
+    assert err < 5e-8 and np.max(np.abs(p - p0)) < 5e-8
+    # fourth order: halving the step divides the return error by about 16
+    q2, _ = ora.step(3, q0, p0, 0.0, T / (n // 2), n // 2)
+    assert 12.0 < np.max(np.abs(q2 - q0)) / err < 20.0
+
+
 def test_special_cases(ora):
     # one HMF particle feels no force and drifts freely
     q, p = ora.step(ora.HMF, np.array([0.7]), np.array([0.25]), 0.0, 0.1, 10)
@@ -167,13 +229,15 @@ def test_special_cases(ora):
     assert np.max(np.abs(fr)) < 1e-13 * np.max(ora.force_abs(ora.RING, lat, 0.01))
     # two bodies: equal and opposite forces
     for model, eps, q in ((1, 0.01, np.array([0.3, -0.4])),
-                          (2, 1e-3, np.array([0.1, -0.2, 0.05, 0.3]))):
+                          (2, 1e-3, np.array([0.1, -0.2, 0.05, 0.3])),
+                          (3, 1e-3, np.array([0.1, -0.2, 0.05, 0.3, -0.1, 0.2]))):
         f = ora.force(model, q, eps)
         if model == 1:
             assert abs(f[0] + f[1]) < 1e-16
             assert f[0] < 0  # attraction: particle 0 sits at larger angle
         else:
-            assert abs(f[0] + f[1]) < 1e-16 and abs(f[2] + f[3]) < 1e-16
+            for c in range(model):
+                assert abs(f[2 * c] + f[2 * c + 1]) < 1e-16
             assert f[0] < 0 and f[2] > 0  # pulled toward particle 1
     # particles at rest have K = 0
     assert ora.kinetic(np.zeros(10)) == 0.0
@@ -247,6 +311,15 @@ def test_step_matches_grad_forward_pass(ora):
     q, p = ora.step(1, q0, p0, 0.01, 0.05, 7)
     val, *_ = ora.grad(1, q0, p0, 0.01, 0.05, 7, 0)
     assert val == ora.kinetic(p)
+
+
+def test_force_rows_equals_full_force_3d(ora):
+    q, _ = inputs.ball_state(50, 71)
+    full = ora.force(3, q, 1e-3).reshape(3, 50)
+    rows = np.array([0, 7, 49])
+    fr, ab = ora.force_rows(3, q, rows, 1e-3, with_abs=True)
+    assert np.max(np.abs(fr - full[:, rows])) < 1e-15
+    assert np.allclose(ab, ora.force_abs(3, q, 1e-3).reshape(3, 50)[:, rows], rtol=1e-14, atol=0)
 
 
 @pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
