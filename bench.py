@@ -38,6 +38,8 @@ WORKLOADS = {
                  name="Ring N=131,072 eps=0.01 dt=0.05 (all-pairs)"),
     "grav2d": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
                    name="2D self-gravitating N=262,144 eps=1e-4 dt=0.01 (all-pairs)"),
+    "grav3d": dict(model=3, N=131_072, eps=1e-3, dt=0.01, seed=5, unit="pair-interactions/s",
+                   name="3D self-gravitating N=131,072 eps=1e-3 dt=0.01 (all-pairs; not one of the paper's models)"),
     "adjoint": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
                     name="2D N=262,144 eps=1e-4 dt=0.01: gradient of K(T) after 100 steps (forward + "
                          "reversed adjoint, checkpoints every 20 steps)"),
@@ -48,20 +50,23 @@ WORKLOADS = {
 # algorithmic bytes per particle per fused HMF stage: read + write FP64 theta and p
 HMF_BYTES_PER_PARTICLE_STAGE = 32
 # FP32-pipe operations and SFU operations per pair in the mixed pair kernels
-PAIR_OPS = {1: (8, 1), 2: (6, 1)}
+PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1)}
 # Per force-kernel variant (md_force_kernel): name, FP32 operations and SFU operations
 # per evaluated pair term, and whether each unordered pair is evaluated once.
 #   one-sided Ring: S and sin(d/2) (2 FMA + 2 MUL), dd (FMA), y^2, S y, acc (FMA) -> 8
 #   tensor-core Ring: S and sin(d/2) on the tensor cores -> 4
 #   one-sided 2D: dx, dy, |r|^2 + eps (2 FMA), fx, fy -> 6
-#   symmetric: + 1 (Ring) / 2 (2D) column accumulations per pair term, plus the
-#   butterfly adds (1/8 per term for Ring, 1/4 for 2D)
+#   one-sided 3D: dx, dy, dz, |r|^2 + eps (3 FMA), y^3 (2 MUL), fx, fy, fz -> 11
+#   symmetric: + 1 (Ring) / 2 (2D) / 3 (3D) column accumulations per pair term, plus
+#   the butterfly adds (1/8 per term for Ring, 1/4 for 2D, 3/4 for 3D at 4 rows/thread)
 PAIR_KERNELS = {
     (1, 2): ("streamk_kernel<RingMixed<8,256>>", 8, 1, False),
     (1, 3): ("streamk_kernel<RingTC<4,256>>", 4, 1, False),
     (1, 5): ("sym_kernel<RingTC<4,256>>", 5.125, 1, True),
     (2, 2): ("streamk_kernel<GravMixed<8,256>>", 6, 1, False),
     (2, 4): ("sym_kernel<GravMixed<8,256>>", 8.25, 1, True),
+    (3, 2): ("streamk_kernel<Grav3DMixed<4,256>>", 11, 1, False),
+    (3, 4): ("sym_kernel<Grav3DMixed<4,256>>", 14.75, 1, True),
 }
 
 
@@ -79,7 +84,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
-    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "ensemble": (20, 3), "adjoint": (1, 0)}[a.workload]
+    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "ensemble": (20, 3),
+            "adjoint": (1, 0)}[a.workload]
     if a.steps is None:
         a.steps = dflt[0]
     if a.warmup is None:
@@ -367,7 +373,7 @@ def run_ours(args, w):
         binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 19)
         nsm = rates[0]
         fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
-        sfu_rate = rates[5] if model == 1 else rates[7]
+        sfu_rate = rates[5] if model in (1, 3) else rates[7]  # rsqrt (Ring, 3D) or rcp (2D)
         kcode = sysm.force_kernel
         kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
         pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops)

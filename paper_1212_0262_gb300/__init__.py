@@ -2,13 +2,14 @@
 
 The force evaluation inside the fourth-order symplectic integrator of Sec. 3 for
 the HMF (Eqs. 2, 5-7), Ring (Eqs. 1, 8-9) and 2D self-gravitating (Eq. 3)
-models, as hand-written sm_103a CUDA kernels behind the C ABI of include/md.h.
+models, and a 3D self-gravitating model with the same coupling and softening, as
+hand-written sm_103a CUDA kernels behind the C ABI of include/md.h.
 """
 from . import binding
 from .binding import MDError
 from .system import Ensemble, System
 
-HMF, RING, GRAV2D = 0, 1, 2
+HMF, RING, GRAV2D, GRAV3D = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 
-__all__ = ["binding", "MDError", "System", "Ensemble", "HMF", "RING", "GRAV2D", "FP64", "MIXED"]
+__all__ = ["binding", "MDError", "System", "Ensemble", "HMF", "RING", "GRAV2D", "GRAV3D", "FP64", "MIXED"]

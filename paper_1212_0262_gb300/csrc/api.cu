@@ -150,7 +150,7 @@ void md_free(md_ctx *c) {
 }
 
 md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
-  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D) {
+  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D) {
     fail_global(MD_EINVAL, "md_init: unknown model %d", model);
     return nullptr;
   }
@@ -172,7 +172,7 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
     return nullptr;
   }
   c->model = model;
-  c->dim = model == MD_GRAV2D ? 2 : 1;
+  c->dim = model == MD_GRAV2D ? 2 : model == MD_GRAV3D ? 3 : 1;
   c->N = N;
   c->eps = eps;
   c->dt = dt;
@@ -211,7 +211,10 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
     md_free(c);
     return nullptr;
   }
-  const int kind = model == MD_HMF ? MD_IC_WATERBAG : model == MD_RING ? MD_IC_RING : MD_IC_DISK;
+  const int kind = model == MD_HMF    ? MD_IC_WATERBAG
+                   : model == MD_RING ? MD_IC_RING
+                   : model == MD_GRAV2D ? MD_IC_DISK
+                                        : MD_IC_BALL;
   if (ic_draw(c, kind, nullptr, seed) != MD_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     g_err = c->err.empty() ? std::string("md_init: initial state") : c->err;
     md_free(c);
@@ -521,6 +524,8 @@ int md_energy(md_ctx *c, double *K, double *V) {
     pot = 0.5 * n * (1.0 - mx * mx - my * my);  // Eq. 5
   } else if (c->model == MD_RING) {
     pot = -c->host_scalars[1] / (2.0 * n);  // Eq. 1 with 1 - cos + eps = 2 (sin^2(d/2) + eps/2)
+  } else if (c->model == MD_GRAV3D) {
+    pot = -c->host_scalars[1] / n;  // softened 3D gravitational potential
   } else {
     pot = c->host_scalars[1] / n;  // Eq. 3
   }
@@ -532,7 +537,8 @@ int md_energy(md_ctx *c, double *K, double *V) {
 
 int md_magnetization(md_ctx *c, double *mx, double *my) {
   CHECK_CTX(c);
-  if (c->model == MD_GRAV2D) return set_err(c, MD_EINVAL, "md_magnetization: not defined for the 2D model");
+  if (c->model == MD_GRAV2D || c->model == MD_GRAV3D)
+    return set_err(c, MD_EINVAL, "md_magnetization: defined for the HMF and Ring models only");
   double *d = c->hmf_m + 12;
   int rc = hmf_sums_fp64(c, d);
   if (rc) return rc;

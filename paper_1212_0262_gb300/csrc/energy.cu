@@ -1,4 +1,5 @@
-// FP64 observables: kinetic energy and the pair potentials of Eqs. 1 and 3.
+// FP64 observables: kinetic energy and the pair potentials of Eqs. 1 and 3 (and
+// of the 3D self-gravitating model).
 //
 // All sums are deterministic: per-thread sums, a fixed shuffle/block tree, one
 // partial per CTA (or per tile pair), and a final pass that adds the partials in
@@ -97,6 +98,39 @@ __global__ void __launch_bounds__(NT) potential_tiles_kernel(const double *__res
   if (threadIdx.x == 0) unit_sums[(int64_t)ti * ntiles + tj] = b.x;
 }
 
+// 3D: one tile pair (ti <= tj) of sum_{i<j} (|r_ij|^2 + eps)^(-1/2); the prefactor
+// -1/N is applied at the end.
+__global__ void __launch_bounds__(NT) potential3d_tiles_kernel(const double *__restrict__ q, int64_t N, int ntiles,
+                                                                double eps, double *unit_sums) {
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (tj < ti) return;
+  __shared__ double sx[PT], sy[PT], sz[PT];
+  const int64_t j0 = (int64_t)tj * PT;
+  for (int t = threadIdx.x; t < PT; t += NT) {
+    const int64_t j = j0 + t;
+    if (j < N) {
+      sx[t] = q[j];
+      sy[t] = q[N + j];
+      sz[t] = q[2 * N + j];
+    }
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)ti * PT + threadIdx.x;
+  double s = 0.0;
+  if (i < N) {
+    const double x = q[i], y = q[N + i], z = q[2 * N + i];
+    const int kbeg = ti == tj ? threadIdx.x + 1 : 0;  // j > i inside the diagonal tile
+    const int kend = (int)((N - j0) < PT ? (N - j0) : PT);
+    for (int k = kbeg; k < kend; k++) {
+      const double dx = x - sx[k], dy = y - sy[k], dz = z - sz[k];
+      s += rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, eps))));
+    }
+  }
+  __shared__ double2 red[NT / 32];
+  double2 b = block_sum2<NT>(s, 0.0, red);
+  if (threadIdx.x == 0) unit_sums[(int64_t)ti * ntiles + tj] = b.x;
+}
+
 int grid_sum(md_ctx *c, int64_t n) {
   int64_t g = (n + NT - 1) / NT;
   int64_t cap = (int64_t)c->nsm * 8;
@@ -117,6 +151,8 @@ __global__ void potential_finalize_kernel(int model, int64_t N, const double *su
     *V = 0.5 * n * (1.0 - mx * mx - my * my);
   } else if (model == MD_RING) {
     *V = -sums[0] / (2.0 * n);
+  } else if (model == MD_GRAV3D) {
+    *V = -sums[0] / n;
   } else {
     *V = sums[0] / n;
   }
@@ -140,6 +176,8 @@ int potential_with_scratch(cudaStream_t st, int nsm, int grid_cap, int model, in
       if (b > (int64_t)nsm * 16) b = (int64_t)nsm * 16;
       half_angle_kernel<<<(int)b, 256, 0, st>>>(q, N, ag);
       potential_tiles_kernel<MD_RING><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, ag, N, ntiles, 0.5 * eps, unit_sums);
+    } else if (model == MD_GRAV3D) {
+      potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
     } else {
       potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, nullptr, N, ntiles, eps, unit_sums);
     }
@@ -186,8 +224,8 @@ int sum_fp64(md_ctx *c, const double *x, int64_t n, double *d_out) {
   return MD_OK;
 }
 
-// Pair-sum part of the potential of Eq. 1 (Ring) or Eq. 3 (2D), prefactor
-// applied, into device *d_out.  Uses ctx->red as scratch.
+// Pair-sum part of the potential of Eq. 1 (Ring), Eq. 3 (2D) or of the 3D model,
+// prefactor applied by the caller, into device *d_out.  Uses ctx->red as scratch.
 int pair_potential_fp64(md_ctx *c, double *d_out) {
   const int64_t N = c->N;
   const int ntiles = (int)((N + PT - 1) / PT);
@@ -207,6 +245,8 @@ int pair_potential_fp64(md_ctx *c, double *d_out) {
     MD_LAUNCHED(c);
     potential_tiles_kernel<MD_RING><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, ag, N, ntiles, 0.5 * c->eps,
                                                                                 unit_sums);
+  } else if (c->model == MD_GRAV3D) {
+    potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
   } else {
     potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, nullptr, N, ntiles, c->eps,
                                                                                   unit_sums);

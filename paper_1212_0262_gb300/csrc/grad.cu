@@ -21,6 +21,7 @@ extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint
   if (!c) return set_err(nullptr, MD_EINVAL, "md_grad: NULL context");
   if (observable != MD_OBS_KINETIC && observable != MD_OBS_MAGNETIZATION)
     return set_err(c, MD_EINVAL, "md_grad: unknown observable %d", observable);
+  if (c->model == MD_GRAV3D) return set_err(c, MD_EINVAL, "md_grad: not available for the 3D model");
   if (observable == MD_OBS_MAGNETIZATION && c->model == MD_GRAV2D)
     return set_err(c, MD_EINVAL, "md_grad: the magnetization is defined for HMF and Ring only");
   if (nsteps < 0 || checkpoint_every < 1) return set_err(c, MD_EINVAL, "md_grad: need nsteps >= 0, checkpoint_every >= 1");

@@ -76,6 +76,19 @@ __global__ void ic_kernel(IcArgs a) {
       }
       break;
     }
+    case MD_IC_BALL: {  // a2 = sigma; counters 3i .. 3i+2, then Gaussian momenta
+      double u = u01(a.seed, 3 * ui), v = u01(a.seed, 3 * ui + 1), w = u01(a.seed, 3 * ui + 2);
+      double r = cbrt(u);
+      double ct = __dsub_rn(1.0, __dmul_rn(2.0, v));
+      double st = sqrt(fmax(0.0, __dsub_rn(1.0, __dmul_rn(ct, ct))));
+      double phi = __dmul_rn(two_pi, w);
+      double rs = __dmul_rn(r, st);
+      a.q[i] = __dmul_rn(rs, cos(phi));
+      a.q[N + i] = __dmul_rn(rs, sin(phi));
+      a.q[2 * N + i] = __dmul_rn(r, ct);
+      for (int d = 0; d < 3; d++) a.p[d * N + i] = __dmul_rn(a.a2, gauss(a.seed, 3 * un + 2 * (d * un + ui)));
+      break;
+    }
     }
   }
 }
@@ -90,7 +103,7 @@ int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed) {
   a.kind = kind;
   a.seed = seed;
   a.a0 = a.a1 = a.a2 = a.a3 = 0.0;
-  const bool angle = c->model != MD_GRAV2D;
+  const bool angle = c->model == MD_HMF || c->model == MD_RING;
   switch (kind) {
   case MD_IC_WATERBAG:
     if (!angle) return set_err(c, MD_EINVAL, "water-bag needs an angle model");
@@ -117,18 +130,23 @@ int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed) {
     a.a1 = -M_PI;
     break;
   case MD_IC_DISK:
-    if (angle) return set_err(c, MD_EINVAL, "disk needs the 2D model");
+    if (c->model != MD_GRAV2D) return set_err(c, MD_EINVAL, "disk needs the 2D model");
     a.a2 = params ? params[0] : 0.3;
     if (!(a.a2 >= 0.0)) return set_err(c, MD_EINVAL, "sigma must be >= 0");
     break;
   case MD_IC_ANNULUS: {
-    if (angle) return set_err(c, MD_EINVAL, "annulus needs the 2D model");
+    if (c->model != MD_GRAV2D) return set_err(c, MD_EINVAL, "annulus needs the 2D model");
     double r1 = params ? params[0] : 1.0, r2 = params ? params[1] : 1.5;
     if (!(r1 >= 0.0) || !(r2 > r1)) return set_err(c, MD_EINVAL, "annulus: need 0 <= r1 < r2");
     a.a0 = r2 * r2 - r1 * r1;
     a.a1 = r1 * r1;
     break;
   }
+  case MD_IC_BALL:
+    if (c->model != MD_GRAV3D) return set_err(c, MD_EINVAL, "ball needs the 3D model");
+    a.a2 = params ? params[0] : 0.3;
+    if (!(a.a2 >= 0.0)) return set_err(c, MD_EINVAL, "sigma must be >= 0");
+    break;
   default:
     return set_err(c, MD_EINVAL, "unknown initial-state kind %d", kind);
   }

@@ -62,7 +62,7 @@ int setup(int dev, double **addr, int *nsm) {
 }  // namespace
 
 extern "C" int md_potential_noalloc(int model, int64_t N, double eps, const double *q, double *V, void *stream) {
-  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D)
+  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D)
     return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: unknown model %d", model);
   if (N < 1 || N > kMaxN)
     return set_err(nullptr, MD_EINVAL,

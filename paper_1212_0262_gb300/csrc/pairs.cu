@@ -163,6 +163,15 @@ __global__ void mirror_kernel(const double *__restrict__ q, const double *__rest
                               void *m0, void *m1) {
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Npad; i += G) {
+    if constexpr (MODEL == MD_GRAV3D) {
+      if (i < N) {
+        write_record3<MIXED>(m0, i, q[i], q[N + i], q[2 * N + i]);
+      } else {
+        write_pad3<MIXED>(m0, i);
+        if (m1) write_pad3<MIXED>(m1, i);
+      }
+      continue;
+    }
     if (i < N) {
       const double y = MODEL == MD_GRAV2D ? q[N + i] : 0.0;
       const double vx = ADJ ? lp[i] : 0.0, vy = (ADJ && MODEL == MD_GRAV2D) ? lp[N + i] : 0.0;
@@ -179,7 +188,7 @@ template <int MODEL, bool MIXED, int FMT>
 __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restrict__ p,
                                          const double *__restrict__ f, int64_t N, double kick,
                                          double drift, void *mirror_out) {
-  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  constexpr int D = dim_of<MODEL>();
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
     double x[D];
@@ -190,7 +199,10 @@ __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restr
       x[d] = fma(drift, pp, q[d * N + i]);
       q[d * N + i] = x[d];
     }
-    write_record_fmt<MODEL, MIXED, false, FMT>(mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+    if constexpr (MODEL == MD_GRAV3D)
+      write_record3<MIXED>(mirror_out, i, x[0], x[1], x[D - 1]);
+    else
+      write_record_fmt<MODEL, MIXED, false, FMT>(mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
   }
 }
 
@@ -204,7 +216,9 @@ int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadM
 int ensure_mirrors(md_ctx *c, bool adj) {
   const int64_t Np = padded(c->N);
   // the FP64 record bounds the FP32 one
-  const size_t per = c->model == MD_RING ? (adj ? 48 : 64) : (adj ? 32 : 16);  // Ring forward: tensor-core record
+  const size_t per = c->model == MD_RING     ? (adj ? 48 : 64)  // Ring forward: tensor-core record
+                     : c->model == MD_GRAV3D ? 32
+                                             : (adj ? 32 : 16);
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
     for (int b = 0; b < 2; b++) {
@@ -253,7 +267,10 @@ int launch_streamk(md_ctx *c, PairArgs a) {
 
 template <int MODEL, bool MIXED, int MODE>
 int dispatch_forward(md_ctx *c, PairArgs a) {
-  if constexpr (MIXED) {
+  if constexpr (MODEL == MD_GRAV3D) {
+    if constexpr (MIXED) return launch_streamk<Grav3DMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    else return launch_streamk<Grav3DF64<2, 128, MODE>, MODEL, MIXED, MODE>(c, a);
+  } else if constexpr (MIXED) {
     if (c->pt.r_mixed == 4) {
       if constexpr (MODEL == MD_RING) return launch_streamk<RingMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
       else return launch_streamk<GravMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
@@ -299,6 +316,9 @@ int refresh(md_ctx *c, const double *lp) {
       mirror_kernel<MD_RING, true, false, 1><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else if (mixed) mirror_kernel<MD_RING, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_RING, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+  } else if (c->model == MD_GRAV3D) {
+    if (mixed) mirror_kernel<MD_GRAV3D, true, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else mirror_kernel<MD_GRAV3D, false, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   } else {
     if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
@@ -361,6 +381,8 @@ int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
   const bool mixed = c->prec == MD_MIXED;
   if (c->model == MD_RING)
     return mixed ? dispatch_mode<MD_RING, true>(c, mode, a) : dispatch_mode<MD_RING, false>(c, mode, a);
+  if (c->model == MD_GRAV3D)
+    return mixed ? dispatch_mode<MD_GRAV3D, true>(c, mode, a) : dispatch_mode<MD_GRAV3D, false>(c, mode, a);
   return mixed ? dispatch_mode<MD_GRAV2D, true>(c, mode, a) : dispatch_mode<MD_GRAV2D, false>(c, mode, a);
 }
 
@@ -411,6 +433,9 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
       kick_drift_cached_kernel<MD_RING, true, 1><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else if (mixed) kick_drift_cached_kernel<MD_RING, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_RING, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+  } else if (c->model == MD_GRAV3D) {
+    if (mixed) kick_drift_cached_kernel<MD_GRAV3D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else kick_drift_cached_kernel<MD_GRAV3D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   } else {
     if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);

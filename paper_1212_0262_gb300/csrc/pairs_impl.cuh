@@ -14,9 +14,44 @@ constexpr int kPadMultiple = 1024;  // mirror padding: multiple of every TI and 
 // bytes per particle of a mirror record
 template <int MODEL, bool MIXED, bool ADJ>
 struct RecordBytes {
-  static constexpr int value =
-      MODEL == MD_RING ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32)) : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
+  static constexpr int value = MODEL == MD_RING     ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32))
+                               : MODEL == MD_GRAV3D ? (MIXED ? 16 : 32)
+                                                    : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
 };
+
+// spatial components of a model's positions
+template <int MODEL>
+constexpr int dim_of() {
+  return MODEL == MD_GRAV2D ? 2 : MODEL == MD_GRAV3D ? 3 : 1;
+}
+
+// 3D records: FP32, per particle pair (2k, 2k+1) the floats (-x, -x', -y, -y'),
+// (-z, -z', 0, 0); FP64, per particle (x, y, z, 0).  Padding: far enough that
+// |r|^2 overflows (FP32: 3e19 per component; FP64: 1e150, whose FP32 seed of the
+// reciprocal square root is 0 and stays 0), so its terms are exactly zero.
+template <bool MIXED>
+__device__ __forceinline__ void write_record3(void *mirror, int64_t i, double x, double y, double z) {
+  if constexpr (MIXED) {
+    float *m = (float *)mirror + (i >> 1) * 8 + (i & 1);
+    m[0] = -(float)x;
+    m[2] = -(float)y;
+    m[4] = -(float)z;
+    m[6] = 0.f;
+  } else {
+    double *m = (double *)mirror + i * 4;
+    m[0] = x;
+    m[1] = y;
+    m[2] = z;
+    m[3] = 0.0;
+  }
+}
+template <bool MIXED>
+__device__ __forceinline__ void write_pad3(void *mirror, int64_t i) {
+  if constexpr (MIXED)
+    write_record3<true>(mirror, i, 3.0e19, 3.0e19, 3.0e19);
+  else
+    write_record3<false>(mirror, i, 1.0e150, 1.0e150, 1.0e150);
+}
 
 struct PairArgs {
   const void *mirror_in;
@@ -552,6 +587,214 @@ struct GravF64 {
   }
 };
 
+// ------------------------------------------------------------ forward 3D FP32
+// f_i = -(1/N) sum_j r_ij s^(-3/2), s = |r_ij|^2 + eps; per pair 11 FP32 operations
+// and one rsqrt.  Accumulators 0, 1, 2 = x, y, z sums of r s^(-3/2).
+template <int R_, int TJ_, int MODE>
+struct Grav3DMixed {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = float;
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_GRAV3D, true, false>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    float2 x[R], y[R], z[R], fx[R], fy[R], fz[R];
+    CompSum cs[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + row_of(r);
+      const float *m = (const float *)mirror + (i >> 1) * 8 + (i & 1);
+      st.x[r] = f2(-m[0]);
+      st.y[r] = f2(-m[2]);
+      st.z[r] = f2(-m[4]);
+      st.fx[r] = st.fy[r] = st.fz[r] = f2(0.f);
+#pragma unroll
+      for (int d = 0; d < NACC; d++) st.cs[r][d] = CompSum{0.f, 0.f};
+    }
+  }
+  __device__ static void flush(State &st) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      csum_add2(st.cs[r][0], st.fx[r]);
+      csum_add2(st.cs[r][1], st.fy[r]);
+      csum_add2(st.cs[r][2], st.fz[r]);
+      st.fx[r] = st.fy[r] = st.fz[r] = f2(0.f);
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 A = sm[2 * k], B = sm[2 * k + 1];
+      const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w), nz = make_float2(B.x, B.y);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const float2 dx = __fadd2_rn(st.x[r], nx), dy = __fadd2_rn(st.y[r], ny), dz = __fadd2_rn(st.z[r], nz);
+        const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+        const float2 y = make_float2(mufu_rsqrt(s.x), mufu_rsqrt(s.y));
+        const float2 w = __fmul2_rn(__fmul2_rn(y, y), y);
+        st.fx[r] = __ffma2_rn(dx, w, st.fx[r]);
+        st.fy[r] = __ffma2_rn(dy, w, st.fy[r]);
+        st.fz[r] = __ffma2_rn(dz, w, st.fz[r]);
+      }
+    }
+    flush(st);
+  }
+  // Off-diagonal block of the Newton's-third-law variant: rows as in tile<>, and
+  // per j the sums over this warp's 32 R rows of the x, y, z terms into
+  // colsm[(warp TJ + j) 3 + d]; four j-pairs at a time, the (x, y) sums reduced by
+  // one butterfly of 16 values and the z sums by one of 8.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k8 = 0; k8 < TJ / 8; k8++) {
+      float vxy[16], vz[8];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const int k = 4 * k8 + kk;
+        const float4 A = sm[2 * k], B = sm[2 * k + 1];
+        const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w), nz = make_float2(B.x, B.y);
+        float2 cx = f2(0.f), cy = f2(0.f), cz = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const float2 dx = __fadd2_rn(st.x[r], nx), dy = __fadd2_rn(st.y[r], ny), dz = __fadd2_rn(st.z[r], nz);
+          const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+          const float2 y = make_float2(mufu_rsqrt(s.x), mufu_rsqrt(s.y));
+          const float2 wt = __fmul2_rn(__fmul2_rn(y, y), y);
+          st.fx[r] = __ffma2_rn(dx, wt, st.fx[r]);
+          st.fy[r] = __ffma2_rn(dy, wt, st.fy[r]);
+          st.fz[r] = __ffma2_rn(dz, wt, st.fz[r]);
+          cx = __ffma2_rn(dx, wt, cx);
+          cy = __ffma2_rn(dy, wt, cy);
+          cz = __ffma2_rn(dz, wt, cz);
+        }
+        vxy[4 * kk + 0] = cx.x;
+        vxy[4 * kk + 1] = cx.y;
+        vxy[4 * kk + 2] = cy.x;
+        vxy[4 * kk + 3] = cy.y;
+        vz[2 * kk + 0] = cz.x;
+        vz[2 * kk + 1] = cz.y;
+      }
+      float sxy = butterfly_sum<16, 16>(vxy, lane);  // value lane >> 1 = 4 kk + 2 d + (j parity)
+      sxy += __shfl_xor_sync(0xffffffffu, sxy, 1);
+      float sz = butterfly_sum<8, 16>(vz, lane);  // value lane >> 2 = 2 kk + (j parity)
+      sz += __shfl_xor_sync(0xffffffffu, sz, 2);
+      sz += __shfl_xor_sync(0xffffffffu, sz, 1);
+      if ((lane & 1) == 0) {
+        const int vi = lane >> 1;
+        const int j = 8 * k8 + 2 * (vi >> 2) + (vi & 1);
+        colsm[(w * TJ + j) * 3 + ((vi >> 1) & 1)] = sxy;
+      }
+      if ((lane & 3) == 0) {
+        const int vi = lane >> 2;
+        colsm[(w * TJ + 8 * k8 + vi) * 3 + 2] = sz;
+      }
+    }
+    flush(st);
+  }
+};
+
+// ------------------------------------------------------------ forward 3D FP64
+template <int R_, int TJ_, int MODE>
+struct Grav3DF64 {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = double;
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_GRAV3D, false, false>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    double x[R], y[R], z[R];
+    double accd[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 4;
+      st.x[r] = m[0];
+      st.y[r] = m[1];
+      st.z[r] = m[2];
+      st.accd[r][0] = st.accd[r][1] = st.accd[r][2] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double4 *sm = (const double4 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double4 o = sm[k];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const double dx = st.x[r] - o.x, dy = st.y[r] - o.y, dz = st.z[r] - o.z;
+        const double y = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, a.epsd))));
+        const double w = y * y * y;
+        st.accd[r][0] = fma(dx, w, st.accd[r][0]);
+        st.accd[r][1] = fma(dy, w, st.accd[r][1]);
+        st.accd[r][2] = fma(dz, w, st.accd[r][2]);
+      }
+    }
+  }
+  // Newton's-third-law variant: per j the sums over this warp's rows of the x, y,
+  // z terms into colsm[(warp TJ + j) 3 + d]; eight j's at a time, (x, y) by a
+  // butterfly of 16 values and z by one of 8.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
+    const double4 *sm = (const double4 *)smb;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k8 = 0; k8 < TJ / 8; k8++) {
+      double vxy[16], vz[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; kk++) {
+        const double4 o = sm[8 * k8 + kk];
+        double cx = 0.0, cy = 0.0, cz = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const double dx = st.x[r] - o.x, dy = st.y[r] - o.y, dz = st.z[r] - o.z;
+          const double y = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, a.epsd))));
+          const double wt = y * y * y;
+          const double tx = dx * wt, ty = dy * wt, tz = dz * wt;
+          st.accd[r][0] += tx;
+          st.accd[r][1] += ty;
+          st.accd[r][2] += tz;
+          cx += tx;
+          cy += ty;
+          cz += tz;
+        }
+        vxy[2 * kk] = cx;
+        vxy[2 * kk + 1] = cy;
+        vz[kk] = cz;
+      }
+      double sxy = butterfly_sum<16, 16>(vxy, lane);  // value lane >> 1 = 2 kk + d
+      sxy += __shfl_xor_sync(0xffffffffu, sxy, 1);
+      double sz = butterfly_sum<8, 16>(vz, lane);  // value lane >> 2 = kk
+      sz += __shfl_xor_sync(0xffffffffu, sz, 2);
+      sz += __shfl_xor_sync(0xffffffffu, sz, 1);
+      if ((lane & 1) == 0) {
+        const int vi = lane >> 1;
+        colsm[(w * TJ + 8 * k8 + (vi >> 1)) * 3 + (vi & 1)] = sxy;
+      }
+      if ((lane & 3) == 0) colsm[(w * TJ + 8 * k8 + (lane >> 2)) * 3 + 2] = sz;
+    }
+  }
+};
+
 // ------------------------------------------------------------ adjoint Ring FP32
 // accumulators: 0 = sum S dd^-3/2 (force), 1 = sum G w (J v), 2 = sum S dd^-5/2 (d/deps)
 template <int R_, int TJ_, int MODE>
@@ -1034,9 +1277,11 @@ __device__ __forceinline__ void write_pad_fmt(void *mirror, int64_t i) {
 // Forward stages: kick, drift, new mirror record (or the force alone).
 template <int MODEL, bool MIXED, int MODE, int FMT>
 __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, const double *acc) {
-  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  constexpr int D = dim_of<MODEL>();
   if (i >= a.N) return;
-  const double scale = MODEL == MD_RING ? -1.0 / (8.0 * (double)a.N) : -2.0 / (double)a.N;
+  const double scale = MODEL == MD_RING ? -1.0 / (8.0 * (double)a.N)
+                       : MODEL == MD_GRAV3D ? -1.0 / (double)a.N
+                                            : -2.0 / (double)a.N;
   double f[D], x[D];
 #pragma unroll
   for (int d = 0; d < D; d++) f[d] = scale * acc[d];
@@ -1056,7 +1301,12 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
       a.fout[d * a.N + i] = f[d];
     }
   }
-  if (MODE == STAGE_KICK_DRIFT) write_record_fmt<MODEL, MIXED, false, FMT>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+  if (MODE == STAGE_KICK_DRIFT) {
+    if constexpr (MODEL == MD_GRAV3D)
+      write_record3<MIXED>(a.mirror_out, i, x[0], x[1], x[D - 1]);
+    else
+      write_record_fmt<MODEL, MIXED, false, FMT>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
+  }
 }
 
 // Reverse stages of md_grad, at the position q_s of one kick (b_adj = a.kick,

@@ -272,7 +272,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.mirror_out = c->mirror[1 - c->mirror_cur];
   a.q = c->q;
   a.p = c->p;
-  a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;
+  a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;  // 2D, 3D: eps
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
   kern<<<a.P, THR, 0, c->stream>>>(a, s);
@@ -285,9 +285,13 @@ int launch_sym(md_ctx *c, PairArgs a) {
 
 template <int MODEL, bool MIXED, int MODE>
 int sym_dispatch(md_ctx *c, PairArgs a) {
-  if constexpr (!MIXED) {
-    if constexpr (MODEL == MD_RING) return launch_sym<RingF64<2, 128, MODE>, MODEL, false, MODE>(c, a);
-    else return launch_sym<GravF64<2, 128, MODE>, MODEL, false, MODE>(c, a);
+  if constexpr (MODEL == MD_GRAV3D) {
+    if constexpr (MIXED) return launch_sym<Grav3DMixed<4, 256, MODE>, MODEL, true, MODE>(c, a);
+    else return launch_sym<Grav3DF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
+  } else if constexpr (!MIXED) {
+    // 4 rows per thread: the column butterflies' FP64 adds are shared by twice the pairs
+    if constexpr (MODEL == MD_RING) return launch_sym<RingF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
+    else return launch_sym<GravF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
   } else if constexpr (MODEL == MD_RING) {
     if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, true, MODE>(c, a);
     if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, true, MODE>(c, a);
@@ -312,10 +316,13 @@ int sym_mode(md_ctx *c, int mode, PairArgs a) {
 // while they fit in kSymMaxColBytes.
 bool sym_applies(const md_ctx *c) {
   if (!c->pt.symmetric) return false;
-  int64_t TI, TJ, nacc = c->model == MD_GRAV2D ? 2 : 1, colbytes;
+  int64_t TI, TJ, nacc = c->dim, colbytes;
+  if (c->model == MD_HMF) return false;
   if (c->prec == MD_FP64) {
-    if (c->pt.r_fp64 != 2 || (c->model != MD_RING && c->model != MD_GRAV2D)) return false;
-    TI = 256, TJ = 128, colbytes = 8;
+    if (c->pt.r_fp64 != 2) return false;
+    TI = 512, TJ = 128, colbytes = 8;
+  } else if (c->model == MD_GRAV3D) {
+    TI = 512, TJ = 256, colbytes = 4;
   } else if (c->model == MD_RING) {
     if (!c->pt.ring_tc || c->pt.ring_tc == 2 || c->pt.r_mixed == 4) return false;
     TI = 256, TJ = 256, colbytes = 4;
@@ -337,5 +344,7 @@ int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout)
   a.fout = fout;
   const bool mixed = c->prec == MD_MIXED;
   if (c->model == MD_RING) return mixed ? sym_mode<MD_RING, true>(c, mode, a) : sym_mode<MD_RING, false>(c, mode, a);
+  if (c->model == MD_GRAV3D)
+    return mixed ? sym_mode<MD_GRAV3D, true>(c, mode, a) : sym_mode<MD_GRAV3D, false>(c, mode, a);
   return mixed ? sym_mode<MD_GRAV2D, true>(c, mode, a) : sym_mode<MD_GRAV2D, false>(c, mode, a);
 }

@@ -10,7 +10,7 @@ import numpy as np
 
 from . import binding as B
 
-MODELS = {"hmf": 0, "ring": 1, "grav2d": 2, "2d": 2}
+MODELS = {"hmf": 0, "ring": 1, "grav2d": 2, "2d": 2, "grav3d": 3, "3d": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 
@@ -56,7 +56,7 @@ class System:
         lib = B.load()
         self.model = _model(model)
         self.N = int(N)
-        self.dim = 2 if self.model == 2 else 1
+        self.dim = {2: 2, 3: 3}.get(self.model, 1)
         self._dt = float(dt)
         h = lib.md_init(self.model, self.N, float(eps), float(dt), int(seed) & (2**64 - 1))
         if not h:
