@@ -125,6 +125,10 @@ int md_set_eps(md_ctx *ctx, double eps);
  *                      N^2 / 2^16 floats (FP32 Ring), N^2 / 2^18 floats (FP32 2D) or
  *                      N^2 / 2^16 doubles (FP64); above 4 GiB of it the one-sided kernel
  *                      runs.
+ *   "rsqrt_offload"    symmetric FP32 Ring kernel: 0 (default), 1 or 2 of the 8 pair-halves per
+ *                      16x8 block take 1/sqrt on the FMA pipe (bit-pattern seed, two cubic
+ *                      steps) instead of the SFU; measured slower on GB300, kept for study
+ *   "sym_threads"      symmetric FP32 Ring kernel CTA shape: 128 (default), 256 or 768
  *   "step_graphs"      md_step replays its steps after the first from captured CUDA
  *                      graphs of 8 steps (1, default) or launches every stage (0).
  * MD_EINVAL for an unknown key or value. */

@@ -23,6 +23,7 @@ struct PairTuning {
   int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
   int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
   int symmetric = 1;  // forward stages: each unordered pair once (Newton's third law)
+  int rsqrt_off = 0;  // symmetric Ring kernel: items of 8 per n-block with the rsqrt on the FMA pipe
   int sym_threads = 128;  // symmetric Ring kernel: 128 threads, 4 m-blocks per warp; 256: 2 m-blocks;
                           // 768: 256 threads with registers capped for 3 CTAs per SM
   int ctas_per_sm = 0;  // 0: occupancy-derived

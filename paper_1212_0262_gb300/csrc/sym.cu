@@ -27,7 +27,7 @@
 //
 // Finish phase (sym_finish_kernel).  Tile T needs its row partials and the m T
 // column partials of the units (I', J), I' < T, J in tile T.  One CTA per
-// (tile, chunk of kSymChunk rows I') sums a chunk's column partials per particle
+// (tile, chunk of sym_chunk rows I') sums a chunk's column partials per particle
 // and component (compensated FP32, then one double); the last chunk of a tile to
 // arrive (atomic ticket, no waiting) adds the row partials in CTA order and the
 // chunk sums in chunk order, and runs the stage epilogue (kick, drift, new mirror
@@ -145,13 +145,20 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
   }
 }
 
-// Finish phase, one CTA per (tile T, chunk c of kSymChunk rows I' < T): the
+// Finish phase, one CTA per (tile T, chunk c of sym_chunk rows I' < T): the
 // chunk's column partials summed per particle and component (compensated FP32)
 // into one double; the last chunk of the tile to arrive (atomic ticket, no
 // waiting) adds the row partials (CTA order) and the chunk sums (chunk order)
 // and runs the stage epilogue.  Tiles with T = 0 have one empty chunk.
-constexpr int kSymChunk = 16;
 constexpr int kFinishThreads = 256;
+
+// Column-partial rows per finish CTA: about 16K loads per CTA whatever the tile's
+// output count (Ring FP32 tiles have 256 outputs, 2D 2048).
+template <class Pol>
+constexpr int sym_chunk() {
+  constexpr int out = Pol::THREADS * Pol::R * Pol::NACC;
+  return out <= 256 ? 64 : out <= 512 ? 32 : 16;
+}
 
 template <class Pol, int MODEL, bool MIXED, int MODE>
 __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, SymArgs s) {
@@ -161,10 +168,11 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
   __shared__ bool s_last;
   const int64_t T = blockIdx.x / s.nc;
   const int c = (int)(blockIdx.x % s.nc);
-  const int nch = T == 0 ? 1 : (int)((T + kSymChunk - 1) / kSymChunk);
+  constexpr int CH = sym_chunk<Pol>();
+  const int nch = T == 0 ? 1 : (int)((T + CH - 1) / CH);
   if (c >= nch) return;
   const int m = s.m;
-  const int64_t I_lo = (int64_t)c * kSymChunk, I_hi = min(T, I_lo + kSymChunk);
+  const int64_t I_lo = (int64_t)c * CH, I_hi = min(T, I_lo + CH);
   double *chunk = s.chunks + (T * s.nc) * OUT;
   using ColT = typename Pol::ColT;
   const ColT *col = (const ColT *)s.colslot;
@@ -243,7 +251,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.P = (int)P;
   int rc = ensure_pair_buffers(c, (int)TI, a.P, NACC);
   if (rc) return rc;
-  s.nc = (int)std::max<int64_t>(1, (a.n_it - 1 + kSymChunk - 1) / kSymChunk);
+  s.nc = (int)std::max<int64_t>(1, (a.n_it - 1 + sym_chunk<Pol>() - 1) / sym_chunk<Pol>());
   const size_t need_row = (size_t)a.n_it * NACC * TI * sizeof(double);
   const size_t need_col = (size_t)a.U * TJ * NACC * sizeof(typename Pol::ColT);
   const size_t need_chunk = (size_t)a.n_it * s.nc * NACC * TI * sizeof(double);
@@ -295,6 +303,8 @@ int sym_dispatch(md_ctx *c, PairArgs a) {
   } else if constexpr (MODEL == MD_RING) {
     if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, true, MODE>(c, a);
     if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, true, MODE>(c, a);
+    if (c->pt.rsqrt_off == 1) return launch_sym<RingTC<4, 256, MODE, NT, 3, 1>, MODEL, true, MODE>(c, a);
+    if (c->pt.rsqrt_off == 2) return launch_sym<RingTC<4, 256, MODE, NT, 3, 2>, MODEL, true, MODE>(c, a);
     return launch_sym<RingTC<4, 256, MODE>, MODEL, true, MODE>(c, a);
   } else {
     return launch_sym<GravMixed<8, 256, MODE>, MODEL, true, MODE>(c, a);

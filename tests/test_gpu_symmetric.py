@@ -132,3 +132,17 @@ def test_symmetric_ring_cta_shapes(N, threads):
     scale = ora.force_abs(1, q, EPS[1])
     err = np.abs(f - fo)
     assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+
+
+@pytest.mark.parametrize("off", [1, 2])
+@pytest.mark.parametrize("N", [1, 257, 1000, 4097])
+def test_symmetric_ring_rsqrt_on_fma_pipe(N, off):
+    """Part of the reciprocal square roots from rsqrt2_fma (bit-pattern seed and two
+    cubic steps) instead of the SFU: same error bound."""
+    s, q, _ = _sym(1, N)
+    s.set_tuning("rsqrt_offload", off)
+    f = s.force()
+    fo = ora.force(1, q, EPS[1])
+    scale = ora.force_abs(1, q, EPS[1])
+    err = np.abs(f - fo)
+    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
