@@ -18,7 +18,7 @@ import threading
 
 import numpy as np
 
-HMF, RING, GRAV2D, GRAV3D, HARMONIC = 0, 1, 2, 3, 9
+HMF, RING, GRAV2D, GRAV3D, SHEET1D, HARMONIC = 0, 1, 2, 3, 4, 9
 OBS_KINETIC, OBS_MAGNETIZATION = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -58,6 +58,7 @@ def _load():
                 "ora_kinetic": (d, [i64, P]),
                 "ora_force_abs": (None, [i32, i64, d, P, P]),
                 "ora_force_rows": (None, [i32, i64, d, P, ctypes.POINTER(ctypes.c_int64), i64, P, P]),
+                "ora_force_sheet_f32": (None, [i64, P, P]),
                 "ora_step": (i32, [i32, i64, d, d, i64, P, P]),
                 "ora_hvp": (None, [i32, i64, d, P, P, P]),
                 "ora_hvp_hmf_meanfield": (None, [i64, P, P, P]),
@@ -106,6 +107,15 @@ def force(model: int, q, eps: float = 0.0) -> np.ndarray:
     q = _arr(q)
     f = np.empty_like(q)
     _load().ora_force(model, q.size // dim(model), eps, _p(q), _p(f))
+    return f
+
+
+def force_sheet_f32(q) -> np.ndarray:
+    """1D-sheet force at eps = 0 with every sign decided on the FP32-rounded
+    positions (the FP32 pair kernel's precision for that decision)."""
+    q = _arr(q)
+    f = np.empty_like(q)
+    _load().ora_force_sheet_f32(q.size, _p(q), _p(f))
     return f
 
 

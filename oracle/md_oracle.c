@@ -40,6 +40,12 @@
  *    Kac 1/N coupling and the additive softening of Eqs. 1-3,
  *    V = -(1/N) sum_{i<j} (|r_ij|^2 + eps)^(-1/2),
  *    f_i = -(1/N) sum_j r_ij (|r_ij|^2 + eps)^(-3/2).
+ *  - 1D self-gravitating sheets (not one of the paper's three models; its
+ *    introduction lists one-dimensional gravity of infinite uniform sheets among
+ *    the long-range models): unit masses, Kac 1/N coupling,
+ *    V = (1/N) sum_{i<j} |x_i - x_j| (eps = 0) or sqrt((x_i - x_j)^2 + eps) (eps > 0),
+ *    f_i = -(1/N) sum_j sign(x_i - x_j) with sign(0) = 0 (eps = 0), or
+ *    -(1/N) sum_j d / sqrt(d^2 + eps).
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,6 +56,7 @@
 #define ORA_RING 1
 #define ORA_GRAV2D 2
 #define ORA_GRAV3D 3
+#define ORA_SHEET1D 4
 #define ORA_HARMONIC 9
 
 #define ORA_OBS_KINETIC 0
@@ -205,6 +212,48 @@ double ora_potential_3d(int64_t N, double eps, const double *q) {
   return -v / (double)N;
 }
 
+/* ------------------------------------------------------------ 1D sheets -- */
+
+static double sgn(double d) { return d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0); }
+
+/* f_i = -(1/N) sum_{j != i} sign(x_i - x_j) (eps = 0), -(1/N) sum_j d / sqrt(d^2 + eps). */
+void ora_force_sheet(int64_t N, double eps, const double *x, double *f) {
+  for (int64_t i = 0; i < N; i++) {
+    double s = 0.0;
+    for (int64_t j = 0; j < N; j++) {
+      if (j == i) continue;
+      double d = x[i] - x[j];
+      s += eps > 0.0 ? d / sqrt(d * d + eps) : sgn(d);
+    }
+    f[i] = -s / (double)N;
+  }
+}
+
+/* The eps = 0 force with every sign decided on the FP32-rounded positions (the
+ * precision in which the FP32 pair kernel takes the decision). */
+void ora_force_sheet_f32(int64_t N, const double *x, double *f) {
+  for (int64_t i = 0; i < N; i++) {
+    double s = 0.0;
+    for (int64_t j = 0; j < N; j++) {
+      if (j == i) continue;
+      float a = (float)x[i], b = (float)x[j];
+      s += a > b ? 1.0 : (a < b ? -1.0 : 0.0);
+    }
+    f[i] = -s / (double)N;
+  }
+}
+
+/* V = (1/N) sum_{i<j} |x_i - x_j| (eps = 0) or sqrt((x_i - x_j)^2 + eps). */
+double ora_potential_sheet(int64_t N, double eps, const double *x) {
+  double v = 0.0;
+  for (int64_t i = 0; i < N; i++)
+    for (int64_t j = i + 1; j < N; j++) {
+      double d = x[i] - x[j];
+      v += eps > 0.0 ? sqrt(d * d + eps) : fabs(d);
+    }
+  return v / (double)N;
+}
+
 /* ------------------------------------------------------------ generic ---- */
 
 void ora_force(int model, int64_t N, double eps, const double *q, double *f) {
@@ -213,6 +262,7 @@ void ora_force(int model, int64_t N, double eps, const double *q, double *f) {
   case ORA_RING: ora_force_ring(N, eps, q, f); break;
   case ORA_GRAV2D: ora_force_2d(N, eps, q, f); break;
   case ORA_GRAV3D: ora_force_3d(N, eps, q, f); break;
+  case ORA_SHEET1D: ora_force_sheet(N, eps, q, f); break;
   case ORA_HARMONIC:
     for (int64_t i = 0; i < N; i++) f[i] = -q[i];
     break;
@@ -225,6 +275,7 @@ double ora_potential(int model, int64_t N, double eps, const double *q) {
   case ORA_RING: return ora_potential_ring(N, eps, q);
   case ORA_GRAV2D: return ora_potential_2d(N, eps, q);
   case ORA_GRAV3D: return ora_potential_3d(N, eps, q);
+  case ORA_SHEET1D: return ora_potential_sheet(N, eps, q);
   case ORA_HARMONIC: {
     double v = 0.0;
     for (int64_t i = 0; i < N; i++) v += 0.5 * q[i] * q[i];
@@ -294,6 +345,16 @@ void ora_force_abs(int model, int64_t N, double eps, const double *q, double *ou
       out[i] = sx / (double)N;
       out[N + i] = sy / (double)N;
       out[2 * N + i] = sz / (double)N;
+    }
+  } else if (model == ORA_SHEET1D) {
+    for (int64_t i = 0; i < N; i++) {
+      double s = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double d = q[i] - q[j];
+        s += eps > 0.0 ? fabs(d) / sqrt(d * d + eps) : fabs(sgn(d));
+      }
+      out[i] = s / (double)N;
     }
   } else {
     for (int64_t i = 0; i < N; i++) out[i] = fabs(q[i]);
@@ -379,6 +440,20 @@ void ora_force_rows(int model, int64_t N, double eps, const double *q, const int
         out_abs[nrows + r] = ay / (double)N;
         out_abs[2 * nrows + r] = az / (double)N;
       }
+    }
+  } else if (model == ORA_SHEET1D) {
+    for (int64_t r = 0; r < nrows; r++) {
+      int64_t i = rows[r];
+      double s = 0.0, a = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double d = q[i] - q[j];
+        double t = eps > 0.0 ? d / sqrt(d * d + eps) : sgn(d);
+        s += t;
+        a += fabs(t);
+      }
+      out[r] = -s / (double)N;
+      if (out_abs) out_abs[r] = a / (double)N;
     }
   }
 }

@@ -109,13 +109,20 @@ def ball_state(N: int, seed: int, sigma=0.3):
     return q, p
 
 
+def sheet_state(N: int, seed: int, x_lo=-1.0, x_hi=1.0, p_lo=-0.5, p_hi=0.5):
+    """1D sheets, water-bag: x ~ U[x_lo, x_hi), p ~ U[p_lo, p_hi) (the HMF recipe's
+    counters and maps with the sheet model's intervals)."""
+    return waterbag(N, seed, x_lo, x_hi, p_lo, p_hi)
+
+
 def uniform_rest(N: int, seed: int):
     """Angle models at rest: theta ~ U[-pi, pi), p = 0."""
     return _affine(uniform(seed, 0, N), -np.pi, np.pi), np.zeros(N)
 
 
 def default_state(model: int, N: int, seed: int):
-    """Per-model default initial state: water-bag (HMF), ring_state, disk_state, ball_state."""
+    """Per-model default initial state: water-bag (HMF), ring_state, disk_state, ball_state,
+    sheet_state."""
     if model == 0:
         return waterbag(N, seed)
     if model == 1:
@@ -124,6 +131,8 @@ def default_state(model: int, N: int, seed: int):
         return disk_state(N, seed)
     if model == 3:
         return ball_state(N, seed)
+    if model == 4:
+        return sheet_state(N, seed)
     raise ValueError(f"unknown model {model}")
 
 

@@ -67,3 +67,13 @@ def test_ball_state_recipe():
     assert abs(np.std(p) - 0.3) < 0.01
     q3, p3 = inputs.default_state(3, 10, 2)
     assert q3.size == 30 and p3.size == 30
+
+
+def test_sheet_state_recipe():
+    """1D sheets: the water-bag counters and maps with x in [-1, 1), p in [-0.5, 0.5)."""
+    q, p = inputs.sheet_state(1000, 9)
+    qw, pw = inputs.waterbag(1000, 9, -1.0, 1.0, -0.5, 0.5)
+    assert np.array_equal(q, qw) and np.array_equal(p, pw)
+    assert q.min() >= -1.0 and q.max() < 1.0 and p.min() >= -0.5 and p.max() < 0.5
+    q4, p4 = inputs.default_state(4, 1000, 9)
+    assert np.array_equal(q4, q)

@@ -26,6 +26,8 @@ def _state(model, N, seed):
         return inputs.ring_state(N, seed)
     if model == 3:
         return inputs.ball_state(N, seed)
+    if model == 4:
+        return inputs.sheet_state(N, seed)
     return inputs.disk_state(N, seed)
 
 
@@ -117,7 +119,8 @@ def test_hmf_meanfield_equals_pairwise(ora, N):
     assert abs(v_mf - v_pw) <= 1e-13 * max(1.0, N)
 
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5), (3, 1e-3), (3, 0.5)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5), (3, 1e-3), (3, 0.5),
+                                       (4, 1e-3), (4, 0.5)])
 def test_force_is_minus_gradient_of_potential(ora, model, eps):
     N = 12
     q, _ = _state(model, N, 21)
@@ -133,7 +136,7 @@ def test_force_is_minus_gradient_of_potential(ora, model, eps):
     assert np.max(np.abs(fd - f)) < 2e-7 * scale, np.max(np.abs(fd - f)) / scale
 
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3), (3, 1e-3)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3), (3, 1e-3), (4, 0.0), (4, 1e-3)])
 def test_total_momentum_conserved(ora, model, eps):
     N = 40
     q0, p0 = _state(model, N, 31)
@@ -167,6 +170,62 @@ def test_angular_momentum_conserved_3d(ora):
     q, p = ora.step(3, q0, p0, 1e-3, 0.05, 20)
     scale = np.sum(np.abs(q0)) * np.abs(p0).max()
     assert np.max(np.abs(L(q, p) - L(q0, p0))) < 1e-12 * scale * 20
+
+
+def test_sheet_force_is_a_count_of_neighbours_on_each_side(ora):
+    """eps = 0: f_i = (number of sheets to the right - number to the left) / N,
+    counted here by sorting (independent of the oracle's pair loop); exact."""
+    N = 301
+    x, _ = inputs.sheet_state(N, 61)
+    x[5] = x[9]  # a coincident pair: sign(0) = 0
+    srt = np.sort(x)
+    left = np.searchsorted(srt, x, side="left")
+    right = N - np.searchsorted(srt, x, side="right")
+    expect = (right - left) / N
+    f = ora.force(4, x, 0.0)
+    assert np.array_equal(f, expect)
+    assert f.sum() == 0.0
+
+
+def test_sheet_force_is_minus_gradient_of_piecewise_linear_potential(ora):
+    """eps = 0: V is linear between crossings, so central differences with a step
+    below the smallest gap are exact up to rounding."""
+    N = 40
+    x = np.sort(inputs.uniform(62, 0, N)) * 2 - 1
+    h = 0.25 * np.min(np.diff(x))
+    f = ora.force(4, x, 0.0)
+    for k in range(N):
+        xp, xm = x.copy(), x.copy()
+        xp[k] += h
+        xm[k] -= h
+        fd = -(ora.potential(4, xp, 0.0) - ora.potential(4, xm, 0.0)) / (2 * h)
+        assert abs(fd - f[k]) < 1e-9
+
+
+def test_sheet_pair_bounce_period(ora):
+    """Two sheets released at separation u0: the separation obeys u'' = -sign(u)
+    (coupling 1/N with N = 2), so they cross and return after T = 4 sqrt(2 u0).  The
+    force jumps at the crossing, so the return error falls only linearly with dt."""
+    u0 = 0.5
+    T = 4 * math.sqrt(2 * u0)
+    q0, p0 = np.array([u0 / 2, -u0 / 2]), np.zeros(2)
+    errs = []
+    for n in (400, 800):
+        q, p = ora.step(4, q0, p0, 0.0, T / n, n)
+        errs.append(np.max(np.abs(q - q0)))
+        assert np.max(np.abs(q - q0)) < 4.0 / n and np.max(np.abs(p - p0)) < 8.0 / n
+    assert 1.6 < errs[0] / errs[1] < 2.4
+
+
+def test_sheet_fp32_decisions(ora):
+    """The FP32-decision force equals the FP64 one when the FP32 roundings keep every
+    order, and counts an FP32 tie as 0."""
+    x = np.linspace(-1, 1, 257)
+    assert np.array_equal(ora.force_sheet_f32(x), ora.force(4, x, 0.0))
+    y = np.array([0.5, 0.5 + 1e-12, -0.25])  # distinct in FP64, equal in FP32
+    f64, f32 = ora.force(4, y, 0.0), ora.force_sheet_f32(y)
+    assert f64[0] == -(-1 + 1) / 3 + 0.0 and f64[1] == -(1 + 1) / 3
+    assert f32[0] == f32[1] == -1 / 3
 
 
 def test_3d_shell_theorem(ora):
@@ -239,6 +298,9 @@ def test_special_cases(ora):
             for c in range(model):
                 assert abs(f[2 * c] + f[2 * c + 1]) < 1e-16
             assert f[0] < 0 and f[2] > 0  # pulled toward particle 1
+    # one sheet, or sheets all at one place, feel no force
+    assert ora.force(4, np.array([0.3]), 0.0)[0] == 0.0
+    assert np.all(ora.force(4, np.full(5, 0.2), 0.0) == 0.0)
     # particles at rest have K = 0
     assert ora.kinetic(np.zeros(10)) == 0.0
 
