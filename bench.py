@@ -40,6 +40,8 @@ WORKLOADS = {
                    name="2D self-gravitating N=262,144 eps=1e-4 dt=0.01 (all-pairs)"),
     "grav3d": dict(model=3, N=131_072, eps=1e-3, dt=0.01, seed=5, unit="pair-interactions/s",
                    name="3D self-gravitating N=131,072 eps=1e-3 dt=0.01 (all-pairs; not one of the paper's models)"),
+    "sheet1d": dict(model=4, N=262_144, eps=0.0, dt=0.01, seed=6, unit="pair-interactions/s",
+                    name="1D sheets N=262,144 eps=0 dt=0.01 (all-pairs sign counts; not one of the paper's models)"),
     "adjoint": dict(model=2, N=262_144, eps=1e-4, dt=0.01, seed=4, unit="pair-interactions/s",
                     name="2D N=262,144 eps=1e-4 dt=0.01: gradient of K(T) after 100 steps (forward + "
                          "reversed adjoint, checkpoints every 20 steps)"),
@@ -50,7 +52,7 @@ WORKLOADS = {
 # algorithmic bytes per particle per fused HMF stage: read + write FP64 theta and p
 HMF_BYTES_PER_PARTICLE_STAGE = 32
 # FP32-pipe operations and SFU operations per pair in the mixed pair kernels
-PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1)}
+PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1), 4: (4, 0)}
 # Per force-kernel variant (md_force_kernel): name, FP32 operations and SFU operations
 # per evaluated pair term, and whether each unordered pair is evaluated once.
 #   one-sided Ring: S and sin(d/2) (2 FMA + 2 MUL), dd (FMA), y^2, S y, acc (FMA) -> 8
@@ -67,6 +69,9 @@ PAIR_KERNELS = {
     (2, 4): ("sym_kernel<GravMixed<8,256>>", 8.25, 1, True),
     (3, 2): ("streamk_kernel<Grav3DMixed<4,256>>", 11, 1, False),
     (3, 4): ("sym_kernel<Grav3DMixed<4,256>>", 14.75, 1, True),
+    # sheets at eps = 0: difference, two comparisons turned into +-1, accumulate (no SFU)
+    (4, 2): ("streamk_kernel<SheetMixed<8,256>>", 4, 0, False),
+    (4, 4): ("sym_kernel<SheetMixed<8,256>>", 5.25, 0, True),
 }
 
 
@@ -84,7 +89,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
-    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "ensemble": (20, 3),
+    dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "sheet1d": (20, 3), "ensemble": (20, 3),
             "adjoint": (1, 0)}[a.workload]
     if a.steps is None:
         a.steps = dflt[0]
@@ -376,7 +381,7 @@ def run_ours(args, w):
         sfu_rate = rates[5] if model in (1, 3) else rates[7]  # rsqrt (Ring, 3D) or rcp (2D)
         kcode = sysm.force_kernel
         kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
-        pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops)
+        pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops) if sops else fp32_rate / fops
         mhz = clocks.get("sm_mhz") or rates[2]
         peak = nsm * pairs_per_clk * mhz * 1e6
         # algorithmic pair terms per force pass: N^2 ordered pairs, or N (N - 1) / 2

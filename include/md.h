@@ -49,6 +49,13 @@ extern "C" {
                      * V = -(1/N) sum_{i<j} (|r_ij|^2 + eps)^(-1/2),
                      * f_i = -(1/N) sum_j r_ij (|r_ij|^2 + eps)^(-3/2).
                      * Forward stages and observables; no md_grad / md_tangent_step. */
+#define MD_SHEET1D 4 /* 1D self-gravitating sheets (named in the paper's introduction among
+                      * long-range models, not studied there): unit masses, Kac 1/N coupling,
+                      * V = (1/N) sum_{i<j} |x_i - x_j| for eps = 0 (f_i = -(1/N) sum_j
+                      * sign(x_i - x_j), sign(0) = 0: exact integer counts), or
+                      * sqrt((x_i - x_j)^2 + eps) for eps > 0.  eps >= 0.  In MD_MIXED the
+                      * eps = 0 signs are decided on the FP32 positions.  Forward stages
+                      * and observables; no md_grad / md_tangent_step. */
 
 /* precisions */
 #define MD_FP64 0
@@ -64,7 +71,8 @@ extern "C" {
 #define MD_ESTATE 6     /* call not valid in the context's current state */
 
 /* initial-condition kinds for md_set_ic (all seeded, counter-based SplitMix64) */
-#define MD_IC_WATERBAG 0     /* params[4] = {th_lo, th_hi, p_lo, p_hi}: theta~U[th_lo,th_hi), p~U[p_lo,p_hi) */
+#define MD_IC_WATERBAG 0     /* params[4] = {th_lo, th_hi, p_lo, p_hi}: theta (or the sheets' x)
+                              * ~U[th_lo,th_hi), p~U[p_lo,p_hi) */
 #define MD_IC_RING 1         /* params[1] = {sigma}: theta~U[-pi,pi), p~N(0,sigma^2) */
 #define MD_IC_DISK 2         /* params[1] = {sigma}: uniform unit disk, p~N(0,sigma^2) per component */
 #define MD_IC_ANNULUS 3      /* params[2] = {r1, r2}: uniform annulus r1<=r<r2, at rest */
@@ -79,12 +87,13 @@ extern "C" {
 typedef struct md_ctx md_ctx;
 typedef struct md_batch md_batch;
 
-/* Create a system of N particles of `model` with softening eps (Ring, 2D, 3D; must
- * be > 0 there, ignored for HMF but must be >= 0) and time step dt (Sec. 3, Eq. 4),
+/* Create a system of N particles of `model` with softening eps (Ring, 2D, 3D: must
+ * be > 0; sheets: >= 0; ignored for HMF but must be >= 0) and time step dt (Sec. 3, Eq. 4),
  * on the current CUDA device.  The state is drawn from `seed` with the model's
  * default recipe: water-bag theta~U[-1,1), p~U[-1.2,1.2) (HMF); theta~U[-pi,pi),
  * p~N(0,0.5^2) (Ring); uniform unit disk, p~N(0,0.3^2) per component (2D);
- * uniform unit ball, p~N(0,0.3^2) per component (3D; state layout x, y, z blocks).
+ * uniform unit ball, p~N(0,0.3^2) per component (3D; state layout x, y, z blocks);
+ * water-bag x~U[-1,1), p~U[-0.5,0.5) (sheets).
  * Precision defaults to MD_FP64.  Returns NULL on failure (see md_last_error(NULL)).
  * The context owns its device memory until md_free. */
 md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed);
@@ -189,7 +198,7 @@ int md_force_device(md_ctx *ctx, double *f);
  * MD_ENONFINITE if either is not finite.  Either pointer may be NULL. */
 int md_energy(md_ctx *ctx, double *K, double *V);
 
-/* Magnetization (Mx, My) of Eq. 7 in FP64 (HMF and Ring; MD_EINVAL for 2D, 3D). */
+/* Magnetization (Mx, My) of Eq. 7 in FP64 (HMF and Ring; MD_EINVAL otherwise). */
 int md_magnetization(md_ctx *ctx, double *mx, double *my);
 
 /* Gradient of an observable of the state reached after nsteps from the current
@@ -199,7 +208,8 @@ int md_magnetization(md_ctx *ctx, double *mx, double *my);
  * checkpoint stored every `checkpoint_every` steps (>= 1).
  * grad_q, grad_p: host arrays of dim*N (required); grad_eps, value: host scalars
  * (may be NULL; grad_eps is 0 for HMF).  Synchronous.  Uses the context's
- * precision for the force and Jacobian-vector products.  MD_EINVAL for MD_GRAV3D. */
+ * precision for the force and Jacobian-vector products.  MD_EINVAL for MD_GRAV3D and
+ * MD_SHEET1D. */
 int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
             double *grad_q, double *grad_p, double *grad_eps, double *value);
 
@@ -209,7 +219,7 @@ int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
  * each drift, J = df/dq).  The building block of largest-Lyapunov-exponent
  * estimates (repeat, renormalising the tangent).  dq, dp: host arrays of dim*N,
  * read and overwritten.  Uses the context's precision.  Synchronous.  MD_EINVAL for
- * MD_GRAV3D. */
+ * MD_GRAV3D and MD_SHEET1D. */
 int md_tangent_step(md_ctx *ctx, int64_t nsteps, double *dq, double *dp);
 
 /* Route the library's device allocations through alloc(bytes, user) and
@@ -225,9 +235,9 @@ int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(v
  * owns the GPU's memory, or a latency-critical loop where cudaMalloc / cudaFree
  * and the device synchronisation they can cause are not acceptable).  The paper
  * has no counterpart; the value is md_energy's V (Eq. 5 for HMF, the i<j sums
- * of Eqs. 1 and 3 for Ring and 2D, and of the 3D potential), computed by the same
- * kernels in FP64.
- *   model: MD_HMF, MD_RING, MD_GRAV2D or MD_GRAV3D; eps as for md_init
+ * of Eqs. 1 and 3 for Ring and 2D, and of the 3D and sheet potentials), computed
+ * by the same kernels in FP64.
+ *   model: MD_HMF, MD_RING, MD_GRAV2D, MD_GRAV3D or MD_SHEET1D; eps as for md_init
  *   N:     1 <= N <= 65536 (the size the static scratch holds); larger N is
  *          rejected with MD_EINVAL and a message in md_last_error(NULL)
  *   q:     device, dim*N doubles (layout as md_set_state), read only

@@ -150,7 +150,7 @@ void md_free(md_ctx *c) {
 }
 
 md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
-  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D) {
+  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D && model != MD_SHEET1D) {
     fail_global(MD_EINVAL, "md_init: unknown model %d", model);
     return nullptr;
   }
@@ -158,8 +158,9 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
     fail_global(MD_EINVAL, "md_init: N must be in [1, 2^40], got %lld", (long long)N);
     return nullptr;
   }
-  if (!is_finite(eps) || eps < 0.0 || (model != MD_HMF && !(eps > 0.0))) {
-    fail_global(MD_EINVAL, "md_init: eps must be finite and %s, got %g", model == MD_HMF ? ">= 0" : "> 0", eps);
+  const bool eps0_ok = model == MD_HMF || model == MD_SHEET1D;  // models with no divergence at eps = 0
+  if (!is_finite(eps) || eps < 0.0 || (!eps0_ok && !(eps > 0.0))) {
+    fail_global(MD_EINVAL, "md_init: eps must be finite and %s, got %g", eps0_ok ? ">= 0" : "> 0", eps);
     return nullptr;
   }
   if (!is_finite(dt)) {
@@ -211,10 +212,10 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
     md_free(c);
     return nullptr;
   }
-  const int kind = model == MD_HMF    ? MD_IC_WATERBAG
-                   : model == MD_RING ? MD_IC_RING
-                   : model == MD_GRAV2D ? MD_IC_DISK
-                                        : MD_IC_BALL;
+  const int kind = model == MD_HMF || model == MD_SHEET1D ? MD_IC_WATERBAG
+                   : model == MD_RING                    ? MD_IC_RING
+                   : model == MD_GRAV2D                  ? MD_IC_DISK
+                                                         : MD_IC_BALL;
   if (ic_draw(c, kind, nullptr, seed) != MD_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
     g_err = c->err.empty() ? std::string("md_init: initial state") : c->err;
     md_free(c);
@@ -527,6 +528,8 @@ int md_energy(md_ctx *c, double *K, double *V) {
     pot = -c->host_scalars[1] / (2.0 * n);  // Eq. 1 with 1 - cos + eps = 2 (sin^2(d/2) + eps/2)
   } else if (c->model == MD_GRAV3D) {
     pot = -c->host_scalars[1] / n;  // softened 3D gravitational potential
+  } else if (c->model == MD_SHEET1D) {
+    pot = c->host_scalars[1] / n;  // 1D sheets: (1/N) sum_{i<j} |x_i - x_j| (softened for eps > 0)
   } else {
     pot = c->host_scalars[1] / n;  // Eq. 3
   }
@@ -538,7 +541,7 @@ int md_energy(md_ctx *c, double *K, double *V) {
 
 int md_magnetization(md_ctx *c, double *mx, double *my) {
   CHECK_CTX(c);
-  if (c->model == MD_GRAV2D || c->model == MD_GRAV3D)
+  if (c->model != MD_HMF && c->model != MD_RING)
     return set_err(c, MD_EINVAL, "md_magnetization: defined for the HMF and Ring models only");
   double *d = c->hmf_m + 12;
   int rc = hmf_sums_fp64(c, d);

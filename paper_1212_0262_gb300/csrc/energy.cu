@@ -131,6 +131,35 @@ __global__ void __launch_bounds__(NT) potential3d_tiles_kernel(const double *__r
   if (threadIdx.x == 0) unit_sums[(int64_t)ti * ntiles + tj] = b.x;
 }
 
+// 1D sheets: one tile pair (ti <= tj) of sum_{i<j} |x_i - x_j| (eps = 0) or
+// sqrt((x_i - x_j)^2 + eps); the prefactor 1/N is applied at the end.
+__global__ void __launch_bounds__(NT) potential_sheet_tiles_kernel(const double *__restrict__ q, int64_t N,
+                                                                    int ntiles, double eps, double *unit_sums) {
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (tj < ti) return;
+  __shared__ double sx[PT];
+  const int64_t j0 = (int64_t)tj * PT;
+  for (int t = threadIdx.x; t < PT; t += NT) {
+    const int64_t j = j0 + t;
+    if (j < N) sx[t] = q[j];
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)ti * PT + threadIdx.x;
+  double s = 0.0;
+  if (i < N) {
+    const double x = q[i];
+    const int kbeg = ti == tj ? threadIdx.x + 1 : 0;  // j > i inside the diagonal tile
+    const int kend = (int)((N - j0) < PT ? (N - j0) : PT);
+    for (int k = kbeg; k < kend; k++) {
+      const double d = x - sx[k];
+      s += eps > 0.0 ? sqrt(fma(d, d, eps)) : fabs(d);
+    }
+  }
+  __shared__ double2 red[NT / 32];
+  double2 b = block_sum2<NT>(s, 0.0, red);
+  if (threadIdx.x == 0) unit_sums[(int64_t)ti * ntiles + tj] = b.x;
+}
+
 int grid_sum(md_ctx *c, int64_t n) {
   int64_t g = (n + NT - 1) / NT;
   int64_t cap = (int64_t)c->nsm * 8;
@@ -153,6 +182,8 @@ __global__ void potential_finalize_kernel(int model, int64_t N, const double *su
     *V = -sums[0] / (2.0 * n);
   } else if (model == MD_GRAV3D) {
     *V = -sums[0] / n;
+  } else if (model == MD_SHEET1D) {
+    *V = sums[0] / n;
   } else {
     *V = sums[0] / n;
   }
@@ -178,6 +209,8 @@ int potential_with_scratch(cudaStream_t st, int nsm, int grid_cap, int model, in
       potential_tiles_kernel<MD_RING><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, ag, N, ntiles, 0.5 * eps, unit_sums);
     } else if (model == MD_GRAV3D) {
       potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
+    } else if (model == MD_SHEET1D) {
+      potential_sheet_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
     } else {
       potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, nullptr, N, ntiles, eps, unit_sums);
     }
@@ -247,6 +280,8 @@ int pair_potential_fp64(md_ctx *c, double *d_out) {
                                                                                 unit_sums);
   } else if (c->model == MD_GRAV3D) {
     potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
+  } else if (c->model == MD_SHEET1D) {
+    potential_sheet_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
   } else {
     potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, nullptr, N, ntiles, c->eps,
                                                                                   unit_sums);

@@ -21,7 +21,8 @@ extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint
   if (!c) return set_err(nullptr, MD_EINVAL, "md_grad: NULL context");
   if (observable != MD_OBS_KINETIC && observable != MD_OBS_MAGNETIZATION)
     return set_err(c, MD_EINVAL, "md_grad: unknown observable %d", observable);
-  if (c->model == MD_GRAV3D) return set_err(c, MD_EINVAL, "md_grad: not available for the 3D model");
+  if (c->model == MD_GRAV3D || c->model == MD_SHEET1D)
+    return set_err(c, MD_EINVAL, "md_grad: available for the HMF, Ring and 2D models");
   if (observable == MD_OBS_MAGNETIZATION && c->model == MD_GRAV2D)
     return set_err(c, MD_EINVAL, "md_grad: the magnetization is defined for HMF and Ring only");
   if (nsteps < 0 || checkpoint_every < 1) return set_err(c, MD_EINVAL, "md_grad: need nsteps >= 0, checkpoint_every >= 1");
@@ -142,9 +143,11 @@ extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint
 
 extern "C" int md_set_eps(md_ctx *c, double eps) {
   if (!c) return set_err(nullptr, MD_EINVAL, "md_set_eps: NULL context");
-  if (!(eps == eps) || eps - eps != 0.0 || eps < 0.0 || (c->model != MD_HMF && !(eps > 0.0)))
-    return set_err(c, MD_EINVAL, "md_set_eps: eps must be finite and %s", c->model == MD_HMF ? ">= 0" : "> 0");
+  const bool eps0_ok = c->model == MD_HMF || c->model == MD_SHEET1D;
+  if (!(eps == eps) || eps - eps != 0.0 || eps < 0.0 || (!eps0_ok && !(eps > 0.0)))
+    return set_err(c, MD_EINVAL, "md_set_eps: eps must be finite and %s", eps0_ok ? ">= 0" : "> 0");
   c->eps = eps;
-  c->fsal_valid = false;  // the cached force depends on eps
+  c->fsal_valid = false;    // the cached force depends on eps
+  c->mirror_valid = false;  // and the sheet model's padding records do
   return MD_OK;
 }

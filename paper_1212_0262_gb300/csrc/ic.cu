@@ -106,10 +106,12 @@ int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed) {
   const bool angle = c->model == MD_HMF || c->model == MD_RING;
   switch (kind) {
   case MD_IC_WATERBAG:
-    if (!angle) return set_err(c, MD_EINVAL, "water-bag needs an angle model");
+    if (!angle && c->model != MD_SHEET1D) return set_err(c, MD_EINVAL, "water-bag needs an angle or sheet model");
     {
+      // defaults: HMF theta~U[-1,1), p~U[-1.2,1.2); sheets x~U[-1,1), p~U[-0.5,0.5)
+      const double pd = c->model == MD_SHEET1D ? 0.5 : 1.2;
       double tl = params ? params[0] : -1.0, th = params ? params[1] : 1.0;
-      double pl = params ? params[2] : -1.2, ph = params ? params[3] : 1.2;
+      double pl = params ? params[2] : -pd, ph = params ? params[3] : pd;
       if (!(th > tl) || !(ph >= pl)) return set_err(c, MD_EINVAL, "water-bag: empty interval");
       a.a0 = th - tl;
       a.a1 = tl;

@@ -62,13 +62,13 @@ int setup(int dev, double **addr, int *nsm) {
 }  // namespace
 
 extern "C" int md_potential_noalloc(int model, int64_t N, double eps, const double *q, double *V, void *stream) {
-  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D)
+  if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D && model != MD_SHEET1D)
     return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: unknown model %d", model);
   if (N < 1 || N > kMaxN)
     return set_err(nullptr, MD_EINVAL,
                    "md_potential_noalloc: N = %lld is outside [1, %lld], the size its static scratch holds",
                    (long long)N, (long long)kMaxN);
-  if (!(eps == eps) || eps < 0.0 || (model != MD_HMF && !(eps > 0.0)))
+  if (!(eps == eps) || eps < 0.0 || (model != MD_HMF && model != MD_SHEET1D && !(eps > 0.0)))
     return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: bad eps %g", eps);
   if (!q || !V) return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: NULL pointer");
   int dev = 0;

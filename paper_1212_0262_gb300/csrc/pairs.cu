@@ -160,9 +160,15 @@ __global__ void __launch_bounds__(NT) streamk_kernel(PairArgs a) {
 // records in both buffers.
 template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __global__ void mirror_kernel(const double *__restrict__ q, const double *__restrict__ lp, int64_t N, int64_t Npad,
-                              void *m0, void *m1) {
+                              void *m0, void *m1, double eps = 0.0) {
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Npad; i += G) {
+    if constexpr (MODEL == MD_SHEET1D) {
+      const double x = i < N ? q[i] : sheet_pad(eps, MIXED);
+      write_record1<MIXED>(m0, i, x);
+      if (i >= N && m1) write_record1<MIXED>(m1, i, x);
+      continue;
+    }
     if constexpr (MODEL == MD_GRAV3D) {
       if (i < N) {
         write_record3<MIXED>(m0, i, q[i], q[N + i], q[2 * N + i]);
@@ -201,6 +207,8 @@ __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restr
     }
     if constexpr (MODEL == MD_GRAV3D)
       write_record3<MIXED>(mirror_out, i, x[0], x[1], x[D - 1]);
+    else if constexpr (MODEL == MD_SHEET1D)
+      write_record1<MIXED>(mirror_out, i, x[0]);
     else
       write_record_fmt<MODEL, MIXED, false, FMT>(mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
   }
@@ -216,9 +224,10 @@ int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadM
 int ensure_mirrors(md_ctx *c, bool adj) {
   const int64_t Np = padded(c->N);
   // the FP64 record bounds the FP32 one
-  const size_t per = c->model == MD_RING     ? (adj ? 48 : 64)  // Ring forward: tensor-core record
-                     : c->model == MD_GRAV3D ? 32
-                                             : (adj ? 32 : 16);
+  const size_t per = c->model == MD_RING      ? (adj ? 48 : 64)  // Ring forward: tensor-core record
+                     : c->model == MD_GRAV3D  ? 32
+                     : c->model == MD_SHEET1D ? 8
+                                              : (adj ? 32 : 16);
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
     for (int b = 0; b < 2; b++) {
@@ -270,6 +279,9 @@ int dispatch_forward(md_ctx *c, PairArgs a) {
   if constexpr (MODEL == MD_GRAV3D) {
     if constexpr (MIXED) return launch_streamk<Grav3DMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
     else return launch_streamk<Grav3DF64<2, 128, MODE>, MODEL, MIXED, MODE>(c, a);
+  } else if constexpr (MODEL == MD_SHEET1D) {
+    if constexpr (MIXED) return launch_streamk<SheetMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    else return launch_streamk<SheetF64<2, 128, MODE>, MODEL, MIXED, MODE>(c, a);
   } else if constexpr (MIXED) {
     if (c->pt.r_mixed == 4) {
       if constexpr (MODEL == MD_RING) return launch_streamk<RingMixed<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
@@ -319,6 +331,11 @@ int refresh(md_ctx *c, const double *lp) {
   } else if (c->model == MD_GRAV3D) {
     if (mixed) mirror_kernel<MD_GRAV3D, true, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV3D, false, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+  } else if (c->model == MD_SHEET1D) {
+    if (mixed)
+      mirror_kernel<MD_SHEET1D, true, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
+    else
+      mirror_kernel<MD_SHEET1D, false, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
   } else {
     if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
@@ -383,6 +400,8 @@ int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
     return mixed ? dispatch_mode<MD_RING, true>(c, mode, a) : dispatch_mode<MD_RING, false>(c, mode, a);
   if (c->model == MD_GRAV3D)
     return mixed ? dispatch_mode<MD_GRAV3D, true>(c, mode, a) : dispatch_mode<MD_GRAV3D, false>(c, mode, a);
+  if (c->model == MD_SHEET1D)
+    return mixed ? dispatch_mode<MD_SHEET1D, true>(c, mode, a) : dispatch_mode<MD_SHEET1D, false>(c, mode, a);
   return mixed ? dispatch_mode<MD_GRAV2D, true>(c, mode, a) : dispatch_mode<MD_GRAV2D, false>(c, mode, a);
 }
 
@@ -436,6 +455,9 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
   } else if (c->model == MD_GRAV3D) {
     if (mixed) kick_drift_cached_kernel<MD_GRAV3D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_GRAV3D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+  } else if (c->model == MD_SHEET1D) {
+    if (mixed) kick_drift_cached_kernel<MD_SHEET1D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else kick_drift_cached_kernel<MD_SHEET1D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   } else {
     if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);

@@ -14,9 +14,10 @@ constexpr int kPadMultiple = 1024;  // mirror padding: multiple of every TI and 
 // bytes per particle of a mirror record
 template <int MODEL, bool MIXED, bool ADJ>
 struct RecordBytes {
-  static constexpr int value = MODEL == MD_RING     ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32))
-                               : MODEL == MD_GRAV3D ? (MIXED ? 16 : 32)
-                                                    : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
+  static constexpr int value = MODEL == MD_RING      ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32))
+                               : MODEL == MD_GRAV3D  ? (MIXED ? 16 : 32)
+                               : MODEL == MD_SHEET1D ? (MIXED ? 4 : 8)
+                                                     : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
 };
 
 // spatial components of a model's positions
@@ -45,6 +46,21 @@ __device__ __forceinline__ void write_record3(void *mirror, int64_t i, double x,
     m[3] = 0.0;
   }
 }
+// 1D-sheet records: FP32, per particle pair (2k, 2k+1) the floats (-x, -x');
+// FP64, x.  Padding must contribute exactly zero: with eps = 0 a NaN position
+// (both comparisons of the sign are false), with eps > 0 a far one (d^2 overflows,
+// the reciprocal square root is 0).
+template <bool MIXED>
+__device__ __forceinline__ void write_record1(void *mirror, int64_t i, double x) {
+  if constexpr (MIXED)
+    ((float *)mirror)[i] = -(float)x;
+  else
+    ((double *)mirror)[i] = x;
+}
+__device__ __forceinline__ double sheet_pad(double eps, bool mixed) {
+  return eps > 0.0 ? (mixed ? 3.0e19 : 1.0e150) : __longlong_as_double(0x7FF8000000000000LL);
+}
+
 template <bool MIXED>
 __device__ __forceinline__ void write_pad3(void *mirror, int64_t i) {
   if constexpr (MIXED)
@@ -812,6 +828,163 @@ struct Grav3DF64 {
   }
 };
 
+// ------------------------------------------------------------ forward 1D sheets FP32
+// eps = 0: the term of a pair is sign(x_i - x_j), decided on the FP32 positions
+// (the FP32 difference of two floats is zero only for equal floats, so its sign is
+// their order), summed exactly (integers below 2^24 per tile); eps > 0:
+// d / sqrt(d^2 + eps) with one rsqrt.  One accumulator.
+template <int R_, int TJ_, int MODE>
+struct SheetMixed {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = float;
+  static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_SHEET1D, true, false>::value;
+  static constexpr bool MASK = false;  // the self term is zero in both forms
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    float2 x[R], acc[R];
+    CompSum cs[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) { out[0] = csum_total(st.cs[r][0]); }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.x[r] = f2(-((const float *)mirror)[i0 + row_of(r)]);
+      st.acc[r] = f2(0.f);
+      st.cs[r][0] = CompSum{0.f, 0.f};
+    }
+  }
+  __device__ static float sgnf(float d) { return (float)(d > 0.f) - (float)(d < 0.f); }
+  __device__ static float2 term(float2 xi, float2 nx, float2 e2, bool smooth) {
+    const float2 d = __fadd2_rn(xi, nx);
+    if (!smooth) return make_float2(sgnf(d.x), sgnf(d.y));
+    const float2 s = __ffma2_rn(d, d, e2);
+    return __fmul2_rn(d, make_float2(mufu_rsqrt(s.x), mufu_rsqrt(s.y)));
+  }
+  __device__ static void flush(State &st) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      csum_add2(st.cs[r][0], st.acc[r]);
+      st.acc[r] = f2(0.f);
+    }
+  }
+  template <bool SMOOTH>
+  __device__ static void body(State &st, const float2 *sm, float2 e2) {
+#pragma unroll 4
+    for (int k = 0; k < TJ / 2; k++) {
+      const float2 nx = sm[k];
+#pragma unroll
+      for (int r = 0; r < R; r++) st.acc[r] = __fadd2_rn(st.acc[r], term(st.x[r], nx, e2, SMOOTH));
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float2 *sm = (const float2 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    if (a.epsd > 0.0) body<true>(st, sm, e2);
+    else body<false>(st, sm, e2);
+    flush(st);
+  }
+  template <bool SMOOTH>
+  __device__ static void body_sym(State &st, const float2 *sm, float2 e2, float *colsm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k8 = 0; k8 < TJ / 16; k8++) {
+      float v[16];
+#pragma unroll
+      for (int kk = 0; kk < 8; kk++) {
+        const float2 nx = sm[8 * k8 + kk];
+        float2 col = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const float2 t = term(st.x[r], nx, e2, SMOOTH);
+          st.acc[r] = __fadd2_rn(st.acc[r], t);
+          col = __fadd2_rn(col, t);
+        }
+        v[2 * kk] = col.x;
+        v[2 * kk + 1] = col.y;
+      }
+      float sum = butterfly_sum<16, 16>(v, lane);  // value lane >> 1 = 2 kk + (j parity)
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      if ((lane & 1) == 0) colsm[w * TJ + 16 * k8 + (lane >> 1)] = sum;
+    }
+  }
+  // Newton's-third-law variant: the i-rows as in tile<>, and per j the sum over this
+  // warp's rows of the same terms into colsm[warp TJ + j]; sixteen j's at a time.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    const float2 *sm = (const float2 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    if (a.epsd > 0.0) body_sym<true>(st, sm, e2, colsm);
+    else body_sym<false>(st, sm, e2, colsm);
+    flush(st);
+  }
+};
+
+// ------------------------------------------------------------ forward 1D sheets FP64
+template <int R_, int TJ_, int MODE>
+struct SheetF64 {
+  static constexpr int THREADS = NT, MINB = 4;
+  using ColT = double;
+  static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_SHEET1D, false, false>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    double x[R];
+    double accd[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) { out[0] = st.accd[r][0]; }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      st.x[r] = ((const double *)mirror)[i0 + row_of(r)];
+      st.accd[r][0] = 0.0;
+    }
+  }
+  __device__ static double term(double xi, double xj, double eps, bool smooth) {
+    const double d = xi - xj;
+    if (!smooth) return (double)(d > 0.0) - (double)(d < 0.0);
+    return d * rsqrt_nr(fma(d, d, eps));
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double *sm = (const double *)smb;
+    const bool smooth = a.epsd > 0.0;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double xj = sm[k];
+#pragma unroll
+      for (int r = 0; r < R; r++) st.accd[r][0] += term(st.x[r], xj, a.epsd, smooth);
+    }
+  }
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
+    const double *sm = (const double *)smb;
+    const bool smooth = a.epsd > 0.0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k16 = 0; k16 < TJ / 16; k16++) {
+      double v[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; kk++) {
+        const double xj = sm[16 * k16 + kk];
+        double col = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const double t = term(st.x[r], xj, a.epsd, smooth);
+          st.accd[r][0] += t;
+          col += t;
+        }
+        v[kk] = col;
+      }
+      double sum = butterfly_sum<16, 16>(v, lane);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      if ((lane & 1) == 0) colsm[w * TJ + 16 * k16 + (lane >> 1)] = sum;
+    }
+  }
+};
+
 // ------------------------------------------------------------ adjoint Ring FP32
 // accumulators: 0 = sum S dd^-3/2 (force), 1 = sum G w (J v), 2 = sum S dd^-5/2 (d/deps)
 template <int R_, int TJ_, int MODE>
@@ -1303,7 +1476,7 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
                                             : -2.0 / (double)a.N;
   double f[D], x[D];
 #pragma unroll
-  for (int d = 0; d < D; d++) f[d] = scale * acc[d];
+  for (int d = 0; d < D; d++) f[d] = MODEL == MD_SHEET1D ? -acc[d] / (double)a.N : scale * acc[d];
   if (MODE == STAGE_FORCE_ONLY) {
 #pragma unroll
     for (int d = 0; d < D; d++) a.fout[d * a.N + i] = f[d];
@@ -1323,6 +1496,8 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
   if (MODE == STAGE_KICK_DRIFT) {
     if constexpr (MODEL == MD_GRAV3D)
       write_record3<MIXED>(a.mirror_out, i, x[0], x[1], x[D - 1]);
+    else if constexpr (MODEL == MD_SHEET1D)
+      write_record1<MIXED>(a.mirror_out, i, x[0]);
     else
       write_record_fmt<MODEL, MIXED, false, FMT>(a.mirror_out, i, x[0], x[D - 1], 0.0, 0.0);
   }

@@ -280,7 +280,7 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.mirror_out = c->mirror[1 - c->mirror_cur];
   a.q = c->q;
   a.p = c->p;
-  a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;  // 2D, 3D: eps
+  a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;  // 2D, 3D, sheets: eps
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
   kern<<<a.P, THR, 0, c->stream>>>(a, s);
@@ -296,6 +296,9 @@ int sym_dispatch(md_ctx *c, PairArgs a) {
   if constexpr (MODEL == MD_GRAV3D) {
     if constexpr (MIXED) return launch_sym<Grav3DMixed<4, 256, MODE>, MODEL, true, MODE>(c, a);
     else return launch_sym<Grav3DF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
+  } else if constexpr (MODEL == MD_SHEET1D) {
+    if constexpr (MIXED) return launch_sym<SheetMixed<8, 256, MODE>, MODEL, true, MODE>(c, a);
+    else return launch_sym<SheetF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
   } else if constexpr (!MIXED) {
     // 4 rows per thread: the column butterflies' FP64 adds are shared by twice the pairs
     if constexpr (MODEL == MD_RING) return launch_sym<RingF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
@@ -333,6 +336,8 @@ bool sym_applies(const md_ctx *c) {
     TI = 512, TJ = 128, colbytes = 8;
   } else if (c->model == MD_GRAV3D) {
     TI = 512, TJ = 256, colbytes = 4;
+  } else if (c->model == MD_SHEET1D) {
+    TI = 1024, TJ = 256, colbytes = 4;
   } else if (c->model == MD_RING) {
     if (!c->pt.ring_tc || c->pt.ring_tc == 2 || c->pt.r_mixed == 4) return false;
     TI = 256, TJ = 256, colbytes = 4;
@@ -356,5 +361,7 @@ int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout)
   if (c->model == MD_RING) return mixed ? sym_mode<MD_RING, true>(c, mode, a) : sym_mode<MD_RING, false>(c, mode, a);
   if (c->model == MD_GRAV3D)
     return mixed ? sym_mode<MD_GRAV3D, true>(c, mode, a) : sym_mode<MD_GRAV3D, false>(c, mode, a);
+  if (c->model == MD_SHEET1D)
+    return mixed ? sym_mode<MD_SHEET1D, true>(c, mode, a) : sym_mode<MD_SHEET1D, false>(c, mode, a);
   return mixed ? sym_mode<MD_GRAV2D, true>(c, mode, a) : sym_mode<MD_GRAV2D, false>(c, mode, a);
 }

@@ -7,7 +7,8 @@
 
 extern "C" int md_tangent_step(md_ctx *c, int64_t nsteps, double *dq, double *dp) {
   if (!c) return set_err(nullptr, MD_EINVAL, "md_tangent_step: NULL context");
-  if (c->model == MD_GRAV3D) return set_err(c, MD_EINVAL, "md_tangent_step: not available for the 3D model");
+  if (c->model == MD_GRAV3D || c->model == MD_SHEET1D)
+    return set_err(c, MD_EINVAL, "md_tangent_step: available for the HMF, Ring and 2D models");
   if (nsteps < 0 || !dq || !dp) return set_err(c, MD_EINVAL, "md_tangent_step: need nsteps >= 0 and arrays");
   if (nsteps == 0) return MD_OK;
   const int64_t n = (int64_t)c->dim * c->N;

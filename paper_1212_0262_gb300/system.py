@@ -10,7 +10,7 @@ import numpy as np
 
 from . import binding as B
 
-MODELS = {"hmf": 0, "ring": 1, "grav2d": 2, "2d": 2, "grav3d": 3, "3d": 3}
+MODELS = {"hmf": 0, "ring": 1, "grav2d": 2, "2d": 2, "grav3d": 3, "3d": 3, "sheet1d": 4, "sheets": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 

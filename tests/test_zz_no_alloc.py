@@ -17,7 +17,7 @@ from paper_1212_0262_gb300 import System, binding, inputs
 pytestmark = pytest.mark.gpu
 
 CASES = [(0, 65536, 0.0), (1, 4097, 0.01), (2, 65536, 1e-4), (1, 1, 0.01), (2, 333, 1e-3), (3, 65536, 1e-3),
-         (3, 1, 1e-3)]
+         (3, 1, 1e-3), (4, 65536, 0.0), (4, 777, 1e-3)]
 
 
 def _noalloc(model, N, eps, q_dev, v_dev, stream):
