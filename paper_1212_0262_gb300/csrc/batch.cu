@@ -14,10 +14,12 @@
 //
 // Mixed precision runs, by default, the Newton's-third-law form of each part
 // (every unordered pair of a system once, as the single-system stages in
-// sym.cu): a pair launch whose parts walk the triangular (system, i-tile,
-// j-tile) units of their systems stream-K style and write row and column
-// partials, then a finish launch with one CTA per (system, tile, chunk of 16
-// column-partial rows) that sums them in a fixed order and runs the epilogue.
+// sym.cu): one pair launch per part, each over the whole GPU, walking the
+// triangular (system, i-tile, j-tile) units of its systems stream-K style and
+// writing row and column partials, then one finish launch with a CTA per
+// (system, tile, chunk of 16 column-partial rows) that sums them in a fixed
+// order and runs the epilogue.  (The one-sided form shares one launch between
+// the parts, split by md_batch_set_tuning's `split`.)
 #include <algorithm>
 #include <vector>
 
@@ -239,7 +241,7 @@ __device__ __forceinline__ void sym_locate(const PartArgs &A, int64_t u, int &s,
 // column partial of every off-diagonal unit.  smem: the j-tile double buffer,
 // then the per-warp column sums.
 template <class Pol>
-__device__ __noinline__ void batch_sym_pairs(const PartArgs &A, int64_t cta, unsigned char *smem) {
+__device__ __forceinline__ void batch_sym_pairs(const PartArgs &A, int64_t cta, unsigned char *smem) {
   constexpr int TJ = Pol::TJ, NACC = Pol::NACC, NW = NT / 32;
   constexpr int TILE_BYTES = TJ * Pol::JB;
   constexpr int CHUNKS = TILE_BYTES / 16;
@@ -400,14 +402,12 @@ constexpr int sym_smem_bytes() {
   return 2 * Pol::TJ * Pol::JB + (NT / 32) * Pol::TJ * Pol::NACC * 4;
 }
 
-template <class PolR, class PolG>
-__global__ void __launch_bounds__(NT) batch_sym_pairs_kernel(PartArgs ring, PartArgs grav) {
-  constexpr int BYTES = sym_smem_bytes<PolR>() > sym_smem_bytes<PolG>() ? sym_smem_bytes<PolR>() : sym_smem_bytes<PolG>();
-  __shared__ __align__(16) unsigned char smem[BYTES];
-  if ((int)blockIdx.x < ring.P)
-    batch_sym_pairs<PolR>(ring, blockIdx.x, smem);
-  else
-    batch_sym_pairs<PolG>(grav, (int64_t)blockIdx.x - ring.P, smem);
+// One launch per part, each sized by its own occupancy (the parts' systems are
+// disjoint, so the launches simply follow each other on the stream).
+template <class Pol>
+__global__ void __launch_bounds__(NT, Pol::MINB) batch_sym_pairs_kernel(PartArgs part) {
+  __shared__ __align__(16) unsigned char smem[sym_smem_bytes<Pol>()];
+  batch_sym_pairs<Pol>(part, blockIdx.x, smem);
 }
 
 template <class PolR, class PolG, int MODE>
@@ -606,10 +606,12 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   const int64_t TI[2] = {TIr, TIg}, TJ[2] = {PolR::TJ, PolG::TJ};
   int rc = ensure_layout(b, TI, TJ, true);
   if (rc) return rc;
-  auto kern = batch_sym_pairs_kernel<PolR, PolG>;
-  const int occ = occupancy(b, (const void *)kern);
-  int64_t Pr, Pg;
-  split_ctas(b, (int64_t)b->nsm * occ, Pr, Pg);
+  // full GPU for each part in turn: CTA counts from each kernel's own occupancy
+  auto kern_r = batch_sym_pairs_kernel<PolR>;
+  auto kern_g = batch_sym_pairs_kernel<PolG>;
+  const int occ_r = occupancy(b, (const void *)kern_r), occ_g = occupancy(b, (const void *)kern_g);
+  const int64_t Pr = std::min<int64_t>((int64_t)b->nsm * occ_r, b->Ur);
+  const int64_t Pg = std::min<int64_t>((int64_t)b->nsm * occ_g, b->Ug);
   const size_t slot_r = (size_t)Pr * 2 * NAr * TIr, slot_g = (size_t)Pg * 2 * NAg * TIg;
   const size_t row_r = (size_t)b->rows_r * NAr * TIr, row_g = (size_t)b->rows_g * NAg * TIg;
   const size_t col_r = (size_t)b->Ur * PolR::TJ * NAr, col_g = (size_t)b->Ug * PolG::TJ * NAg;
@@ -646,8 +648,14 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ar.cur = ag.cur = b->cur;
   ar.b = ag.b = bc;
   ar.d = ag.d = dc;
-  kern<<<(int)(Pr + Pg), NT, 0, b->stream>>>(ar, ag);
-  b->launches++;
+  if (Pr > 0) {
+    kern_r<<<(int)Pr, NT, 0, b->stream>>>(ar);
+    b->launches++;
+  }
+  if (Pg > 0) {
+    kern_g<<<(int)Pg, NT, 0, b->stream>>>(ag);
+    b->launches++;
+  }
   batch_sym_finish_kernel<PolR, PolG, MODE><<<(unsigned)(b->nfin_r + b->nfin_g), kFinishThreadsB, 0, b->stream>>>(ar, ag);
   b->launches++;
   cudaError_t e = cudaGetLastError();
