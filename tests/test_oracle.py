@@ -384,7 +384,7 @@ def test_force_rows_equals_full_force_3d(ora):
     assert np.allclose(ab, ora.force_abs(3, q, 1e-3).reshape(3, 50)[:, rows], rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3), (4, 0.0), (4, 1e-3)])
 def test_force_rows_equals_full_force(ora, model, eps):
     q, _ = _state(model, 50, 91)
     rows = np.array([0, 7, 49, 23])
