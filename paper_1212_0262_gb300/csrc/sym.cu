@@ -37,6 +37,8 @@
 // the few CTAs that cover the many short rows at the end of the order.
 // Column partials take U TJ NACC floats: beyond kSymMaxColBytes the one-sided
 // kernel runs instead.
+#include <mutex>
+
 #include "pairs_impl.cuh"
 
 namespace {
@@ -230,12 +232,12 @@ int launch_sym(md_ctx *c, PairArgs a) {
   constexpr int64_t TI = (int64_t)THR * Pol::R;
   constexpr int TJ = Pol::TJ, NACC = Pol::NACC;
   auto kern = sym_pairs_kernel<Pol>;
-  static bool carveout_set = false;  // once per kernel, before any stream capture
-  if (!carveout_set) {
-    // the grid is sized for the occupancy limit: make the shared-memory carveout allow it
+  // the grid is sized for the occupancy limit: make the shared-memory carveout allow it
+  // (once per kernel, on the first call, which runs before any stream capture)
+  static std::once_flag carveout_once;
+  std::call_once(carveout_once, [&] {
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    carveout_set = true;
-  }
+  });
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THR, 0);
   if (occ < 1) occ = 1;

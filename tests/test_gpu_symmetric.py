@@ -146,3 +146,17 @@ def test_symmetric_ring_rsqrt_on_fma_pipe(N, off):
     scale = ora.force_abs(1, q, EPS[1])
     err = np.abs(f - fo)
     assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
+
+
+def test_symmetric_falls_back_to_one_sided_beyond_the_column_cap():
+    """Ring N = 1,048,576 needs 7.6 GB of column partials, beyond the 4 GiB cap: the
+    one-sided tensor-core kernel runs instead, with the same error bound."""
+    N = 1 << 20
+    s = System(1, N, 0.01, 0.05, 47, precision="mixed")
+    assert s.force_kernel == 3  # one-sided, tensor-core products
+    q, _ = s.get_state()
+    f = s.force()
+    rows = np.array([0, 12345, N - 1])
+    fo, scale = ora.force_rows(1, q, rows, 0.01, with_abs=True)
+    assert np.all(np.abs(f[rows] - fo[0]) <= 2e-5 * scale[0])
+    s.close()
