@@ -285,3 +285,24 @@ def test_step_on_the_legacy_default_stream(model):
     qa, pa = a.get_state()
     qb, pb = b.get_state()
     assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+
+
+@pytest.mark.parametrize("offset", [1e3, -2.5e4, 3e6])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+@pytest.mark.parametrize("model", [0, 1])
+def test_large_angles_keep_parity(model, prec, tol, offset):
+    """The FP64 state is never wrapped, so angles grow over long runs; the FP32 paths
+    reduce theta - 2 pi k before FP32 arithmetic (HMF: float-pair split and FP32
+    Cody-Waite; Ring mirror: FP64 Cody-Waite).  Forces at angles shifted far from
+    [-pi, pi) keep the bounds."""
+    N = 2049
+    q, p = inputs.default_state(model, N, 77)
+    q = q + offset
+    with System(model, N, EPS[model], 0.05, 1, precision=prec) as s:
+        s.set_state(q, p)
+        f = s.force()
+    fo = ora.force(model, q, EPS[model])
+    scale = ora.force_abs(model, q, EPS[model])
+    # the angles themselves carry |theta| ulp(1) of representation error in FP64
+    slack = 0.0 if prec == "mixed" else 4 * abs(offset) * 2.2e-16 * scale
+    assert np.all(np.abs(f - fo) <= tol * scale + slack + 1e-300), (np.abs(f - fo) / scale).max()
