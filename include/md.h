@@ -224,7 +224,11 @@ int md_tangent_step(md_ctx *ctx, int64_t nsteps, double *dq, double *dp);
 
 /* Route the library's device allocations through alloc(bytes, user) and
  * free(ptr, user) (for example a caching allocator of the host framework).
- * alloc returns NULL on failure, which the library reports as MD_ENOMEM.
+ * alloc returns NULL on failure, which the library reports as MD_ENOMEM; it must
+ * return device memory aligned to 256 bytes (a block that is not is handed back to
+ * free and the allocation fails with MD_ENOMEM).  The library synchronises the
+ * device before it passes a block to free (cudaFree would), so the allocator may
+ * reuse it at once.
  * Passing NULL for both restores cudaMalloc / cudaFree.  Applies to allocations
  * made after the call; memory is freed by the allocator that made it. */
 int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(void *ptr, void *user),

@@ -72,6 +72,10 @@ void *dev_alloc(size_t bytes) {
   if (g_alloc) {
     ptr = g_alloc(bytes, g_alloc_user);
     if (!ptr) return nullptr;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 255u) != 0) {  // the kernels' vector loads need 256 B
+      if (g_free) g_free(ptr, g_alloc_user);
+      return nullptr;
+    }
     g_blocks[ptr] = AllocRec{g_free, g_alloc_user};
   } else {
     if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
@@ -93,10 +97,14 @@ void dev_free(void *p) {
     r = it->second;
     g_blocks.erase(it);
   }
-  if (r.free_fn)
+  if (r.free_fn) {
+    // cudaFree waits for the device; a caching allocator may hand the block out at
+    // once, so finish every queued kernel that may still read it first
+    cudaDeviceSynchronize();
     r.free_fn(p, r.user);
-  else
+  } else {
     cudaFree(p);
+  }
 }
 
 void yoshida_coefficients(double c[4]) {
