@@ -587,7 +587,7 @@ def run_adjoint(args, w):
     import numpy as np
     import torch
 
-    from paper_1212_0262_gb300 import System
+    from paper_1212_0262_gb300 import System, binding
 
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
@@ -616,6 +616,25 @@ def run_adjoint(args, w):
     rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
     err = {"grad_q": rel(out["mixed"][1], out["fp64"][1]), "grad_p": rel(out["mixed"][2], out["fp64"][2]),
            "grad_eps": abs(out["mixed"][3] - out["fp64"][3]) / abs(out["fp64"][3]), "N": n2}
+    # roofline by time: the forward stages (unordered pair terms of the symmetric 2D
+    # kernel) and the reverse stages (the one-sided reverse kernel: per ordered pair
+    # dx, dy, s (2), inv^2, w (2), the (r.w) product (4), f (2), J w (4), df/deps (2) =
+    # 19 FP32 operations and one rcp) at their pipe bounds, against the measured time
+    roofline = None
+    if args.prec == "mixed":
+        rates = np.zeros(19)
+        binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 19)
+        nsm, fp32 = rates[0], max(rates[1], rates[3])
+        mhz = clocks.get("sm_mhz") or rates[2]
+        clk = nsm * mhz * 1e6
+        fwd_terms = 3 * nsteps * N * (N - 1) / 2
+        rev_pairs = (3 * nsteps + 1) * float(N) * N
+        t_fwd = fwd_terms / (clk * min(fp32 / PAIR_KERNELS[(2, 4)][1], rates[7]))
+        t_rev = rev_pairs / (clk * min(fp32 / 19.0, rates[7]))
+        roofline = {"bound": "alu", "achieved": (t_fwd + t_rev) / el, "peak": 1.0, "unit": "fraction of the pipe-bound time",
+                    "frac": (t_fwd + t_rev) / el, "traffic": None,
+                    "kernel": "sym_pairs_kernel<GravMixed> forward + streamk_kernel<GravMixedAdj> reverse",
+                    "ideal_seconds": {"forward": t_fwd, "reverse": t_rev}, "sm_mhz": mhz}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": pairs / el, "unit": w["unit"], "n_gpus": ws, "steps": args.steps,
@@ -625,7 +644,7 @@ def run_adjoint(args, w):
                                             "nsteps": nsteps, "checkpoint_every": K},
             "gradient_seconds": el, "value_K_T": val, "grad_eps": ge,
             "mixed_vs_fp64_gradient_rel_error": err, "gpu_launches": launches, "clocks": clocks,
-            "roofline": None, "cpu_baseline": None, "e2e": None}), flush=True)
+            "roofline": roofline, "cpu_baseline": None, "e2e": None}), flush=True)
     s.close()
 
 
@@ -634,13 +653,13 @@ def main():
     if args.workload == "ensemble" and args.impl == "ours":
         run_ensemble(args, WORKLOADS["ensemble"])
         return
-    if args.workload == "adjoint" and args.impl == "ours":
-        run_adjoint(args, WORKLOADS["adjoint"])
-        return
     w = dict(WORKLOADS[args.workload])
     if args.n:
         w["N"] = args.n
         w["name"] = w["name"].split(" N=")[0] + f" N={args.n:,} (reduced size)"
+    if args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint(args, w)
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return

@@ -353,10 +353,15 @@ __device__ __noinline__ void batch_sym_finish(const PartArgs &A, int64_t f) {
   for (int o = threadIdx.x; o < OUT; o += kFinishThreadsB) {
     const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);
     CompSum cs{0.f, 0.f};
+    // unit (I2, T m + jsub) advances by n_jt - m (I2 + 1) from I2 to I2 + 1
+    int64_t off = (S.ubeg + sym_rowstart(I_lo, S.n_jt, m) + (T * m + jsub - (int64_t)m * I_lo)) * (TJ * NACC) + rest;
+    int64_t step = (S.n_jt - (int64_t)m * (I_lo + 1)) * (TJ * NACC);
+    const int64_t dstep = (int64_t)m * (TJ * NACC);
 #pragma unroll 8
     for (int64_t I2 = I_lo; I2 < I_hi; I2++) {
-      const int64_t u = S.ubeg + sym_rowstart(I2, S.n_jt, m) + (T * m + jsub - (int64_t)m * I2);
-      csum_add(cs, __ldcg(A.colslot + u * (TJ * NACC) + rest));
+      csum_add(cs, __ldcg(A.colslot + off));
+      off += step;
+      step -= dstep;
     }
     chunk[(int64_t)c * OUT + o] = csum_total(cs);
   }

@@ -182,11 +182,17 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
     const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);
     CompSum cs{0.f, 0.f};  // FP32 column partials: compensated FP32 sum
     double sd = 0.0;       // FP64 column partials
+    // unit (I2, T m + jsub) = rowstart(I2) + T m + jsub - m I2; from I2 to I2 + 1 it
+    // advances by the length of row I2 minus m, i.e. n_jt - m (I2 + 1)
+    int64_t off = (sym_rowstart(I_lo, a.n_jt, m) + (T * m + jsub - (int64_t)m * I_lo)) * (TJ * NACC) + rest;
+    int64_t step = (a.n_jt - (int64_t)m * (I_lo + 1)) * (TJ * NACC);
+    const int64_t dstep = (int64_t)m * (TJ * NACC);
 #pragma unroll 8
     for (int64_t I2 = I_lo; I2 < I_hi; I2++) {
-      const int64_t u = sym_rowstart(I2, a.n_jt, m) + (T * m + jsub - (int64_t)m * I2);
-      if constexpr (sizeof(ColT) == 4) csum_add(cs, __ldcg(col + u * (TJ * NACC) + rest));
-      else sd += __ldcg(col + u * (TJ * NACC) + rest);
+      if constexpr (sizeof(ColT) == 4) csum_add(cs, __ldcg(col + off));
+      else sd += __ldcg(col + off);
+      off += step;
+      step -= dstep;
     }
     chunk[(int64_t)c * OUT + o] = sizeof(ColT) == 4 ? csum_total(cs) : sd;
   }

@@ -306,3 +306,31 @@ def test_large_angles_keep_parity(model, prec, tol, offset):
     # the angles themselves carry |theta| ulp(1) of representation error in FP64
     slack = 0.0 if prec == "mixed" else 4 * abs(offset) * 2.2e-16 * scale
     assert np.all(np.abs(f - fo) <= tol * scale + slack + 1e-300), (np.abs(f - fo) / scale).max()
+
+
+def test_small_config_hmf_n1e4_fp64_100_steps():
+    """The small configuration as stated: HMF, N = 10,000, FP64, water-bag theta in
+    [-1, 1), p in [-1.2, 1.2) (seed 1), dt = 0.1, 100 steps; total energy,
+    magnetization and relative energy error against the oracle's run of the same
+    steps (mean-field HMF has a small Lyapunov exponent, so summation-order
+    differences stay near rounding over this span)."""
+    N, dt, nsteps = 10_000, 0.1, 100
+    q0, p0 = inputs.waterbag(N, 1)
+    with System(0, N, 0.0, dt, 1, precision="fp64") as s:
+        s.set_state(q0, p0)
+        e0 = sum(s.energy())
+        s.step(nsteps)
+        q, p = s.get_state()
+        K, V = s.energy()
+        mx, my = s.magnetization()
+    qo, po = ora.step(0, q0, p0, 0.0, dt, nsteps)
+    assert np.max(np.abs(q - qo)) <= 1e-10 * max(1.0, np.abs(qo).max())
+    assert np.max(np.abs(p - po)) <= 1e-10 * max(1.0, np.abs(po).max())
+    eo = ora.energy(0, qo, po)
+    e0o = ora.energy(0, q0, p0)
+    assert abs((K + V) - eo) <= 1e-10 * abs(eo)
+    assert abs(e0 - e0o) <= 1e-12 * abs(e0o)
+    mxo, myo = ora.magnetization(qo)
+    assert abs(mx - mxo) < 1e-10 and abs(my - myo) < 1e-10
+    de, deo = abs((K + V - e0) / e0), abs((eo - e0o) / e0o)
+    assert abs(de - deo) <= 1e-3 * deo + 1e-13, (de, deo)
