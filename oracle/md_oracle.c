@@ -540,6 +540,40 @@ void ora_hvp(int model, int64_t N, double eps, const double *q, const double *v,
       out[i] = -2.0 * ax / (double)N;
       out[N + i] = -2.0 * ay / (double)N;
     }
+  } else if (model == ORA_GRAV3D) {
+    /* phi(r) = -(1/N) r s^(-3/2):  dphi/dr w = -(1/N)[w s^(-3/2) - 3 r (r.w) s^(-5/2)]. */
+    const double *x = q, *y = q + N, *z = q + 2 * N, *vx = v, *vy = v + N, *vz = v + 2 * N;
+    for (int64_t i = 0; i < N; i++) {
+      double ax = 0.0, ay = 0.0, az = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+        double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
+        double s = dx * dx + dy * dy + dz * dz + eps;
+        double s32 = s * sqrt(s), s52 = s * s * sqrt(s);
+        double rw = dx * wx + dy * wy + dz * wz;
+        ax += wx / s32 - 3.0 * dx * rw / s52;
+        ay += wy / s32 - 3.0 * dy * rw / s52;
+        az += wz / s32 - 3.0 * dz * rw / s52;
+      }
+      out[i] = -ax / (double)N;
+      out[N + i] = -ay / (double)N;
+      out[2 * N + i] = -az / (double)N;
+    }
+  } else if (model == ORA_SHEET1D) {
+    /* eps > 0: phi(d) = -(1/N) d / sqrt(d^2 + eps), dphi/dd = -(1/N) eps (d^2 + eps)^(-3/2);
+     * eps = 0: the sign force is piecewise constant, its derivative 0 between crossings. */
+    for (int64_t i = 0; i < N; i++) {
+      double a = 0.0;
+      if (eps > 0.0)
+        for (int64_t j = 0; j < N; j++) {
+          if (j == i) continue;
+          double d = q[i] - q[j];
+          double sd = d * d + eps;
+          a += eps / (sd * sqrt(sd)) * (v[i] - v[j]);
+        }
+      out[i] = -a / (double)N;
+    }
   } else {
     for (int64_t i = 0; i < N; i++) out[i] = -v[i];
   }
@@ -590,6 +624,36 @@ void ora_dforce_deps(int model, int64_t N, double eps, const double *q, double *
       }
       out[i] = 2.0 * sx / (double)N;
       out[N + i] = 2.0 * sy / (double)N;
+    }
+  } else if (model == ORA_GRAV3D) {
+    /* d/deps of -(1/N) r s^(-3/2) = (3/(2N)) r s^(-5/2). */
+    const double *x = q, *y = q + N, *z = q + 2 * N;
+    for (int64_t i = 0; i < N; i++) {
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+        double s = dx * dx + dy * dy + dz * dz + eps;
+        double s52 = s * s * sqrt(s);
+        sx += dx / s52;
+        sy += dy / s52;
+        sz += dz / s52;
+      }
+      out[i] = 1.5 * sx / (double)N;
+      out[N + i] = 1.5 * sy / (double)N;
+      out[2 * N + i] = 1.5 * sz / (double)N;
+    }
+  } else if (model == ORA_SHEET1D && eps > 0.0) {
+    /* d/deps of -(1/N) d (d^2 + eps)^(-1/2) = (1/(2N)) d (d^2 + eps)^(-3/2). */
+    for (int64_t i = 0; i < N; i++) {
+      double a = 0.0;
+      for (int64_t j = 0; j < N; j++) {
+        if (j == i) continue;
+        double d = q[i] - q[j];
+        double sd = d * d + eps;
+        a += d / (sd * sqrt(sd));
+      }
+      out[i] = 0.5 * a / (double)N;
     }
   } else {
     int64_t n = (int64_t)ora_dim(model) * N;

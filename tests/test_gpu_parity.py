@@ -334,3 +334,36 @@ def test_small_config_hmf_n1e4_fp64_100_steps():
     assert abs(mx - mxo) < 1e-10 and abs(my - myo) < 1e-10
     de, deo = abs((K + V - e0) / e0), abs((eo - e0o) / e0o)
     assert abs(de - deo) <= 1e-3 * deo + 1e-13, (de, deo)
+
+
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
+def test_switching_precision_eps_and_state_between_steps(model):
+    """Every cache (force, mirrors in both record formats, HMF sums and the FP64
+    (cos, sin) buffer, step graphs) follows precision switches, eps changes and
+    state replacements between steps: the run matches the oracle's run of the same
+    segments (FP32 pair arithmetic in the mixed segments bounds the agreement)."""
+    eps = {0: 0.0, 1: 0.01, 2: 1e-3, 3: 1e-3, 4: 1e-3}[model]
+    eps2 = {0: 0.0, 1: 0.02, 2: 2e-3, 3: 2e-3, 4: 0.0}[model]
+    N, dt = 1000, 0.02
+    q0, p0 = inputs.default_state(model, N, 90)
+    with System(model, N, eps, dt, 1, precision="fp64") as s:
+        s.set_state(q0, p0)
+        s.step(3)
+        s.set_precision("mixed")
+        s.step(10)
+        s.set_precision("fp64")
+        s.step(9)
+        s.set_eps(eps2)
+        s.step(3)
+        qm, pm = s.get_state()
+        q1, p1 = inputs.default_state(model, N, 91)
+        s.set_state(q1, p1)
+        s.step(2)
+        q, p = s.get_state()
+    qo, po = ora.step(model, q0, p0, eps, dt, 22)
+    qo, po = ora.step(model, qo, po, eps2, dt, 3)
+    assert np.max(np.abs(qm - qo)) <= 1e-5 * max(1.0, np.abs(qo).max())
+    assert np.max(np.abs(pm - po)) <= 1e-5 * max(1.0, np.abs(po).max())
+    qo, po = ora.step(model, q1, p1, eps2, dt, 2)
+    assert np.max(np.abs(q - qo)) <= 1e-11 * max(1.0, np.abs(qo).max())
+    assert np.max(np.abs(p - po)) <= 1e-11 * max(1.0, np.abs(po).max())

@@ -315,7 +315,7 @@ def test_two_body_energy_conservation(ora):
 
 # --------------------------------------------- derivatives and the adjoint -
 
-@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3)])
+@pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (2, 1e-3), (3, 1e-3), (4, 1e-3), (4, 0.5)])
 def test_hvp_matches_finite_difference_of_force(ora, model, eps):
     N = 16
     q, _ = _state(model, N, 51)
@@ -329,7 +329,7 @@ def test_hvp_matches_finite_difference_of_force(ora, model, eps):
         assert np.max(np.abs(jmf - jv)) < 1e-13 * np.max(np.abs(jv))
 
 
-@pytest.mark.parametrize("model,eps", [(1, 0.01), (2, 1e-3)])
+@pytest.mark.parametrize("model,eps", [(1, 0.01), (2, 1e-3), (3, 1e-3), (4, 1e-3), (4, 0.5)])
 def test_dforce_deps_matches_finite_difference(ora, model, eps):
     q, _ = _state(model, 16, 61)
     h = 1e-7 * eps
@@ -339,7 +339,7 @@ def test_dforce_deps_matches_finite_difference(ora, model, eps):
 
 
 @pytest.mark.parametrize("model,eps,obs", [(0, 0.0, 0), (0, 0.0, 1), (1, 0.01, 0), (1, 0.01, 1),
-                                           (2, 1e-3, 0)])
+                                           (2, 1e-3, 0), (3, 1e-2, 0), (4, 0.05, 0)])
 def test_adjoint_matches_central_differences(ora, model, eps, obs):
     N, dt, ns = 12, 0.05, 6
     q0, p0 = _state(model, N, 71 + model)
