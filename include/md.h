@@ -48,14 +48,14 @@ extern "C" {
                      * Kac 1/N coupling and additive softening as in Eqs. 1-3:
                      * V = -(1/N) sum_{i<j} (|r_ij|^2 + eps)^(-1/2),
                      * f_i = -(1/N) sum_j r_ij (|r_ij|^2 + eps)^(-3/2).
-                     * Forward stages and observables; no md_grad / md_tangent_step. */
+                     * md_grad / md_tangent_step with the kinetic observable. */
 #define MD_SHEET1D 4 /* 1D self-gravitating sheets (named in the paper's introduction among
                       * long-range models, not studied there): unit masses, Kac 1/N coupling,
                       * V = (1/N) sum_{i<j} |x_i - x_j| for eps = 0 (f_i = -(1/N) sum_j
                       * sign(x_i - x_j), sign(0) = 0: exact integer counts), or
                       * sqrt((x_i - x_j)^2 + eps) for eps > 0.  eps >= 0.  In MD_MIXED the
-                      * eps = 0 signs are decided on the FP32 positions.  Forward stages
-                      * and observables; no md_grad / md_tangent_step. */
+                      * eps = 0 signs are decided on the FP32 positions.  md_grad and
+                      * md_tangent_step need eps > 0 (the eps = 0 force is piecewise constant). */
 
 /* precisions */
 #define MD_FP64 0
@@ -208,8 +208,8 @@ int md_magnetization(md_ctx *ctx, double *mx, double *my);
  * checkpoint stored every `checkpoint_every` steps (>= 1).
  * grad_q, grad_p: host arrays of dim*N (required); grad_eps, value: host scalars
  * (may be NULL; grad_eps is 0 for HMF).  Synchronous.  Uses the context's
- * precision for the force and Jacobian-vector products.  MD_EINVAL for MD_GRAV3D and
- * MD_SHEET1D. */
+ * precision for the force and Jacobian-vector products.  MD_EINVAL for
+ * MD_OBS_MAGNETIZATION outside HMF and Ring, and for MD_SHEET1D at eps = 0. */
 int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
             double *grad_q, double *grad_p, double *grad_eps, double *value);
 
@@ -219,7 +219,7 @@ int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
  * each drift, J = df/dq).  The building block of largest-Lyapunov-exponent
  * estimates (repeat, renormalising the tangent).  dq, dp: host arrays of dim*N,
  * read and overwritten.  Uses the context's precision.  Synchronous.  MD_EINVAL for
- * MD_GRAV3D and MD_SHEET1D. */
+ * MD_SHEET1D at eps = 0. */
 int md_tangent_step(md_ctx *ctx, int64_t nsteps, double *dq, double *dp);
 
 /* Route the library's device allocations through alloc(bytes, user) and

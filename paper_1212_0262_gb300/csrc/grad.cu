@@ -13,7 +13,7 @@
 // makes exact up to rounding; every `checkpoint_every` steps the state is reset
 // to an FP64 copy stored by the forward pass, which bounds the accumulated
 // rounding drift.  Each reverse stage is one fused kernel: force, J lambda_p and
-// df/deps from a single pair pass (Ring/2D) or from four mean-field sums (HMF).
+// df/deps from a single pair pass (pair models) or from four mean-field sums (HMF).
 #include "md_internal.cuh"
 
 extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint_every, double *grad_q,
@@ -21,9 +21,9 @@ extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint
   if (!c) return set_err(nullptr, MD_EINVAL, "md_grad: NULL context");
   if (observable != MD_OBS_KINETIC && observable != MD_OBS_MAGNETIZATION)
     return set_err(c, MD_EINVAL, "md_grad: unknown observable %d", observable);
-  if (c->model == MD_GRAV3D || c->model == MD_SHEET1D)
-    return set_err(c, MD_EINVAL, "md_grad: available for the HMF, Ring and 2D models");
-  if (observable == MD_OBS_MAGNETIZATION && c->model == MD_GRAV2D)
+  if (c->model == MD_SHEET1D && !(c->eps > 0.0))
+    return set_err(c, MD_EINVAL, "md_grad: the eps = 0 sheet force is piecewise constant; derivatives need eps > 0");
+  if (observable == MD_OBS_MAGNETIZATION && c->model != MD_HMF && c->model != MD_RING)
     return set_err(c, MD_EINVAL, "md_grad: the magnetization is defined for HMF and Ring only");
   if (nsteps < 0 || checkpoint_every < 1) return set_err(c, MD_EINVAL, "md_grad: need nsteps >= 0, checkpoint_every >= 1");
   if (!grad_q || !grad_p) return set_err(c, MD_EINVAL, "md_grad: NULL gradient output");

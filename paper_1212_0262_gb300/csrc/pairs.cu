@@ -27,6 +27,10 @@
 //          df_i/deps = (3/(32N)) sum S dd^(-5/2)          (C = cos d)
 //   2D:    (Jv)_i = -(2/N) sum [w/s - 2 r (r.w)/s^2],  w = v_i - v_j, s = |r|^2 + eps,
 //          df_i/deps = (2/N) sum r / s^2
+//   3D:    (Jv)_i = -(1/N) sum [w s^(-3/2) - 3 r (r.w) s^(-5/2)],
+//          df_i/deps = (3/(2N)) sum r s^(-5/2)
+//   sheets (eps > 0, f_i = -(1/N) sum d s^(-1/2), s = d^2 + eps):
+//          (Jv)_i = -(eps/N) sum s^(-3/2) w,  df_i/deps = (1/(2N)) sum d s^(-3/2)
 // MIXED: the mirror holds FP32 values, two j's are processed per packed
 // f32x2 instruction (FFMA2/FMUL2/FADD2), 1/sqrt and 1/x use the SFU
 // (rsqrt.approx / rcp.approx, as the paper uses rsqrt), per-tile sums are FP32
@@ -165,8 +169,26 @@ __global__ void mirror_kernel(const double *__restrict__ q, const double *__rest
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Npad; i += G) {
     if constexpr (MODEL == MD_SHEET1D) {
       const double x = i < N ? q[i] : sheet_pad(eps, MIXED);
-      write_record1<MIXED>(m0, i, x);
-      if (i >= N && m1) write_record1<MIXED>(m1, i, x);
+      if constexpr (ADJ) {
+        const double v = i < N ? lp[i] : 0.0;
+        write_record1_adj<MIXED>(m0, i, x, v);
+        if (i >= N && m1) write_record1_adj<MIXED>(m1, i, x, v);
+      } else {
+        write_record1<MIXED>(m0, i, x);
+        if (i >= N && m1) write_record1<MIXED>(m1, i, x);
+      }
+      continue;
+    }
+    if constexpr (MODEL == MD_GRAV3D && ADJ) {
+      // pads far away (their terms vanish in the pair kernels), lambda_p = 0
+      double x[3], v[3];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        x[d] = i < N ? q[d * N + i] : (MIXED ? 3.0e19 : 1.0e150);
+        v[d] = i < N ? lp[d * N + i] : 0.0;
+      }
+      write_record3_adj<MIXED>(m0, i, x, v);
+      if (i >= N && m1) write_record3_adj<MIXED>(m1, i, x, v);
       continue;
     }
     if constexpr (MODEL == MD_GRAV3D) {
@@ -225,8 +247,8 @@ int ensure_mirrors(md_ctx *c, bool adj) {
   const int64_t Np = padded(c->N);
   // the FP64 record bounds the FP32 one
   const size_t per = c->model == MD_RING      ? (adj ? 48 : 64)  // Ring forward: tensor-core record
-                     : c->model == MD_GRAV3D  ? 32
-                     : c->model == MD_SHEET1D ? 8
+                     : c->model == MD_GRAV3D  ? (adj ? 64 : 32)
+                     : c->model == MD_SHEET1D ? (adj ? 16 : 8)
                                               : (adj ? 32 : 16);
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
@@ -329,13 +351,13 @@ int refresh(md_ctx *c, const double *lp) {
     else if (mixed) mirror_kernel<MD_RING, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_RING, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   } else if (c->model == MD_GRAV3D) {
-    if (mixed) mirror_kernel<MD_GRAV3D, true, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
-    else mirror_kernel<MD_GRAV3D, false, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    if (mixed) mirror_kernel<MD_GRAV3D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else mirror_kernel<MD_GRAV3D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   } else if (c->model == MD_SHEET1D) {
     if (mixed)
-      mirror_kernel<MD_SHEET1D, true, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
+      mirror_kernel<MD_SHEET1D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
     else
-      mirror_kernel<MD_SHEET1D, false, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
+      mirror_kernel<MD_SHEET1D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
   } else {
     if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
@@ -405,6 +427,25 @@ int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
   return mixed ? dispatch_mode<MD_GRAV2D, true>(c, mode, a) : dispatch_mode<MD_GRAV2D, false>(c, mode, a);
 }
 
+template <int MODE>
+int reverse_pair_launch(md_ctx *c, PairArgs a) {
+  const bool mixed = c->prec == MD_MIXED;
+  switch (c->model) {
+  case MD_RING:
+    if (mixed) return launch_streamk<RingMixedAdj<4, 256, MODE>, MD_RING, true, MODE>(c, a);
+    return launch_streamk<RingF64Adj<2, 128, MODE>, MD_RING, false, MODE>(c, a);
+  case MD_GRAV3D:
+    if (mixed) return launch_streamk<Grav3DMixedAdj<2, 256, MODE>, MD_GRAV3D, true, MODE>(c, a);
+    return launch_streamk<Grav3DF64Adj<2, 128, MODE>, MD_GRAV3D, false, MODE>(c, a);
+  case MD_SHEET1D:
+    if (mixed) return launch_streamk<SheetMixedAdj<4, 256, MODE>, MD_SHEET1D, true, MODE>(c, a);
+    return launch_streamk<SheetF64Adj<2, 128, MODE>, MD_SHEET1D, false, MODE>(c, a);
+  default:
+    if (mixed) return launch_streamk<GravMixedAdj<2, 256, MODE>, MD_GRAV2D, true, MODE>(c, a);
+    return launch_streamk<GravF64Adj<2, 128, MODE>, MD_GRAV2D, false, MODE>(c, a);
+  }
+}
+
 int pair_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, double *lq, double *lp,
                        double *epsacc) {
   PairArgs a{};
@@ -414,13 +455,7 @@ int pair_adjoint_stage(md_ctx *c, double b_adj, double b_undo, double drift, dou
   a.lq = lq;
   a.lp = lp;
   a.epsacc = epsacc;
-  constexpr int M = STAGE_ADJOINT;
-  if (c->model == MD_RING) {
-    if (c->prec == MD_MIXED) return launch_streamk<RingMixedAdj<4, 256, M>, MD_RING, true, M>(c, a);
-    return launch_streamk<RingF64Adj<2, 128, M>, MD_RING, false, M>(c, a);
-  }
-  if (c->prec == MD_MIXED) return launch_streamk<GravMixedAdj<2, 256, M>, MD_GRAV2D, true, M>(c, a);
-  return launch_streamk<GravF64Adj<2, 128, M>, MD_GRAV2D, false, M>(c, a);
+  return reverse_pair_launch<STAGE_ADJOINT>(c, a);
 }
 
 int pair_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double *dp) {
@@ -429,13 +464,7 @@ int pair_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double 
   a.drift = drift;
   a.lq = dq;
   a.lp = dp;
-  constexpr int M = STAGE_TANGENT;
-  if (c->model == MD_RING) {
-    if (c->prec == MD_MIXED) return launch_streamk<RingMixedAdj<4, 256, M>, MD_RING, true, M>(c, a);
-    return launch_streamk<RingF64Adj<2, 128, M>, MD_RING, false, M>(c, a);
-  }
-  if (c->prec == MD_MIXED) return launch_streamk<GravMixedAdj<2, 256, M>, MD_GRAV2D, true, M>(c, a);
-  return launch_streamk<GravF64Adj<2, 128, M>, MD_GRAV2D, false, M>(c, a);
+  return reverse_pair_launch<STAGE_TANGENT>(c, a);
 }
 
 int kick_drift_cached(md_ctx *c, double kick, double drift) {

@@ -15,8 +15,8 @@ constexpr int kPadMultiple = 1024;  // mirror padding: multiple of every TI and 
 template <int MODEL, bool MIXED, bool ADJ>
 struct RecordBytes {
   static constexpr int value = MODEL == MD_RING      ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 48 : 32))
-                               : MODEL == MD_GRAV3D  ? (MIXED ? 16 : 32)
-                               : MODEL == MD_SHEET1D ? (MIXED ? 4 : 8)
+                               : MODEL == MD_GRAV3D  ? (MIXED ? (ADJ ? 24 : 16) : (ADJ ? 64 : 32))
+                               : MODEL == MD_SHEET1D ? (MIXED ? (ADJ ? 8 : 4) : (ADJ ? 16 : 8))
                                                      : (MIXED ? (ADJ ? 16 : 8) : (ADJ ? 32 : 16));
 };
 
@@ -59,6 +59,41 @@ __device__ __forceinline__ void write_record1(void *mirror, int64_t i, double x)
 }
 __device__ __forceinline__ double sheet_pad(double eps, bool mixed) {
   return eps > 0.0 ? (mixed ? 3.0e19 : 1.0e150) : __longlong_as_double(0x7FF8000000000000LL);
+}
+
+// Adjoint records (positions and lambda_p): 3D FP32 per particle pair the floats
+// (-x, -x', -y, -y'), (-z, -z', -vx, -vx'), (-vy, -vy', -vz, -vz'); FP64 per particle
+// (x, y, z, vx, vy, vz, 0, 0).  Sheets FP32 per pair (-x, -x', -v, -v'); FP64 (x, v).
+template <bool MIXED>
+__device__ __forceinline__ void write_record3_adj(void *mirror, int64_t i, const double *x, const double *v) {
+  if constexpr (MIXED) {
+    float *m = (float *)mirror + (i >> 1) * 12 + (i & 1);
+    m[0] = -(float)x[0];
+    m[2] = -(float)x[1];
+    m[4] = -(float)x[2];
+    m[6] = -(float)v[0];
+    m[8] = -(float)v[1];
+    m[10] = -(float)v[2];
+  } else {
+    double *m = (double *)mirror + i * 8;
+    for (int d = 0; d < 3; d++) {
+      m[d] = x[d];
+      m[3 + d] = v[d];
+    }
+    m[6] = m[7] = 0.0;
+  }
+}
+template <bool MIXED>
+__device__ __forceinline__ void write_record1_adj(void *mirror, int64_t i, double x, double v) {
+  if constexpr (MIXED) {
+    float *m = (float *)mirror + (i >> 1) * 4 + (i & 1);
+    m[0] = -(float)x;
+    m[2] = -(float)v;
+  } else {
+    double *m = (double *)mirror + i * 2;
+    m[0] = x;
+    m[1] = v;
+  }
 }
 
 template <bool MIXED>
@@ -1128,6 +1163,246 @@ struct GravMixedAdj {
   }
 };
 
+// ------------------------------------------------------------ adjoint 3D FP32
+// accumulators: 0-2 = force sums of r s^(-3/2); 3-5 = J w sums of w s^(-3/2) - 3 r (r.w) s^(-5/2)
+// (w = lambda_i - lambda_j); 6-8 = d/deps sums of r s^(-5/2)
+template <int R_, int TJ_, int MODE>
+struct Grav3DMixedAdj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 9, JB = RecordBytes<MD_GRAV3D, true, true>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    float2 x[R], y[R], z[R], vx[R], vy[R], vz[R], acc[R][NACC];
+    CompSum cs[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + row_of(r);
+      const float *m = (const float *)mirror + (i >> 1) * 12 + (i & 1);
+      st.x[r] = f2(-m[0]);
+      st.y[r] = f2(-m[2]);
+      st.z[r] = f2(-m[4]);
+      st.vx[r] = f2(-m[6]);
+      st.vy[r] = f2(-m[8]);
+      st.vz[r] = f2(-m[10]);
+#pragma unroll
+      for (int d = 0; d < NACC; d++) {
+        st.acc[r][d] = f2(0.f);
+        st.cs[r][d] = CompSum{0.f, 0.f};
+      }
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd), m3 = f2(-3.f);
+#pragma unroll 1
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 A = sm[3 * k], B = sm[3 * k + 1], C = sm[3 * k + 2];
+      const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w), nz = make_float2(B.x, B.y);
+      const float2 nvx = make_float2(B.z, B.w), nvy = make_float2(C.x, C.y), nvz = make_float2(C.z, C.w);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const float2 dx = __fadd2_rn(st.x[r], nx), dy = __fadd2_rn(st.y[r], ny), dz = __fadd2_rn(st.z[r], nz);
+        const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+        const float2 y = make_float2(mufu_rsqrt(s.x), mufu_rsqrt(s.y));
+        const float2 y2 = __fmul2_rn(y, y);
+        const float2 w3 = __fmul2_rn(y2, y), w5 = __fmul2_rn(w3, y2);
+        const float2 wx = __fadd2_rn(st.vx[r], nvx), wy = __fadd2_rn(st.vy[r], nvy), wz = __fadd2_rn(st.vz[r], nvz);
+        const float2 rw = __ffma2_rn(dx, wx, __ffma2_rn(dy, wy, __fmul2_rn(dz, wz)));
+        const float2 t = __fmul2_rn(rw, __fmul2_rn(w5, m3));
+        float2 *ac = st.acc[r];
+        ac[0] = __ffma2_rn(dx, w3, ac[0]);
+        ac[1] = __ffma2_rn(dy, w3, ac[1]);
+        ac[2] = __ffma2_rn(dz, w3, ac[2]);
+        ac[3] = __ffma2_rn(t, dx, __ffma2_rn(wx, w3, ac[3]));
+        ac[4] = __ffma2_rn(t, dy, __ffma2_rn(wy, w3, ac[4]));
+        ac[5] = __ffma2_rn(t, dz, __ffma2_rn(wz, w3, ac[5]));
+        ac[6] = __ffma2_rn(dx, w5, ac[6]);
+        ac[7] = __ffma2_rn(dy, w5, ac[7]);
+        ac[8] = __ffma2_rn(dz, w5, ac[8]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+      for (int d = 0; d < NACC; d++) {
+        csum_add2(st.cs[r][d], st.acc[r][d]);
+        st.acc[r][d] = f2(0.f);
+      }
+  }
+};
+
+// ------------------------------------------------------------ adjoint 3D FP64
+template <int R_, int TJ_, int MODE>
+struct Grav3DF64Adj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 9, JB = RecordBytes<MD_GRAV3D, false, true>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    double x[R], y[R], z[R], vx[R], vy[R], vz[R];
+    double accd[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 8;
+      st.x[r] = m[0];
+      st.y[r] = m[1];
+      st.z[r] = m[2];
+      st.vx[r] = m[3];
+      st.vy[r] = m[4];
+      st.vz[r] = m[5];
+#pragma unroll
+      for (int d = 0; d < NACC; d++) st.accd[r][d] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double4 *sm = (const double4 *)smb;
+#pragma unroll 1
+    for (int k = 0; k < TJ; k++) {
+      const double4 P = sm[2 * k], V = sm[2 * k + 1];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const double dx = st.x[r] - P.x, dy = st.y[r] - P.y, dz = st.z[r] - P.z;
+        const double y = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, a.epsd))));
+        const double y2 = y * y, w3 = y2 * y, w5 = w3 * y2;
+        const double wx = st.vx[r] - P.w, wy = st.vy[r] - V.x, wz = st.vz[r] - V.y;
+        const double t = -3.0 * fma(dx, wx, fma(dy, wy, dz * wz)) * w5;
+        double *ac = st.accd[r];
+        ac[0] = fma(dx, w3, ac[0]);
+        ac[1] = fma(dy, w3, ac[1]);
+        ac[2] = fma(dz, w3, ac[2]);
+        ac[3] = fma(t, dx, fma(wx, w3, ac[3]));
+        ac[4] = fma(t, dy, fma(wy, w3, ac[4]));
+        ac[5] = fma(t, dz, fma(wz, w3, ac[5]));
+        ac[6] = fma(dx, w5, ac[6]);
+        ac[7] = fma(dy, w5, ac[7]);
+        ac[8] = fma(dz, w5, ac[8]);
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------ adjoint sheets FP32 (eps > 0)
+// accumulators: 0 = force sum of d s^(-1/2); 1 = J w sum of s^(-3/2) w (times eps in the
+// epilogue); 2 = d/deps sum of d s^(-3/2); s = d^2 + eps
+template <int R_, int TJ_, int MODE>
+struct SheetMixedAdj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_SHEET1D, true, true>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    float2 x[R], v[R], acc[R][NACC];
+    CompSum cs[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = csum_total(st.cs[r][d]);
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int64_t i = i0 + row_of(r);
+      const float *m = (const float *)mirror + (i >> 1) * 4 + (i & 1);
+      st.x[r] = f2(-m[0]);
+      st.v[r] = f2(-m[2]);
+#pragma unroll
+      for (int d = 0; d < NACC; d++) {
+        st.acc[r][d] = f2(0.f);
+        st.cs[r][d] = CompSum{0.f, 0.f};
+      }
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+#pragma unroll 2
+    for (int k = 0; k < TJ / 2; k++) {
+      const float4 A = sm[k];
+      const float2 nx = make_float2(A.x, A.y), nv = make_float2(A.z, A.w);
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const float2 d = __fadd2_rn(st.x[r], nx);
+        const float2 s = __ffma2_rn(d, d, e2);
+        const float2 y = make_float2(mufu_rsqrt(s.x), mufu_rsqrt(s.y));
+        const float2 w3 = __fmul2_rn(__fmul2_rn(y, y), y);
+        st.acc[r][0] = __ffma2_rn(d, y, st.acc[r][0]);
+        st.acc[r][1] = __ffma2_rn(w3, __fadd2_rn(st.v[r], nv), st.acc[r][1]);
+        st.acc[r][2] = __ffma2_rn(d, w3, st.acc[r][2]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+      for (int d = 0; d < NACC; d++) {
+        csum_add2(st.cs[r][d], st.acc[r][d]);
+        st.acc[r][d] = f2(0.f);
+      }
+  }
+};
+
+// ------------------------------------------------------------ adjoint sheets FP64 (eps > 0)
+template <int R_, int TJ_, int MODE>
+struct SheetF64Adj {
+  static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_SHEET1D, false, true>::value;
+  static constexpr bool MASK = false;
+  static constexpr int NR = R;
+  static constexpr int FMT = 0;
+  __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
+  struct State {
+    double x[R], v[R];
+    double accd[R][NACC];
+  };
+  __device__ static void total(const State &st, int r, double *out) {
+#pragma unroll
+    for (int d = 0; d < NACC; d++) out[d] = st.accd[r][d];
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const double *m = (const double *)mirror + (i0 + row_of(r)) * 2;
+      st.x[r] = m[0];
+      st.v[r] = m[1];
+      st.accd[r][0] = st.accd[r][1] = st.accd[r][2] = 0.0;
+    }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
+    const double2 *sm = (const double2 *)smb;
+#pragma unroll 2
+    for (int k = 0; k < TJ; k++) {
+      const double2 o = sm[k];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const double d = st.x[r] - o.x;
+        const double y = rsqrt_nr(fma(d, d, a.epsd));
+        const double w3 = y * y * y;
+        st.accd[r][0] = fma(d, y, st.accd[r][0]);
+        st.accd[r][1] = fma(w3, st.v[r] - o.y, st.accd[r][1]);
+        st.accd[r][2] = fma(d, w3, st.accd[r][2]);
+      }
+    }
+  }
+};
+
 // ------------------------------------------------------------ adjoint Ring FP64
 template <int R_, int TJ_, int MODE>
 struct RingF64Adj {
@@ -1508,24 +1783,52 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
 //   lambda_q += b_adj J(q_s) lambda_p ;  epsacc += b_adj <lambda_p, df/deps(q_s)>
 //   p -= b_undo f(q_s)                          (undo the kick)
 //   lambda_p += d lambda_q ;  q -= d p          (adjoint and undo of the drift)
-template <int MODEL, bool MIXED>
-__device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, const double *acc) {
-  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
-  if (i >= a.N) return;
+// Force, J v and df/deps of particle i from the reverse-stage accumulators
+// (layout of the *Adj policies: [force sums][J w sums][d/deps sums], D each).
+template <int MODEL>
+__device__ __forceinline__ void adjoint_terms(const PairArgs &a, const double *acc, double *f, double *jv, double *de) {
+  constexpr int D = dim_of<MODEL>();
   const double n = (double)a.N;
-  double f[D], jv[D], de[D];
-  if (MODEL == MD_RING) {
-    f[0] = -acc[0] / (8.0 * n);
-    jv[0] = -acc[1] / (8.0 * n);
-    de[0] = 3.0 * acc[2] / (32.0 * n);
-  } else {
 #pragma unroll
-    for (int d = 0; d < D; d++) {
+  for (int d = 0; d < D; d++) {
+    if (MODEL == MD_RING) {
+      f[d] = -acc[0] / (8.0 * n);
+      jv[d] = -acc[1] / (8.0 * n);
+      de[d] = 3.0 * acc[2] / (32.0 * n);
+    } else if (MODEL == MD_GRAV2D) {
       f[d] = -2.0 * acc[d] / n;
       jv[d] = -2.0 * acc[2 + d] / n;
       de[d] = 2.0 * acc[4 + d] / n;
+    } else if (MODEL == MD_GRAV3D) {
+      f[d] = -acc[d] / n;
+      jv[d] = -acc[3 + d] / n;
+      de[d] = 1.5 * acc[6 + d] / n;
+    } else {  // sheets (eps > 0)
+      f[d] = -acc[0] / n;
+      jv[d] = -a.epsd * acc[1] / n;
+      de[d] = 0.5 * acc[2] / n;
     }
   }
+}
+
+// Adjoint record (positions x, lambda_p v) of particle i, per model.
+template <int MODEL, bool MIXED>
+__device__ __forceinline__ void write_adjoint_record(void *mirror, int64_t i, const double *x, const double *v) {
+  constexpr int D = dim_of<MODEL>();
+  if constexpr (MODEL == MD_GRAV3D)
+    write_record3_adj<MIXED>(mirror, i, x, v);
+  else if constexpr (MODEL == MD_SHEET1D)
+    write_record1_adj<MIXED>(mirror, i, x[0], v[0]);
+  else
+    write_record<MODEL, MIXED, true>(mirror, i, x[0], x[D - 1], v[0], v[D - 1]);
+}
+
+template <int MODEL, bool MIXED>
+__device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, const double *acc) {
+  constexpr int D = dim_of<MODEL>();
+  if (i >= a.N) return;
+  double f[D], jv[D], de[D];
+  adjoint_terms<MODEL>(a, acc, f, jv, de);
   double lq[D], lp[D], x[D], e = 0.0;
 #pragma unroll
   for (int d = 0; d < D; d++) {
@@ -1544,7 +1847,7 @@ __device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, con
     a.lq[d * a.N + i] = lq[d];
   }
   a.epsacc[i] = fma(a.kick, e, a.epsacc[i]);
-  if (a.drift != 0.0) write_record<MODEL, MIXED, true>(a.mirror_out, i, x[0], x[D - 1], lp[0], lp[D - 1]);
+  if (a.drift != 0.0) write_adjoint_record<MODEL, MIXED>(a.mirror_out, i, x, lp);
 }
 
 // Tangent stages (forward-mode derivative of the stage map), with a.lq = dq and
@@ -1552,16 +1855,14 @@ __device__ __forceinline__ void finish_adjoint(const PairArgs &a, int64_t i, con
 // a new adjoint-format record (q, dq) for the next stage.
 template <int MODEL, bool MIXED>
 __device__ __forceinline__ void finish_tangent(const PairArgs &a, int64_t i, const double *acc) {
-  constexpr int D = MODEL == MD_GRAV2D ? 2 : 1;
+  constexpr int D = dim_of<MODEL>();
   if (i >= a.N) return;
-  const double n = (double)a.N;
-  double x[D], v[D];
+  double f[D], jv[D], de[D], x[D], v[D];
+  adjoint_terms<MODEL>(a, acc, f, jv, de);
 #pragma unroll
   for (int d = 0; d < D; d++) {
-    const double f = MODEL == MD_RING ? -acc[0] / (8.0 * n) : -2.0 * acc[d] / n;
-    const double jv = MODEL == MD_RING ? -acc[1] / (8.0 * n) : -2.0 * acc[2 + d] / n;
-    const double pp = fma(a.kick, f, a.p[d * a.N + i]);
-    const double dpp = fma(a.kick, jv, a.lp[d * a.N + i]);
+    const double pp = fma(a.kick, f[d], a.p[d * a.N + i]);
+    const double dpp = fma(a.kick, jv[d], a.lp[d * a.N + i]);
     a.p[d * a.N + i] = pp;
     a.lp[d * a.N + i] = dpp;
     x[d] = a.q[d * a.N + i];
@@ -1573,7 +1874,7 @@ __device__ __forceinline__ void finish_tangent(const PairArgs &a, int64_t i, con
       a.lq[d * a.N + i] = v[d];
     }
   }
-  if (a.drift != 0.0) write_record<MODEL, MIXED, true>(a.mirror_out, i, x[0], x[D - 1], v[0], v[D - 1]);
+  if (a.drift != 0.0) write_adjoint_record<MODEL, MIXED>(a.mirror_out, i, x, v);
 }
 
 template <class Pol, int MODEL, bool MIXED, int MODE>

@@ -1,14 +1,14 @@
 // md_tangent_step: the state and a tangent vector advanced together by the
 // linearisation of md_step's map (forward-mode derivative), the building block
 // of largest-Lyapunov-exponent estimates.  Each stage is one fused kernel: the
-// force and J(q) dq from a single pair pass (Ring/2D) or from four mean-field
+// force and J(q) dq from a single pair pass (pair models) or from four mean-field
 // sums (HMF), then the kick and drift of both.
 #include "md_internal.cuh"
 
 extern "C" int md_tangent_step(md_ctx *c, int64_t nsteps, double *dq, double *dp) {
   if (!c) return set_err(nullptr, MD_EINVAL, "md_tangent_step: NULL context");
-  if (c->model == MD_GRAV3D || c->model == MD_SHEET1D)
-    return set_err(c, MD_EINVAL, "md_tangent_step: available for the HMF, Ring and 2D models");
+  if (c->model == MD_SHEET1D && !(c->eps > 0.0))
+    return set_err(c, MD_EINVAL, "md_tangent_step: the eps = 0 sheet force is piecewise constant; derivatives need eps > 0");
   if (nsteps < 0 || !dq || !dp) return set_err(c, MD_EINVAL, "md_tangent_step: need nsteps >= 0 and arrays");
   if (nsteps == 0) return MD_OK;
   const int64_t n = (int64_t)c->dim * c->N;

@@ -15,8 +15,8 @@ from paper_1212_0262_gb300.autograd import rollout
 
 pytestmark = pytest.mark.gpu
 
-EPS = {0: 0.0, 1: 0.01, 2: 1e-3}
-DT = {0: 0.1, 1: 0.05, 2: 0.01}
+EPS = {0: 0.0, 1: 0.01, 2: 1e-3, 3: 1e-2, 4: 0.05}
+DT = {0: 0.1, 1: 0.05, 2: 0.01, 3: 0.01, 4: 0.01}
 
 
 def _sys(model, N, prec="fp64", seed=3):
@@ -30,7 +30,7 @@ def _rel(a, b):
     return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
 
 
-@pytest.mark.parametrize("model,obs", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0)])
+@pytest.mark.parametrize("model,obs", [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (3, 0), (4, 0)])
 @pytest.mark.parametrize("N,nsteps,K", [(64, 20, 7), (257, 9, 3)])
 def test_fp64_gradient_matches_oracle_adjoint(model, obs, N, nsteps, K):
     s, q, p = _sys(model, N)
@@ -43,7 +43,7 @@ def test_fp64_gradient_matches_oracle_adjoint(model, obs, N, nsteps, K):
         assert abs(ge - oe) <= 1e-10 * max(abs(oe), 1e-300)
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 def test_state_is_unchanged_and_checkpoint_interval_does_not_matter(model):
     s, q, p = _sys(model, 300)
     g1 = s.grad(12, 0, 1)
@@ -57,7 +57,7 @@ def test_state_is_unchanged_and_checkpoint_interval_does_not_matter(model):
     assert abs(s.energy()[0] - g1[0]) <= 1e-13 * abs(g1[0])
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 def test_zero_steps_gives_the_terminal_adjoint(model):
     s, q, p = _sys(model, 100)
     val, gq, gp, ge = s.grad(0, 0, 5)
@@ -76,7 +76,7 @@ def _fd_observable(s, q, p, eps, nsteps, obs):
 
 
 @pytest.mark.parametrize("model,N,nsteps,obs", [(2, 1024, 100, 0), (1, 1024, 40, 0), (1, 512, 40, 1),
-                                                (0, 4096, 40, 1)])
+                                                (0, 4096, 40, 1), (3, 1024, 60, 0), (4, 1024, 60, 0)])
 def test_gradient_matches_central_differences(model, N, nsteps, obs):
     """Directional derivatives along seeded random directions, and d/d eps."""
     s, q, p = _sys(model, N, seed=11)
@@ -99,7 +99,7 @@ def test_gradient_matches_central_differences(model, N, nsteps, obs):
         assert abs(fde - ge) <= 1e-6 * max(abs(ge), abs(fde)), (fde, ge)
 
 
-@pytest.mark.parametrize("model", [1, 2])
+@pytest.mark.parametrize("model", [1, 2, 3, 4])
 def test_mixed_gradient_close_to_fp64(model):
     s, q, p = _sys(model, 2048)
     ref = s.grad(20, 0, 5)
@@ -121,3 +121,30 @@ def test_autograd_function_backward():
     np.testing.assert_allclose(q0.grad.numpy(), 3.0 * gq, rtol=0, atol=0)
     np.testing.assert_allclose(p0.grad.numpy(), 3.0 * gp, rtol=0, atol=0)
     assert eps.grad.item() == 3.0 * ge
+
+
+@pytest.mark.parametrize("N", [1, 3, 1000, 1025, 2049])
+@pytest.mark.parametrize("model", [3, 4])
+def test_fp64_gradient_ragged_sizes(model, N):
+    """The 3D and sheet reverse-stage kernels across one to several i-tiles with
+    ragged tails (padding records far away, lambda_p = 0)."""
+    s, q, p = _sys(model, N, seed=5)
+    val, gq, gp, ge = s.grad(5, 0, 2)
+    ov, oq, op, oe = ora.grad(model, q, p, EPS[model], DT[model], 5, 0)
+    assert _rel(gq, oq) <= 1e-10 and _rel(gp, op) <= 1e-10
+    assert abs(ge - oe) <= 1e-10 * max(abs(oe), 1e-300) + 1e-300
+
+
+def test_reverse_stages_refuse_what_has_no_derivative():
+    """Sheets at eps = 0 (a piecewise-constant force) and the magnetization of the
+    models without an angle: MD_EINVAL with a message, the context still usable."""
+    s = System(4, 100, 0.0, 0.01, 1)
+    with pytest.raises(RuntimeError, match="eps > 0"):
+        s.grad(3, 0, 2)
+    with pytest.raises(RuntimeError, match="eps > 0"):
+        s.tangent_step(1, np.zeros(100), np.zeros(100))
+    s.step(1)
+    for model in (2, 3, 4):
+        t, _, _ = _sys(model, 64)
+        with pytest.raises(RuntimeError, match="HMF and Ring"):
+            t.grad(3, 1, 2)

@@ -8,11 +8,11 @@ from paper_1212_0262_gb300 import System, inputs
 
 pytestmark = pytest.mark.gpu
 
-EPS = {0: 0.0, 1: 0.01, 2: 1e-3}
-DT = {0: 0.1, 1: 0.05, 2: 0.01}
+EPS = {0: 0.0, 1: 0.01, 2: 1e-3, 3: 1e-2, 4: 0.05}
+DT = {0: 0.1, 1: 0.05, 2: 0.01, 3: 0.01, 4: 0.01}
 
 
-@pytest.mark.parametrize("model", [0, 1, 2])
+@pytest.mark.parametrize("model", [0, 1, 2, 3, 4])
 def test_tangent_matches_oracle_central_differences(model):
     N, nsteps = 200, 12
     q0, p0 = inputs.default_state(model, N, 13)
@@ -33,7 +33,7 @@ def test_tangent_matches_oracle_central_differences(model):
     assert np.max(np.abs(dq - fq)) <= 1e-6 * scale and np.max(np.abs(dp - fp)) <= 1e-6 * scale
 
 
-@pytest.mark.parametrize("model", [1, 2])
+@pytest.mark.parametrize("model", [1, 2, 3, 4])
 def test_mixed_tangent_close_to_fp64(model):
     N = 1024
     q0, p0 = inputs.default_state(model, N, 5)
