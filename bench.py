@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--workload", default="hmf", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="processes of the oracle legs (0 = every core of this process's affinity set)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
@@ -194,13 +196,13 @@ def device_uuid(dev):
 
 # ------------------------------------------------------------ oracle legs -
 
-def oracle_steps(w, n: int, steps: int, warmup: int = 0):
-    """Run the FP64 CPU oracle on a sample of the workload and return
-    (units processed in the timed steps, seconds, description).
-    HMF: the first n particles' recipe (an n-particle water-bag drawn from the
-    workload's seed), `steps` integrator steps in one call (3 force evaluations
-    per step plus one at the start).  Ring/2D: per step, 3 force evaluations of
-    n sampled rows against all N partners (direct pair sums)."""
+def _oracle_part(w, part: int, parts: int, n: int, steps: int, warmup: int, barrier=None, out=None):
+    """One share of the oracle leg, run in this process or in a spawned one.
+    HMF: an n-particle water-bag drawn from the workload's seed (every share runs
+    its own replica), `steps` integrator steps in one call.  Ring/2D: every
+    parts-th of n sampled rows, 3 force evaluations per step against all N
+    partners (direct pair sums).  Timed on CLOCK_MONOTONIC from a barrier shared
+    by all shares; returns (or puts) (units, t_start, t_end)."""
     import numpy as np
 
     import oracle as ora
@@ -211,31 +213,112 @@ def oracle_steps(w, n: int, steps: int, warmup: int = 0):
         q, p = inputs.waterbag(n, w["seed"])
         if warmup:
             q, p = ora.step(0, q, p, 0.0, w["dt"], warmup)
-        t0 = time.perf_counter()
-        ora.step(0, q, p, 0.0, w["dt"], steps)
-        el = time.perf_counter() - t0
-        return n * steps, el, f"{n}-particle HMF water-bag (seed {w['seed']}), {steps} oracle steps in one call"
-    q, _ = inputs.default_state(model, N, w["seed"])
-    rows = np.linspace(0, N - 1, n).astype(np.int64)
-    for _ in range(3 * warmup):
-        ora.force_rows(model, q, rows, w["eps"])
-    t0 = time.perf_counter()
-    for _ in range(3 * steps):
-        ora.force_rows(model, q, rows, w["eps"])
-    el = time.perf_counter() - t0
-    return 3 * n * N * steps, el, (f"{n} of {N} rows x {N} partners, 3 force evaluations per step, "
-                                   f"{steps} steps (direct pair sums)")
+        units = n * steps
+
+        def work():
+            ora.step(0, q, p, 0.0, w["dt"], steps)
+    else:
+        q, _ = inputs.default_state(model, N, w["seed"])
+        rows = np.linspace(0, N - 1, n).astype(np.int64)[part::parts]
+        for _ in range(3 * warmup):
+            ora.force_rows(model, q, rows, w["eps"])
+        units = 3 * len(rows) * N * steps
+
+        def work():
+            for _ in range(3 * steps):
+                ora.force_rows(model, q, rows, w["eps"])
+    if barrier is not None:
+        barrier.wait(timeout=600)
+    t0 = time.monotonic()
+    work()
+    t1 = time.monotonic()
+    if out is None:
+        return units, t0, t1
+    out.put((units, t0, t1))
+    return None
 
 
-def oracle_sample_size(w, seconds: float, steps: int) -> int:
-    """Sample size so that `steps` oracle steps take about `seconds` here."""
+def host_cores() -> int:
+    """Cores this process may run on (its CPU affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_steps(w, n: int, steps: int, warmup: int = 0, cores: int = 1):
+    """Run the FP64 CPU oracle, as it stands, on a sample of the workload over
+    `cores` processes (spawned, so that no CUDA state is inherited) and return
+    (units processed in the timed steps, wall seconds, description)."""
+    model, N = w["model"], w["N"]
+    if cores <= 1:
+        units, t0, t1 = _oracle_part(w, 0, 1, n, steps, warmup)
+        el = t1 - t0
+    else:
+        import multiprocessing as mp
+        import queue
+
+        ctx = mp.get_context("spawn")
+        barrier, out = ctx.Barrier(cores), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_part, args=(w, k, cores, n, steps, warmup, barrier, out), daemon=True)
+                 for k in range(cores)]
+        for pr in procs:
+            pr.start()
+        res = []
+        t_end = time.monotonic() + 900
+        try:
+            while len(res) < cores:
+                try:
+                    res.append(out.get(timeout=1.0))
+                except queue.Empty:
+                    failed = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+                    if failed or time.monotonic() > t_end:
+                        raise RuntimeError(f"oracle leg: worker processes failed (exit codes {failed})")
+        finally:
+            for pr in procs:
+                pr.join(timeout=30)
+                if pr.is_alive():
+                    pr.terminate()
+        units = sum(r[0] for r in res)
+        el = max(r[2] for r in res) - min(r[1] for r in res)
+    if model == 0:
+        who = f"{cores} processes, each " if cores > 1 else ""
+        desc = f"{who}{n}-particle HMF water-bag (seed {w['seed']}), {steps} oracle steps in one call"
+    else:
+        over = f" split over {cores} processes" if cores > 1 else ""
+        desc = (f"{n} of {N} rows{over} x {N} partners, 3 force evaluations per step, "
+                f"{steps} steps (direct pair sums)")
+    return units, el, desc
+
+
+def oracle_sample_size(w, seconds: float, steps: int, cores: int = 1) -> int:
+    """Sample size so that `steps` oracle steps over `cores` processes take about
+    `seconds` here (HMF: the replica size; Ring/2D: the rows over all processes)."""
     model, N = w["model"], w["N"]
     n0 = 20000 if model == 0 else 2
     units, el, _ = oracle_steps(w, n0, 1)
     per_unit = el / units
     per_step_units = seconds / steps / per_unit
-    n = int(per_step_units if model == 0 else per_step_units / (3 * N))
-    return max(1000 if model == 0 else 1, min(N, n))
+    if model == 0:
+        # replicas of at most 2e6 particles each when several processes run
+        return max(1000, min(N, int(per_step_units), 2_000_000 if cores > 1 else N))
+    return max(cores, min(N, int(per_step_units / (3 * N)) * cores))
+
+
+def ensemble_oracle(seconds: float, steps: int, warmup: int, cores: int):
+    """The oracle on one Ring and one 2D member of the ensemble (the first of each
+    half), about `seconds` each: (units, seconds, description)."""
+    models, Ns, eps, dts, seeds = ensemble_spec()
+    units = el = 0.0
+    parts = []
+    for s in (0, len(Ns) // 2):
+        ws_ = dict(model=models[s], N=int(Ns[s]), eps=eps[s], dt=dts[s], seed=seeds[s])
+        n = oracle_sample_size(ws_, seconds, steps + warmup, cores)
+        u_, e_, smp = oracle_steps(ws_, n, steps, warmup, cores)
+        units += u_
+        el += e_
+        parts.append(f"system {s} ({'Ring' if models[s] == 1 else '2D'}, N={Ns[s]}): {smp}")
+    return units, el, "; ".join(parts)
 
 
 def run_reference(args, w):
@@ -243,29 +326,20 @@ def run_reference(args, w):
     if rank != 0:
         return
     K, W = args.steps, args.warmup
+    cores = args.cpu_cores or host_cores()
     if w["model"] == -1:
-        # ensemble: the oracle on one Ring and one 2D member (the first of each half)
-        models, Ns, eps, dts, seeds = ensemble_spec()
-        units = el = 0.0
-        parts = []
-        for s in (0, len(Ns) // 2):
-            ws_ = dict(model=models[s], N=int(Ns[s]), eps=eps[s], dt=dts[s], seed=seeds[s])
-            n = oracle_sample_size(ws_, 30.0, K + W)
-            u_, e_, smp = oracle_steps(ws_, n, K, W)
-            units += u_
-            el += e_
-            parts.append(f"system {s} ({'Ring' if models[s] == 1 else '2D'}, N={Ns[s]}): {smp}")
-        rate, sample = units / el, "; ".join(parts)
+        units, el, sample = ensemble_oracle(30.0, K, W, cores)
+        rate = units / el
     else:
-        n = oracle_sample_size(w, 60.0, K + W)
-        units, el, sample = oracle_steps(w, n, K, W)
+        n = oracle_sample_size(w, 60.0, K + W, cores)
+        units, el, sample = oracle_steps(w, n, K, W, cores)
         rate = units / el
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": w["unit"], "n_gpus": args.gpus,
         "steps": K, "warmup": W, "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"]},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": rate, "unit": w["unit"]},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": rate, "unit": w["unit"]},
         "e2e": {"value": rate, "unit": w["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -451,10 +525,15 @@ def run_ours(args, w):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ksteps = 4 if model == 0 else 1
-        n = oracle_sample_size(w, 12.0, ksteps)
-        units, el, sample = oracle_steps(w, n, ksteps)
-        cpu = {"value": units / el, "unit": w["unit"], "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": el}
+        cores = args.cpu_cores or host_cores()
+        n1 = oracle_sample_size(w, 5.0, ksteps)
+        u1, e1, s1 = oracle_steps(w, n1, ksteps)
+        n = oracle_sample_size(w, 10.0, ksteps, cores)
+        if model == 0:  # capped replicas: more steps instead, about the same seconds
+            ksteps = max(ksteps, int(round(ksteps * oracle_sample_size(w, 10.0, ksteps) / n)))
+        units, el, sample = oracle_steps(w, n, ksteps, 0, cores)
+        cpu = {"value": units / el, "unit": w["unit"], "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": el, "single_core": {"value": u1 / e1, "sample": s1, "seconds": e1}}
 
     if rank == 0:
         line = {
@@ -557,6 +636,43 @@ def run_ensemble(args, w):
     # time-optimal term rate for this mix of Ring and 2D terms
     peak = terms / (w_ring / (nsm * per_clk_ring * mhz * 1e6) + w_2d / (nsm * per_clk_2d * mhz * 1e6))
     achieved = terms / (avg_ms * 1e-3)
+
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        # every system's state from pinned host memory, the steps and every state
+        # back, through the public ensemble API (wall clock)
+        dims = [2 if m == 2 else 1 for m in models]
+        sizes = [d * int(n) for d, n in zip(dims, Ns)]
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        qh = torch.empty(int(offs[-1]), dtype=torch.float64, pin_memory=True).numpy()
+        ph = torch.empty(int(offs[-1]), dtype=torch.float64, pin_memory=True).numpy()
+        for k in range(len(Ns)):
+            qk, pk = ens.get_state(k)
+            qh[offs[k]:offs[k + 1]], ph[offs[k]:offs[k + 1]] = qk, pk
+        ke = max(1, min(K, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(len(Ns)):
+            ens.set_state(k, qh[offs[k]:offs[k + 1]], ph[offs[k]:offs[k + 1]])
+        ens.step(ke)
+        for k in range(len(Ns)):
+            b_ = binding.load()
+            ens._chk(b_.md_batch_get_state(ens._h, k, _c.c_void_p(qh[offs[k]:].ctypes.data),
+                                          _c.c_void_p(ph[offs[k]:].ctypes.data)))
+        el = time.perf_counter() - t0
+        nb = 2 * 8 * float(offs[-1])
+        e2e = {"value": 3 * pairs_per_stage * ke / el, "unit": w["unit"], "h2d_bytes_per_step": nb / ke,
+               "d2h_bytes_per_step": nb / ke, "steps": ke,
+               "note": "md_batch_set_state(host, every system) + md_batch_step + "
+                       "md_batch_get_state(host, every system), wall clock"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = args.cpu_cores or host_cores()
+        units, el, sample = ensemble_oracle(5.0, 1, 0, cores)
+        cpu = {"value": units / el, "unit": w["unit"], "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": el}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
@@ -573,7 +689,7 @@ def run_ensemble(args, w):
                          "pair_terms_per_stage": terms, "avg_stage_ms": avg_ms, "stages": nl},
             "autotune": {"seconds": tune_s, "best_force_launch_ms": tuned_ms},
             "rel_energy_error": {"max": float(de.max()), "median": float(np.median(de))},
-            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     ens.close()

@@ -1,0 +1,55 @@
+"""Host-side pieces of bench.py (no GPU): the oracle legs over several spawned
+processes count the same units as one process, and the reference arm prints one
+JSON line of the contract's shape."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench(ora):
+    import bench as b
+
+    return b
+
+
+def test_split_rows_cover_the_same_work(bench):
+    w = dict(model=2, N=4096, eps=1e-4, dt=0.01, seed=4)
+    u1, e1, d1 = bench.oracle_steps(w, 12, 1)
+    u2, e2, d2 = bench.oracle_steps(w, 12, 1, 0, 3)
+    assert u1 == u2 == 3 * 12 * 4096
+    assert e1 > 0 and e2 > 0
+    assert "split over 3 processes" in d2 and "split" not in d1
+
+
+def test_hmf_replicas_count_every_process(bench):
+    w = dict(model=0, N=10**6, eps=0.0, dt=0.1, seed=2)
+    u, el, d = bench.oracle_steps(w, 5000, 2, 1, 2)
+    assert u == 2 * 5000 * 2 and el > 0 and d.startswith("2 processes")
+
+
+def test_sample_size_scales_rows_with_processes(bench):
+    w = dict(model=1, N=8192, eps=0.01, dt=0.05, seed=3)
+    n = bench.oracle_sample_size(w, 0.2, 1, 4)
+    assert 4 <= n <= 8192 and n % 4 == 0 or n == 8192
+    w0 = dict(model=0, N=5 * 10**7, eps=0.0, dt=0.1, seed=2)
+    assert bench.oracle_sample_size(w0, 60.0, 1, 8) <= 2_000_000
+
+
+def test_reference_arm_prints_one_contract_line():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "ring", "--steps", "1",
+                        "--warmup", "0", "--cpu-cores", "2", "--n", "2048"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "pair-interactions/s" and d["value"] > 0
+    assert d["cpu_baseline"]["cores"] == 2 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
