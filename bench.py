@@ -57,6 +57,7 @@ PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1), 4: (4, 0)}
 # per evaluated pair term, and whether each unordered pair is evaluated once.
 #   one-sided Ring: S and sin(d/2) (2 FMA + 2 MUL), dd (FMA), y^2, S y, acc (FMA) -> 8
 #   tensor-core Ring: S and sin(d/2) on the tensor cores -> 4
+#   tensor-core 2D: dx and dy on the tensor cores -> |r|^2 + eps (2 FMA), fx, fy -> 4
 #   one-sided 2D: dx, dy, |r|^2 + eps (2 FMA), fx, fy -> 6
 #   one-sided 3D: dx, dy, dz, |r|^2 + eps (3 FMA), y^3 (2 MUL), fx, fy, fz -> 11
 #   symmetric: + 1 (Ring) / 2 (2D) / 3 (3D) column accumulations per pair term, plus
@@ -67,6 +68,9 @@ PAIR_KERNELS = {
     (1, 5): ("sym_kernel<RingTC<4,256>>", 5.125, 1, True),
     (2, 2): ("streamk_kernel<GravMixed<8,256>>", 6, 1, False),
     (2, 4): ("sym_kernel<GravMixed<8,256>>", 8.25, 1, True),
+    # tensor-core 2D: dx and dy on the tensor cores; symmetric butterfly adds 7 per 32 terms
+    (2, 3): ("streamk_kernel<GravTC<4,256>>", 4, 1, False),
+    (2, 5): ("sym_kernel<GravTC<4,256>>", 6.22, 1, True),
     (3, 2): ("streamk_kernel<Grav3DMixed<4,256>>", 11, 1, False),
     (3, 4): ("sym_kernel<Grav3DMixed<4,256>>", 14.75, 1, True),
     # sheets at eps = 0: difference, two comparisons turned into +-1, accumulate (no SFU)

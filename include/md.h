@@ -127,6 +127,11 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "rcp_offload"      2D FP32: every 8th pair of j's takes 1/x on the FMA pipe (0 or 8)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32
  *                      tensor-core products (0 off; 1 or 2: 4 or 2 16-row blocks per warp)
+ *   "grav_tc"          2D FP32 forward stages: dx and dy from tensor-core products of an
+ *                      exact three-way TF32 split of each coordinate (0 off; symmetric
+ *                      kernel shape 1: 4 16-row blocks per warp, 128 threads; 2: 2 blocks,
+ *                      256 threads; 3: as 1 with registers for 3 CTAs per SM).  Needs
+ *                      r_mixed 8 and rcp_offload 0.
  *   "symmetric"        forward stages of Ring (FP32: with ring_tc 1) and 2D, FP32 and
  *                      FP64 (r_fp64 2): every unordered pair evaluated once and added to
  *                      both particles (Newton's third law; the paper evaluates both
@@ -148,9 +153,9 @@ int md_set_tuning(md_ctx *ctx, const char *key, int64_t value);
 #define MD_KERNEL_HMF 0          /* HMF mean-field stage (Sec. 3.1) */
 #define MD_KERNEL_PAIRS_FP64 1   /* FP64 all-pairs, every ordered pair */
 #define MD_KERNEL_PAIRS 2        /* FP32 all-pairs on the CUDA cores, every ordered pair */
-#define MD_KERNEL_PAIRS_TC 3     /* FP32 Ring with tensor-core products, every ordered pair */
-#define MD_KERNEL_PAIRS_SYM 4    /* FP32 2D, every unordered pair once */
-#define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 Ring with tensor-core products, every unordered pair once */
+#define MD_KERNEL_PAIRS_TC 3     /* FP32 with tensor-core products (Ring, 2D), every ordered pair */
+#define MD_KERNEL_PAIRS_SYM 4    /* FP32 on the CUDA cores, every unordered pair once */
+#define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 with tensor-core products (Ring, 2D), every unordered pair once */
 #define MD_KERNEL_PAIRS_FP64_SYM 6 /* FP64 all-pairs, every unordered pair once */
 int md_force_kernel(const md_ctx *ctx);
 

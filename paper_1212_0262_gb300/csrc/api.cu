@@ -270,6 +270,7 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
   else if (k == "rcp_offload" && (value == 0 || value == 8)) c->pt.rcp_off = (int)value;
   else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
+  else if (k == "grav_tc" && value >= 0 && value <= 3) c->pt.grav_tc = (int)value;
   else if (k == "symmetric" && (value == 0 || value == 1)) c->pt.symmetric = (int)value;
   else if (k == "rsqrt_offload" && value >= 0 && value <= 2) c->pt.rsqrt_off = (int)value;
   else if (k == "sym_threads" && (value == 128 || value == 256 || value == 768)) c->pt.sym_threads = (int)value;

@@ -22,6 +22,9 @@ struct PairTuning {
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
   int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
   int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
+  int grav_tc = 0;    // 2D FP32: coordinate differences from tensor-core MMAs (exact 3-way TF32 split);
+                      // symmetric kernel: 1: 4 m-blocks per warp, 128 threads; 2: 2 m-blocks, 256 threads;
+                      // 3: as 1 with registers capped for 3 CTAs per SM
   int symmetric = 1;  // forward stages: each unordered pair once (Newton's third law)
   int rsqrt_off = 0;  // symmetric Ring kernel: items of 8 per n-block with the rsqrt on the FMA pipe
   int sym_threads = 128;  // symmetric Ring kernel: 128 threads, 4 m-blocks per warp; 256: 2 m-blocks;
@@ -78,7 +81,7 @@ struct md_ctx {
   int mirror_cur = 0;
   bool mirror_valid = false;
   int mirror_prec = -1;
-  int mirror_fmt = -1;  // record format of the valid mirror (0 interleaved, 1 tensor-core fragments)
+  int mirror_fmt = -1;  // record format of the valid mirror (0 interleaved, 1 Ring / 2 2D tensor-core fragments)
   double *sk_slots = nullptr;
   size_t sk_slots_bytes = 0;
   unsigned *sk_tickets = nullptr;

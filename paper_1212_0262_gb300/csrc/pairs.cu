@@ -241,6 +241,11 @@ __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restr
 // The Ring FP32 forward path uses the tensor-core records and policy.
 bool ring_tc(const md_ctx *c) { return c->model == MD_RING && c->prec == MD_MIXED && c->pt.ring_tc; }
 
+
+// Mirror record format of the forward stages: 0 interleaved, 1 Ring and 2 2D
+// tensor-core fragments.
+int mirror_format(const md_ctx *c) { return ring_tc(c) ? 1 : grav_tc(c) ? 2 : 0; }
+
 int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadMultiple; }
 
 int ensure_mirrors(md_ctx *c, bool adj) {
@@ -249,7 +254,7 @@ int ensure_mirrors(md_ctx *c, bool adj) {
   const size_t per = c->model == MD_RING      ? (adj ? 48 : 64)  // Ring forward: tensor-core record
                      : c->model == MD_GRAV3D  ? (adj ? 64 : 32)
                      : c->model == MD_SHEET1D ? (adj ? 16 : 8)
-                                              : (adj ? 32 : 16);
+                                              : (adj ? 32 : 64);  // 2D forward: tensor-core record
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
     for (int b = 0; b < 2; b++) {
@@ -315,7 +320,8 @@ int dispatch_forward(md_ctx *c, PairArgs a) {
         return launch_streamk<RingTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
       }
       return launch_streamk<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
-    } else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
+    } else if (grav_tc(c)) return launch_streamk<GravTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
     else return launch_streamk<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
   } else {
     if (c->pt.r_fp64 == 4) {
@@ -359,7 +365,9 @@ int refresh(md_ctx *c, const double *lp) {
     else
       mirror_kernel<MD_SHEET1D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
   } else {
-    if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    if (mixed && !ADJ && grav_tc(c))
+      mirror_kernel<MD_GRAV2D, true, false, 2><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    else if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   }
   MD_LAUNCHED(c);
@@ -398,7 +406,7 @@ int mirror_refresh(md_ctx *c) {
   if (rc) return rc;
   c->mirror_valid = true;
   c->mirror_prec = c->prec;
-  c->mirror_fmt = ring_tc(c) ? 1 : 0;
+  c->mirror_fmt = mirror_format(c);
   return MD_OK;
 }
 
@@ -408,7 +416,7 @@ int adjoint_mirror_refresh(md_ctx *c, const double *lp) {
 }
 
 int pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
-  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != (ring_tc(c) ? 1 : 0)) {
+  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != mirror_format(c)) {
     int rc = mirror_refresh(c);
     if (rc) return rc;
   }
@@ -468,7 +476,7 @@ int pair_tangent_stage(md_ctx *c, double kick, double drift, double *dq, double 
 }
 
 int kick_drift_cached(md_ctx *c, double kick, double drift) {
-  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != (ring_tc(c) ? 1 : 0)) {
+  if (!c->mirror_valid || c->mirror_prec != c->prec || c->mirror_fmt != mirror_format(c)) {
     int rc = mirror_refresh(c);
     if (rc) return rc;
   }
@@ -488,7 +496,9 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
     if (mixed) kick_drift_cached_kernel<MD_SHEET1D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_SHEET1D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   } else {
-    if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    if (mixed && grav_tc(c))
+      kick_drift_cached_kernel<MD_GRAV2D, true, 2><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    else if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   }
   MD_LAUNCHED(c);
@@ -500,7 +510,7 @@ extern "C" int md_force_kernel(const md_ctx *c) {
   if (!c) return -1;
   if (c->model == MD_HMF) return MD_KERNEL_HMF;
   if (c->prec != MD_MIXED) return sym_applies(c) ? MD_KERNEL_PAIRS_FP64_SYM : MD_KERNEL_PAIRS_FP64;
-  const bool tc = ring_tc(c) && c->pt.r_mixed != 4;
+  const bool tc = (ring_tc(c) && c->pt.r_mixed != 4) || grav_tc(c);
   if (sym_applies(c)) return tc ? MD_KERNEL_PAIRS_TC_SYM : MD_KERNEL_PAIRS_SYM;
   return tc ? MD_KERNEL_PAIRS_TC : MD_KERNEL_PAIRS;
 }

@@ -104,6 +104,12 @@ __device__ __forceinline__ void write_pad3(void *mirror, int64_t i) {
     write_record3<false>(mirror, i, 1.0e150, 1.0e150, 1.0e150);
 }
 
+// The 2D FP32 forward path takes its coordinate differences from the tensor cores
+// (the default tile shape only: r_mixed 8, every reciprocal on the SFU).
+inline bool grav_tc(const md_ctx *c) {
+  return c->model == MD_GRAV2D && c->prec == MD_MIXED && c->pt.grav_tc && c->pt.r_mixed == 8 && !c->pt.rcp_off;
+}
+
 struct PairArgs {
   const void *mirror_in;
   void *mirror_out;
@@ -386,9 +392,9 @@ __device__ __forceinline__ float2 rsqrt2_fma(float2 d) {
 // ------------------------------------------------------------ forward 2D FP32
 // OFF > 0: every OFF-th pair of j's takes its reciprocals from rcp2_fma, which
 // moves work from the SFU (the binding pipe of this kernel) to the FMA pipe.
-template <int R_, int TJ_, int MODE, int OFF = 0>
+template <int R_, int TJ_, int MODE, int OFF = 0, int MINB_ = 4>
 struct GravMixed {
-  static constexpr int THREADS = NT, MINB = 4;  // CTA size and CTAs per SM of the register budget
+  static constexpr int THREADS = NT, MINB = MINB_;  // CTA size and CTAs per SM of the register budget
   using ColT = float;                           // column partials of the symmetric form
   static constexpr int R = R_, TJ = TJ_, NACC = 2, JB = RecordBytes<MD_GRAV2D, true, false>::value;
   static constexpr bool MASK = false;
@@ -1717,11 +1723,203 @@ struct RingTC {
   }
 };
 
+// ------------------------------------------------------------ forward 2D FP32, tensor cores
+// The coordinate differences dx = x_i - x_j, dy = y_i - y_j of a 16 x 8 block of
+// pairs are one m16n8k8 TF32 product each.  An FP32 coordinate is split exactly
+// into three TF32 parts, x = h + m + l (h = x rounded to TF32, m = the rest rounded
+// to TF32, l = what is left, at most 3 significant bits), laid along K:
+//   A row i:  [h_i, m_i, l_i, 1, 1, 1, 0, 0]
+//   B col j:  [1, 1, 1, -h_j, -m_j, -l_j, 0, 0]
+// so the product is x_i - x_j with exact TF32 products, rounded once more by the
+// FP32 accumulation.  What is left per pair on the FMA pipe is s = dx^2 + dy^2 + eps
+// (2 FFMA) and the force sums (2 FFMA per side), with one rcp on the SFU: the
+// subtraction of the plain kernel moves to the tensor pipe.
+// Record of the 8 particles of an n-block: per lane (g, t) of the B fragment the
+// pair (B[t][g], B[t+4][g]) for x, then for y (64 floats later): 512 bytes.
+
+__device__ __forceinline__ void tf32_split3(float x, float &h, float &m, float &l) {
+  h = __uint_as_float(tf32_rn(x));
+  const float r = x - h;  // exact
+  m = __uint_as_float(tf32_rn(r));
+  l = r - m;  // exact, and a TF32 value
+}
+
+__device__ __forceinline__ void write_tc2_record(void *mirror, int64_t i, float x, float y) {
+  float *m = (float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
+  float xh, xm, xl, yh, ym, yl;
+  tf32_split3(x, xh, xm, xl);
+  tf32_split3(y, yh, ym, yl);
+  float2 *X = (float2 *)m, *Y = (float2 *)(m + 64);
+  X[0] = make_float2(1.f, -xm);
+  X[1] = make_float2(1.f, -xl);
+  X[2] = make_float2(1.f, 0.f);
+  X[3] = make_float2(-xh, 0.f);
+  Y[0] = make_float2(1.f, -ym);
+  Y[1] = make_float2(1.f, -yl);
+  Y[2] = make_float2(1.f, 0.f);
+  Y[3] = make_float2(-yh, 0.f);
+}
+
+// padding: far away (|r|^2 overflows to inf, so 1/s = 0 and the term vanishes)
+__device__ __forceinline__ void write_tc2_pad(void *mirror, int64_t i) { write_tc2_record(mirror, i, 3.0e19f, 3.0e19f); }
+
+template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 2>
+struct GravTC {
+  static constexpr int THREADS = THREADS_;    // CTA size (the one-sided skeletons use NT)
+  static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget is set for
+  using ColT = float;                         // column partials of the symmetric form
+  static constexpr int RM = RM_;              // 16-row m-blocks per warp
+  static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = THREADS * R = 16 RM rows per warp
+  static constexpr int TJ = TJ_, NACC = 2, JB = 64;
+  static constexpr bool MASK = true;
+  static constexpr int NR = 2 * RM;           // rows g and g+8 of each m-block
+  static constexpr int FMT = 2;               // 2D tensor-core fragment records
+  static_assert(THREADS * R == 16 * RM * (THREADS / 32), "tile rows: warps x RM m-blocks x 16");
+  static_assert(TJ % 16 == 0, "two n-blocks per column reduction");
+  __device__ static int mrow(int rr) {        // row offset in the tile of item rr = 2 r + h
+    const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+    return w * 16 * RM + 16 * (rr >> 1) + g + 8 * (rr & 1);
+  }
+  __device__ static int row_of(int rr) { return (threadIdx.x & 3) == 0 ? mrow(rr) : -1; }
+  struct State {
+    unsigned aX[RM][4], aY[RM][4];
+    float2 acc[RM][2][2];  // [m-block][row g / g+8][x, y], columns 2t and 2t+1
+    CompSum cs[RM][2][2];
+  };
+  __device__ static void total(const State &st, int rr, double *out) {
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      double v = csum_total(st.cs[rr >> 1][rr & 1][d]);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      out[d] = v;
+    }
+  }
+  __device__ static void load(State &st, const void *mirror, int64_t i0) {
+    const int t = threadIdx.x & 3;
+#pragma unroll
+    for (int r = 0; r < RM; r++) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int64_t i = i0 + mrow(2 * r + h);
+        const float *m = (const float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
+        // A row: [h, m, l, 1, 1, 1, 0, 0]; the record holds -m at 1, -l at 3, -h at 6
+        const float xa = (t == 0) ? -m[6] : (t == 1) ? -m[1] : (t == 2) ? -m[3] : 1.f;
+        const float ya = (t == 0) ? -m[70] : (t == 1) ? -m[65] : (t == 2) ? -m[67] : 1.f;
+        const float hi = (t < 2) ? 1.f : 0.f;  // A[row][t + 4]
+        st.aX[r][h] = __float_as_uint(xa);
+        st.aX[r][2 + h] = __float_as_uint(hi);
+        st.aY[r][h] = __float_as_uint(ya);
+        st.aY[r][2 + h] = __float_as_uint(hi);
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+          st.acc[r][h][d] = f2(0.f);
+          st.cs[r][h][d] = CompSum{0.f, 0.f};
+        }
+      }
+    }
+  }
+  __device__ static void flush(State &st) {
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+          csum_add2(st.cs[r][h][d], st.acc[r][h][d]);
+          st.acc[r][h][d] = f2(0.f);
+        }
+  }
+  template <bool DIAG>
+  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
+    const float *sm = (const float *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, t = lane & 3;
+#pragma unroll 2
+    for (int k = 0; k < TJ / 8; k++) {
+      const float2 bx = *(const float2 *)(sm + k * 128 + lane * 2);
+      const float2 by = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
+#pragma unroll
+      for (int r = 0; r < RM; r++) {
+        float dX[4], dY[4];
+        mma_tf32(dX, st.aX[r], __float_as_uint(bx.x), __float_as_uint(bx.y));
+        mma_tf32(dY, st.aY[r], __float_as_uint(by.x), __float_as_uint(by.y));
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const float2 dx = make_float2(dX[2 * h], dX[2 * h + 1]);  // row g + 8h, columns 2t, 2t+1
+          const float2 dy = make_float2(dY[2 * h], dY[2 * h + 1]);
+          const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+          float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+          if (DIAG) {
+            const int64_t i = i0 + mrow(2 * r + h), j = j0 + 8 * k + 2 * t;
+            if (i == j) inv.x = 0.f;
+            if (i == j + 1) inv.y = 0.f;
+          }
+          st.acc[r][h][0] = __ffma2_rn(dx, inv, st.acc[r][h][0]);
+          st.acc[r][h][1] = __ffma2_rn(dy, inv, st.acc[r][h][1]);
+        }
+      }
+    }
+    flush(st);
+  }
+  // Off-diagonal block of the Newton's-third-law variant: the i-rows as in tile<>,
+  // and for every j the sums over this warp's 16 RM rows of the same terms, into
+  // colsm[(warp TJ + j) 2 + component].  Per lane and n-block the columns 2t, 2t+1
+  // are summed over the lane's rows; two n-blocks at a time (8 values per lane)
+  // are then reduced over the 8 lanes g by a butterfly.
+  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    const float *sm = (const float *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, t = lane & 3, w = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int k2 = 0; k2 < TJ / 16; k2++) {
+      float v[8];
+#pragma unroll
+      for (int kk = 0; kk < 2; kk++) {
+        const int k = 2 * k2 + kk;
+        const float2 bx = *(const float2 *)(sm + k * 128 + lane * 2);
+        const float2 by = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
+        float2 cx = f2(0.f), cy = f2(0.f);
+#pragma unroll
+        for (int r = 0; r < RM; r++) {
+          float dX[4], dY[4];
+          mma_tf32(dX, st.aX[r], __float_as_uint(bx.x), __float_as_uint(bx.y));
+          mma_tf32(dY, st.aY[r], __float_as_uint(by.x), __float_as_uint(by.y));
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const float2 dx = make_float2(dX[2 * h], dX[2 * h + 1]);
+            const float2 dy = make_float2(dY[2 * h], dY[2 * h + 1]);
+            const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+            const float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+            st.acc[r][h][0] = __ffma2_rn(dx, inv, st.acc[r][h][0]);
+            st.acc[r][h][1] = __ffma2_rn(dy, inv, st.acc[r][h][1]);
+            cx = __ffma2_rn(dx, inv, cx);
+            cy = __ffma2_rn(dy, inv, cy);
+          }
+        }
+        v[4 * kk + 0] = cx.x;
+        v[4 * kk + 1] = cx.y;
+        v[4 * kk + 2] = cy.x;
+        v[4 * kk + 3] = cy.y;
+      }
+      // lane (g, t) ends with value g = 4 kk + 2 component + column parity
+      const float sum = butterfly_sum<8, 16>(v, lane);
+      const int vn = lane >> 2;
+      const int j = 8 * (2 * k2 + (vn >> 2)) + 2 * t + (vn & 1);
+      colsm[(w * TJ + j) * 2 + ((vn >> 1) & 1)] = sum;
+    }
+    flush(st);
+  }
+};
+
 // Record writers by format: FMT 0 = interleaved FP32 / FP64 records above,
-// FMT 1 = tensor-core fragment records (Ring FP32 forward only).
+// FMT 1 = Ring tensor-core fragment records, FMT 2 = 2D tensor-core fragment
+// records (FP32 forward stages only).
 template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __device__ __forceinline__ void write_record_fmt(void *mirror, int64_t i, double x, double y, double vx, double vy) {
-  if constexpr (FMT == 1) {
+  if constexpr (FMT == 2) {
+    write_tc2_record(mirror, i, (float)x, (float)y);
+  } else if constexpr (FMT == 1) {
     const float r = (float)reduce_2pi(x);
     float s, c, a, g;
     sincos_small(r, &s, &c);
@@ -1733,7 +1931,9 @@ __device__ __forceinline__ void write_record_fmt(void *mirror, int64_t i, double
 }
 template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __device__ __forceinline__ void write_pad_fmt(void *mirror, int64_t i) {
-  if constexpr (FMT == 1)
+  if constexpr (FMT == 2)
+    write_tc2_pad(mirror, i);
+  else if constexpr (FMT == 1)
     write_tc_pad(mirror, i);
   else
     write_pad<MODEL, MIXED, ADJ>(mirror, i);
