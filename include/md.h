@@ -123,7 +123,8 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "r_mixed"          i-particles per thread of the FP32 pair kernels (4 or 8)
  *   "r_fp64"           i-particles per thread of the FP64 pair kernels (2 or 4)
  *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
- *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = occupancy limit)
+ *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = default: 4 for the FP32
+ *                      sine/cosine stages, the occupancy limit otherwise)
  *   "rcp_offload"      2D FP32: every 8th pair of j's takes 1/x on the FMA pipe (0 or 8)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32
  *                      tensor-core products (0 off; 1 or 2: 4 or 2 16-row blocks per warp)

@@ -70,6 +70,7 @@ struct md_ctx {
   unsigned *hmf_ticket = nullptr;
   int hmf_grid_max = 0;
   int hmf_cur = 0;
+  int hmf_rev = 0;                    // sweep direction of the next stage (alternates)
   bool hmf_m_valid = false;           // FP64: the (cos, sin) buffer is valid with the sums
   double *hmf_cs = nullptr;           // FP64 path: (cos, sin) of the current angles, N double2
   size_t hmf_cs_bytes = 0;

@@ -137,11 +137,11 @@ def test_full_size_sampled_force_parity(prec):
 
 
 def test_unsupported_calls_are_rejected():
+    """The magnetization (and its gradient) needs an angle; the disk recipe is the
+    2D model's.  Gradients of the kinetic energy are supported."""
     s, q, p = _sys(100)
     with pytest.raises(MDError):
-        s.grad(2)
-    with pytest.raises(MDError):
-        s.tangent_step(1, np.zeros(300), np.zeros(300))
+        s.grad(2, 1)
     with pytest.raises(MDError):
         s.magnetization()
     with pytest.raises(MDError):

@@ -152,6 +152,8 @@ def test_full_size_sampled_force_parity(prec):
 
 
 def test_unsupported_calls_are_rejected():
+    """At eps = 0 the sheet force is piecewise constant: no derivatives; no angle,
+    so no magnetization."""
     s, _, _ = _sys(100)
     with pytest.raises(MDError):
         s.grad(2)
