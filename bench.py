@@ -250,39 +250,46 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def _spawn_parts(target, part_args):
+    """Run target(*args, barrier, out) once per entry of part_args in spawned processes
+    (no CUDA state is inherited) and return their (units, t_start, t_end) reports."""
+    import multiprocessing as mp
+    import queue
+
+    n = len(part_args)
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(n), ctx.Queue()
+    procs = [ctx.Process(target=target, args=tuple(a) + (barrier, out), daemon=True) for a in part_args]
+    for pr in procs:
+        pr.start()
+    res = []
+    t_end = time.monotonic() + 900
+    try:
+        while len(res) < n:
+            try:
+                res.append(out.get(timeout=1.0))
+            except queue.Empty:
+                failed = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+                if failed or time.monotonic() > t_end:
+                    raise RuntimeError(f"oracle leg: worker processes failed (exit codes {failed})")
+    finally:
+        for pr in procs:
+            pr.join(timeout=30)
+            if pr.is_alive():
+                pr.terminate()
+    return res
+
+
 def oracle_steps(w, n: int, steps: int, warmup: int = 0, cores: int = 1):
     """Run the FP64 CPU oracle, as it stands, on a sample of the workload over
-    `cores` processes (spawned, so that no CUDA state is inherited) and return
-    (units processed in the timed steps, wall seconds, description)."""
+    `cores` processes and return (units processed in the timed steps, wall
+    seconds, description)."""
     model, N = w["model"], w["N"]
     if cores <= 1:
         units, t0, t1 = _oracle_part(w, 0, 1, n, steps, warmup)
         el = t1 - t0
     else:
-        import multiprocessing as mp
-        import queue
-
-        ctx = mp.get_context("spawn")
-        barrier, out = ctx.Barrier(cores), ctx.Queue()
-        procs = [ctx.Process(target=_oracle_part, args=(w, k, cores, n, steps, warmup, barrier, out), daemon=True)
-                 for k in range(cores)]
-        for pr in procs:
-            pr.start()
-        res = []
-        t_end = time.monotonic() + 900
-        try:
-            while len(res) < cores:
-                try:
-                    res.append(out.get(timeout=1.0))
-                except queue.Empty:
-                    failed = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
-                    if failed or time.monotonic() > t_end:
-                        raise RuntimeError(f"oracle leg: worker processes failed (exit codes {failed})")
-        finally:
-            for pr in procs:
-                pr.join(timeout=30)
-                if pr.is_alive():
-                    pr.terminate()
+        res = _spawn_parts(_oracle_part, [(w, k, cores, n, steps, warmup) for k in range(cores)])
         units = sum(r[0] for r in res)
         el = max(r[2] for r in res) - min(r[1] for r in res)
     if model == 0:
@@ -293,6 +300,48 @@ def oracle_steps(w, n: int, steps: int, warmup: int = 0, cores: int = 1):
         desc = (f"{n} of {N} rows{over} x {N} partners, 3 force evaluations per step, "
                 f"{steps} steps (direct pair sums)")
     return units, el, desc
+
+
+def _oracle_grad_part(w, n: int, nsteps: int, grads: int, barrier=None, out=None):
+    """`grads` oracle gradients of K(T) after nsteps steps on an n-particle system
+    of the workload's recipe (each process its own replica); pair interactions
+    counted as the GPU leg counts them, n^2 (6 nsteps + 1) per gradient."""
+    import oracle as ora
+    from paper_1212_0262_gb300 import inputs
+
+    q, p = inputs.default_state(w["model"], n, w["seed"])
+    ora.grad(w["model"], q, p, w["eps"], w["dt"], 1)
+    if barrier is not None:
+        barrier.wait(timeout=600)
+    t0 = time.monotonic()
+    for _ in range(grads):
+        ora.grad(w["model"], q, p, w["eps"], w["dt"], nsteps)
+    t1 = time.monotonic()
+    units = float(n) * n * (6 * nsteps + 1) * grads
+    if out is None:
+        return units, t0, t1
+    out.put((units, t0, t1))
+    return None
+
+
+def oracle_grad(w, seconds: float, grads: int, nsteps: int = 100, cores: int = 1):
+    """The oracle's discrete adjoint on an n-particle sample, n sized so that `grads`
+    gradients take about `seconds` per process: (units, wall seconds, description)."""
+    u0, t0, t1 = _oracle_grad_part(w, 64, nsteps, 1)
+    per_unit = (t1 - t0) / u0
+    n = int((seconds / grads / per_unit / (6 * nsteps + 1)) ** 0.5)
+    n = max(64, min(w["N"], n))
+    if cores <= 1:
+        units, a, b = _oracle_grad_part(w, n, nsteps, grads)
+        el = b - a
+    else:
+        res = _spawn_parts(_oracle_grad_part, [(w, n, nsteps, grads)] * cores)
+        units = sum(r[0] for r in res)
+        el = max(r[2] for r in res) - min(r[1] for r in res)
+    who = f"{cores} processes, each " if cores > 1 else ""
+    return units, el, (f"{who}{grads} oracle gradient(s) of K(T) after {nsteps} steps on a system of {n} particles "
+                       f"of the same recipe (forward pass storing every kick position, reversed "
+                       f"adjoint pass; n^2 (6 nsteps + 1) pair interactions each)")
 
 
 def oracle_sample_size(w, seconds: float, steps: int, cores: int = 1) -> int:
@@ -333,6 +382,9 @@ def run_reference(args, w):
     cores = args.cpu_cores or host_cores()
     if w["model"] == -1:
         units, el, sample = ensemble_oracle(30.0, K, W, cores)
+        rate = units / el
+    elif args.workload == "adjoint":
+        units, el, sample = oracle_grad(w, 60.0 / max(1, K + W) * K, K, cores=cores)
         rate = units / el
     else:
         n = oracle_sample_size(w, 60.0, K + W, cores)
@@ -733,6 +785,27 @@ def run_adjoint(args, w):
     for prec in ("fp64", "mixed"):
         with System(2, n2, w["eps"], w["dt"], w["seed"], precision=prec) as s2:
             out[prec] = s2.grad(nsteps, 0, K)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        # the state from pinned host memory and the gradient back to host arrays,
+        # through the public API (wall clock)
+        qh = torch.empty(2 * N, dtype=torch.float64, pin_memory=True).numpy()
+        ph = torch.empty(2 * N, dtype=torch.float64, pin_memory=True).numpy()
+        qh[:], ph[:] = s.get_state()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.set_state(qh, ph)
+        s.grad(nsteps, 0, K)
+        e_el = time.perf_counter() - t1
+        e2e = {"value": pairs / e_el, "unit": w["unit"], "h2d_bytes_per_step": 2 * 8 * 2 * N,
+               "d2h_bytes_per_step": 2 * 8 * 2 * N + 16, "steps": 1,
+               "note": "md_set_state(host) + md_grad (gradients to host arrays), wall clock"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = args.cpu_cores or host_cores()
+        units, c_el, sample = oracle_grad(w, 10.0, 1, nsteps, cores)
+        cpu = {"value": units / c_el, "unit": w["unit"], "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": c_el}
     rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
     err = {"grad_q": rel(out["mixed"][1], out["fp64"][1]), "grad_p": rel(out["mixed"][2], out["fp64"][2]),
            "grad_eps": abs(out["mixed"][3] - out["fp64"][3]) / abs(out["fp64"][3]), "N": n2}
@@ -764,7 +837,7 @@ def run_adjoint(args, w):
                                             "nsteps": nsteps, "checkpoint_every": K},
             "gradient_seconds": el, "value_K_T": val, "grad_eps": ge,
             "mixed_vs_fp64_gradient_rel_error": err, "gpu_launches": launches, "clocks": clocks,
-            "roofline": roofline, "cpu_baseline": None, "e2e": None}), flush=True)
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}), flush=True)
     s.close()
 
 

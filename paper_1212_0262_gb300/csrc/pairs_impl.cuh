@@ -810,10 +810,10 @@ struct Grav3DF64 {
   }
   template <bool DIAG>
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
-    const double4 *sm = (const double4 *)smb;
+    const double4_16a *sm = (const double4_16a *)smb;
 #pragma unroll 2
     for (int k = 0; k < TJ; k++) {
-      const double4 o = sm[k];
+      const double4_16a o = sm[k];
 #pragma unroll
       for (int r = 0; r < R; r++) {
         const double dx = st.x[r] - o.x, dy = st.y[r] - o.y, dz = st.z[r] - o.z;
@@ -829,14 +829,14 @@ struct Grav3DF64 {
   // z terms into colsm[(warp TJ + j) 3 + d]; eight j's at a time, (x, y) by a
   // butterfly of 16 values and z by one of 8.
   __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
-    const double4 *sm = (const double4 *)smb;
+    const double4_16a *sm = (const double4_16a *)smb;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll 1
     for (int k8 = 0; k8 < TJ / 8; k8++) {
       double vxy[16], vz[8];
 #pragma unroll
       for (int kk = 0; kk < 8; kk++) {
-        const double4 o = sm[8 * k8 + kk];
+        const double4_16a o = sm[8 * k8 + kk];
         double cx = 0.0, cy = 0.0, cz = 0.0;
 #pragma unroll
         for (int r = 0; r < R; r++) {
@@ -1278,10 +1278,10 @@ struct Grav3DF64Adj {
   }
   template <bool DIAG>
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
-    const double4 *sm = (const double4 *)smb;
+    const double4_16a *sm = (const double4_16a *)smb;
 #pragma unroll 1
     for (int k = 0; k < TJ; k++) {
-      const double4 P = sm[2 * k], V = sm[2 * k + 1];
+      const double4_16a P = sm[2 * k], V = sm[2 * k + 1];
 #pragma unroll
       for (int r = 0; r < R; r++) {
         const double dx = st.x[r] - P.x, dy = st.y[r] - P.y, dz = st.z[r] - P.z;
@@ -1952,23 +1952,24 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
   double f[D], x[D];
 #pragma unroll
   for (int d = 0; d < D; d++) f[d] = MODEL == MD_SHEET1D ? -acc[d] / (double)a.N : scale * acc[d];
-  if (MODE == STAGE_FORCE_ONLY) {
+  if constexpr (MODE == STAGE_FORCE_ONLY) {
 #pragma unroll
     for (int d = 0; d < D; d++) a.fout[d * a.N + i] = f[d];
     return;
-  }
+  } else {
 #pragma unroll
-  for (int d = 0; d < D; d++) {
-    const double pp = fma(a.kick, f[d], a.p[d * a.N + i]);
-    a.p[d * a.N + i] = pp;
-    if (MODE == STAGE_KICK_DRIFT) {
-      x[d] = fma(a.drift, pp, a.q[d * a.N + i]);
-      a.q[d * a.N + i] = x[d];
-    } else {
-      a.fout[d * a.N + i] = f[d];
+    for (int d = 0; d < D; d++) {
+      const double pp = fma(a.kick, f[d], a.p[d * a.N + i]);
+      a.p[d * a.N + i] = pp;
+      if (MODE == STAGE_KICK_DRIFT) {
+        x[d] = fma(a.drift, pp, a.q[d * a.N + i]);
+        a.q[d * a.N + i] = x[d];
+      } else {
+        a.fout[d * a.N + i] = f[d];
+      }
     }
   }
-  if (MODE == STAGE_KICK_DRIFT) {
+  if constexpr (MODE == STAGE_KICK_DRIFT) {
     if constexpr (MODEL == MD_GRAV3D)
       write_record3<MIXED>(a.mirror_out, i, x[0], x[1], x[D - 1]);
     else if constexpr (MODEL == MD_SHEET1D)

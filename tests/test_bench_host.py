@@ -53,3 +53,10 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["unit"] == "pair-interactions/s" and d["value"] > 0
     assert d["cpu_baseline"]["cores"] == 2 and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_oracle_gradient_leg_counts_both_passes(bench):
+    w = dict(model=2, N=262144, eps=1e-4, dt=0.01, seed=4)
+    u, el, d = bench.oracle_grad(w, 0.3, 1, nsteps=4, cores=2)
+    n = int(d.split(" particles")[0].split()[-1])
+    assert u == 2 * float(n) * n * (6 * 4 + 1) and el > 0 and d.startswith("2 processes")
