@@ -100,3 +100,45 @@ def test_one_sided_tunings_agree_with_the_symmetric_default():
             assert np.max(np.abs(q - qr)) <= 1e-5 * max(1.0, np.abs(qr).max()), (r, s)
         e2.close()
     ref.close()
+
+
+def test_bench_ensemble_sampled_systems_match_the_single_system_path():
+    """The 256-system ensemble of the bench (128 Ring at eps = 0.01, 128 2D at
+    eps = 1e-4, N = floor(4096 16^u)), autotuned as the bench runs it: after one
+    step, the smallest and largest system of each model equal the same system
+    advanced alone by md_step (whose forces the full-size sampled parity tests pin to
+    the oracle) to rounding; after two steps every system's energy error is within
+    twice that of the same ensemble run in FP64."""
+    nsys = 256
+    Ns = inputs.ensemble_sizes(nsys, 1000)
+    models = [1 if s < nsys // 2 else 2 for s in range(nsys)]
+    eps = [0.01 if m == 1 else 1e-4 for m in models]
+    dts = [0.05 if m == 1 else 0.01 for m in models]
+    seeds = [1000 + s for s in range(nsys)]
+    ens = Ensemble(models, Ns, eps, dts, seeds, precision="mixed")
+    ens.autotune()
+    K0, V0 = ens.energy()
+    ens.step(1)
+    half = nsys // 2
+    pick = [int(np.argmin(Ns[:half])), int(np.argmax(Ns[:half])),
+            half + int(np.argmin(Ns[half:])), half + int(np.argmax(Ns[half:]))]
+    for s in pick:
+        with System(models[s], int(Ns[s]), eps[s], dts[s], seeds[s], precision="mixed") as sy:
+            sy.step(1)
+            q, p = sy.get_state()
+        qb, pb = ens.get_state(s)
+        assert np.max(np.abs(qb - q)) <= 1e-9 * max(1.0, np.abs(q).max()), s
+        assert np.max(np.abs(pb - p)) <= 1e-9 * max(1.0, np.abs(p).max()), s
+    ens.step(1)
+    K, V = ens.energy()
+    e0 = K0 + V0
+    de_mixed = np.abs(K + V - e0) / np.abs(e0)
+    ens.close()
+    ref = Ensemble(models, Ns, eps, dts, seeds, precision="fp64")
+    Kr0, Vr0 = ref.energy()
+    assert np.allclose(Kr0 + Vr0, e0, rtol=1e-12, atol=0.0)
+    ref.step(2)
+    Kr, Vr = ref.energy()
+    de_fp64 = np.abs(Kr + Vr - e0) / np.abs(e0)
+    ref.close()
+    assert np.all(de_mixed <= 2.0 * de_fp64 + 1e-9), np.max(de_mixed - 2.0 * de_fp64)
