@@ -253,6 +253,48 @@ def test_3d_shell_theorem(ora):
     assert abs((V_all - V_shell) - (-12.0 / (N * D))) < 1e-6 * 12.0 / (N * D)
 
 
+def test_ring_is_3d_gravity_on_the_unit_circle(ora):
+    """The Ring model (Eq. 1) is softened 3D gravity restricted to the unit circle:
+    |r_i - r_j|^2 = 2 (1 - cos(theta_i - theta_j)), so with the 3D softening 2 eps
+    V_ring(theta, eps) = V_3D((cos, sin, 0), 2 eps), and the Ring force is the
+    tangential component (-sin, cos, 0) . F_3D of the 3D force (chord geometry, not
+    the Ring formulas: a wrong sqrt(2), eps or sign in either fails)."""
+    rng = np.random.default_rng(12)
+    N, eps = 37, 0.01
+    th = rng.uniform(-np.pi, np.pi, N) + 2 * np.pi * rng.integers(-3, 4, N)
+    q3 = np.concatenate([np.cos(th), np.sin(th), np.zeros(N)])
+    v_r, v_3 = ora.potential(1, th, eps), ora.potential(3, q3, 2 * eps)
+    assert abs(v_r - v_3) <= 1e-13 * abs(v_r)
+    F = ora.force(3, q3, 2 * eps).reshape(3, N)
+    f_t = -np.sin(th) * F[0] + np.cos(th) * F[1]
+    f_r = ora.force(1, th, eps)
+    assert np.max(np.abs(f_r - f_t)) <= 1e-12 * np.max(ora.force_abs(1, th, eps))
+
+
+def test_2d_shell_theorem_for_the_log_potential(ora):
+    """Newton's theorem for the 2D (logarithmic) potential of Eq. 3: M unit masses on a
+    regular M-gon of radius a act on a distant test mass like M masses at the centre,
+    and exert no force on a mass inside, both up to O((ratio)^(M-1)); eps = 1e-12."""
+    M, a, eps = 16, 0.05, 1e-12
+    ang = 0.3 + 2 * np.pi * np.arange(M) / M
+    ring = np.stack([a * np.cos(ang), a * np.sin(ang)], axis=1)
+    D = 1.0
+    test = np.array([0.6, -0.8]) * D
+    r = np.vstack([ring, test])
+    N = M + 1
+    q = r.T.reshape(-1)
+    f = ora.force(2, q, eps).reshape(2, N)[:, -1]
+    f_point = -(2.0 / N) * M * test / D ** 2
+    assert np.max(np.abs(f - f_point)) < 1e-9 * np.linalg.norm(f_point)
+    V_all = ora.potential(2, q, eps)
+    V_ring = ora.potential(2, ring.T.reshape(-1), eps) * M / N  # same 1/N coupling
+    assert abs((V_all - V_ring) - (M / N) * math.log(D ** 2)) < 1e-9
+    inside = np.vstack([ring / a * 0.1, [[0.012, 0.021]]])  # ring radius 0.1, |x| = 0.024
+    fi = ora.force(2, inside.T.reshape(-1), eps).reshape(2, N)[:, -1]
+    scale = (2.0 / N) * M / 0.1
+    assert np.max(np.abs(fi)) < 1e-8 * scale
+
+
 def test_3d_two_body_circular_orbit(ora):
     """Two unit masses at separation d with speeds v = 1/(2 sqrt(d)) (eps = 0, N = 2:
     coupling 1/2) move on a circle: the separation stays d and they are back at the
