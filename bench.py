@@ -518,9 +518,17 @@ def run_ours(args, w):
         # unordered pairs when each is evaluated once
         terms = N * (N - 1) / 2 if sym else N * N
         achieved = terms / (avg_ms * 1e-3)
+        # DRAM bytes per stage (pair and finish kernels) of the default symmetric FP32
+        # kernels, from the committed ncu record when the sources are unchanged
+        traffic = None
+        if args.prec == "mixed" and (model, kcode) in ((1, 5), (2, 4)) and not args.tune:
+            traffic = recorded_traffic(f"{args.workload}_stage_sym_mixed",
+                                       ["paper_1212_0262_gb300/csrc/sym.cu",
+                                        "paper_1212_0262_gb300/csrc/pairs_impl.cuh",
+                                        "paper_1212_0262_gb300/csrc/md_internal.cuh"], float(N) * N)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                     "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "kernel": f"{kname}, {args.prec}",
                     "peak_derivation": {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
                                         "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
