@@ -77,6 +77,23 @@ PAIR_KERNELS = {
     (4, 2): ("streamk_kernel<SheetMixed<8,256>>", 4, 0, False),
     (4, 4): ("sym_kernel<SheetMixed<8,256>>", 5.25, 0, True),
 }
+# FP64 kernels: name, FP64-pipe operations per evaluated pair term (the reciprocal
+# square root or reciprocal: FP32 seed on the SFU with integer-pipe conversions, then
+# 5 or 3 FP64 operations), whether each unordered pair is evaluated once.
+#   Ring: S and sin(d/2) (2 each), dd, rsqrt (5); symmetric: S y^3 (3), row and column
+#   adds, butterfly 1/2 -> 15.5; one-sided: S y, y^2, accumulate -> 13
+#   2D: dx, dy, s (2), rcp (3); symmetric: 2 products, 2 row and 2 column adds,
+#   butterfly 1 -> 14; one-sided: 2 FMA accumulations -> 9
+#   3D: dx, dy, dz, s (3), rsqrt (5), y^3 (2); symmetric: 3 products, 3 + 3 adds,
+#   butterfly 1.4 -> 23.4; one-sided: 3 FMA accumulations -> 16
+PAIR_KERNELS_FP64 = {
+    (1, 6): ("sym_kernel<RingF64<4,128>>", 15.5, True),
+    (1, 1): ("streamk_kernel<RingF64<2,128>>", 13, False),
+    (2, 6): ("sym_kernel<GravF64<4,128>>", 14, True),
+    (2, 1): ("streamk_kernel<GravF64<2,128>>", 9, False),
+    (3, 6): ("sym_kernel<Grav3DF64<4,128>>", 23.4, True),
+    (3, 1): ("streamk_kernel<Grav3DF64<2,128>>", 16, False),
+}
 
 
 def parse():
@@ -512,6 +529,10 @@ def run_ours(args, w):
         kcode = sysm.force_kernel
         kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
         pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops) if sops else fp32_rate / fops
+        f64 = PAIR_KERNELS_FP64.get((model, kcode)) if args.prec == "fp64" else None
+        if f64:  # FP64 kernels: bound by the FP64 pipe (measured DFMA rate)
+            kname, dops, sym = f64
+            pairs_per_clk = rates[13] / dops
         mhz = clocks.get("sm_mhz") or rates[2]
         peak = nsm * pairs_per_clk * mhz * 1e6
         # algorithmic pair terms per force pass: N^2 ordered pairs, or N (N - 1) / 2
@@ -530,10 +551,14 @@ def run_ours(args, w):
                     "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "kernel": f"{kname}, {args.prec}",
-                    "peak_derivation": {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
-                                        "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
-                                        "sfu_ops_per_pair": sops, "sm_mhz": mhz},
+                    "peak_derivation": ({"sms": nsm, "fp64_ops_per_sm_clk": rates[13], "fp64_ops_per_pair": f64[1],
+                                         "sm_mhz": mhz} if f64 else
+                                        {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
+                                         "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
+                                         "sfu_ops_per_pair": sops, "sm_mhz": mhz}),
                     "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
+        if args.prec == "fp64" and not f64:
+            roofline = None  # FP64 sheets: sign counting, no stated pipe bound
 
     # FP64 path on the same workload (few steps) and the matching mixed energy error
     extra = {}

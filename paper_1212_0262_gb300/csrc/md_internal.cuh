@@ -218,26 +218,38 @@ __device__ __forceinline__ float mufu_rcp(float x) {
   return r;
 }
 
-// 1/sqrt(d) in FP64: FP32 hardware seed refined by two Newton-Raphson steps for
-// y^-2 = d (y <- y + y (1 - d y^2) / 2); each step squares the relative error.
-__device__ __forceinline__ double rsqrt_nr(double d) {
-  double y = (double)mufu_rsqrt((float)d);
-  double e = fma(-(d * y), y, 1.0);
-  y = fma(0.5 * y, e, y);
-  e = fma(-(d * y), y, 1.0);
-  y = fma(0.5 * y, e, y);
-  return y;
+// Seeds for the FP64 reciprocal (square) roots below.  A positive double becomes a
+// float by moving bits (mantissa truncated; beyond the float range +inf, below the
+// normal range 0), and a non-negative float a double the same way, so neither
+// conversion runs on the FP64 pipe, which bounds the FP64 pair kernels.
+__device__ __forceinline__ float seed_d2f(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned f = ((hi - 0x38000000u) << 3) | (lo >> 29);
+  return __uint_as_float(hi >= 0x47F00000u ? 0x7f800000u : hi < 0x38100000u ? 0u : f);
+}
+__device__ __forceinline__ double seed_f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  if (u == 0u) return 0.0;
+  if (u >= 0x7f800000u) return __longlong_as_double(0x7ff0000000000000LL);
+  return __hiloint2double((int)((u >> 3) + 0x38000000u), (int)(u << 29));
 }
 
-// 1/s in FP64: FP32 hardware seed refined by two Newton-Raphson steps for
-// 1/y = s (y <- y + y (1 - s y)).
+// 1/sqrt(d) in FP64 for d in the normal float range: FP32 hardware seed y (relative
+// error below 2^-22), then one third-order Householder step for y^-2 = d:
+// e = 1 - d y^2, y <- y (1 + e/2 + 3 e^2/8) (the series of (1 - e)^(-1/2) to e^2),
+// which leaves a truncation error of (5/16) e^3 < 2^-63.
+__device__ __forceinline__ double rsqrt_nr(double d) {
+  const double y = seed_f2d(mufu_rsqrt(seed_d2f(d)));
+  const double e = fma(-(d * y), y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+// 1/s in FP64 for s in the normal float range: FP32 hardware seed y, then one
+// third-order step e = 1 - s y, y <- y (1 + e + e^2) (truncation error e^3 < 2^-66).
 __device__ __forceinline__ double rcp_nr(double s) {
-  double y = (double)mufu_rcp((float)s);
-  double e = fma(-s, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-s, y, 1.0);
-  y = fma(y, e, y);
-  return y;
+  const double y = seed_f2d(mufu_rcp(seed_d2f(s)));
+  const double e = fma(-s, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // sin and cos of a float of modest size (|x| < 2^20), for arguments that were
