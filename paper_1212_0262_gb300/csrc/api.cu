@@ -67,23 +67,31 @@ std::unordered_map<void *, AllocRec> g_blocks;
 
 void *dev_alloc(size_t bytes) {
   if (bytes == 0) bytes = 16;
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  // the hook is called outside the lock (a caller's allocator may itself allocate
+  // through this library or take locks of its own); only the registry is guarded
+  void *(*alloc)(size_t, void *);
+  void (*free_fn)(void *, void *);
+  void *user;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    alloc = g_alloc;
+    free_fn = g_free;
+    user = g_alloc_user;
+  }
   void *ptr = nullptr;
-  if (g_alloc) {
-    ptr = g_alloc(bytes, g_alloc_user);
+  if (alloc) {
+    ptr = alloc(bytes, user);
     if (!ptr) return nullptr;
     if ((reinterpret_cast<uintptr_t>(ptr) & 255u) != 0) {  // the kernels' vector loads need 256 B
-      if (g_free) g_free(ptr, g_alloc_user);
+      free_fn(ptr, user);
       return nullptr;
     }
-    g_blocks[ptr] = AllocRec{g_free, g_alloc_user};
-  } else {
-    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    g_blocks[ptr] = AllocRec{nullptr, nullptr};
+  } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
   }
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_blocks[ptr] = AllocRec{alloc ? free_fn : nullptr, alloc ? user : nullptr};
   return ptr;
 }
 
