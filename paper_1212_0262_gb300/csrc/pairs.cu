@@ -168,14 +168,16 @@ __global__ void mirror_kernel(const double *__restrict__ q, const double *__rest
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Npad; i += G) {
     if constexpr (MODEL == MD_SHEET1D) {
-      const double x = i < N ? q[i] : sheet_pad(eps, MIXED);
       if constexpr (ADJ) {
+        const double x = i < N ? q[i] : sheet_pad(eps, MIXED);
         const double v = i < N ? lp[i] : 0.0;
         write_record1_adj<MIXED>(m0, i, x, v);
         if (i >= N && m1) write_record1_adj<MIXED>(m1, i, x, v);
+      } else if (i < N) {
+        write_record1<MIXED>(m0, i, q[i]);
       } else {
-        write_record1<MIXED>(m0, i, x);
-        if (i >= N && m1) write_record1<MIXED>(m1, i, x);
+        write_pad1<MIXED>(m0, i, eps);
+        if (m1) write_pad1<MIXED>(m1, i, eps);
       }
       continue;
     }

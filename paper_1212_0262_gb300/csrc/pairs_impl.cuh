@@ -46,16 +46,37 @@ __device__ __forceinline__ void write_record3(void *mirror, int64_t i, double x,
     m[3] = 0.0;
   }
 }
-// 1D-sheet records: FP32, per particle pair (2k, 2k+1) the floats (-x, -x');
-// FP64, x.  Padding must contribute exactly zero: with eps = 0 a NaN position
-// (both comparisons of the sign are false), with eps > 0 a far one (d^2 overflows,
-// the reciprocal square root is 0).
+// 1D-sheet records: FP32, per particle pair (2k, 2k+1) the floats (-x, -x').
+// FP64 sheet records hold an order-preserving integer key of x: the bits for x >= 0,
+// the bits with the magnitude flipped for x < 0, so signed comparison of keys orders
+// as the doubles do (-0 is stored as +0: equal values, equal keys).  The sign of
+// x_i - x_j at eps = 0 is then two integer comparisons on the ALU pipe, exactly the
+// FP64 decision; at eps > 0 the kernel turns the key back into x.
+__device__ __forceinline__ long long sheet_key(double x) {
+  const long long b = __double_as_longlong(x + 0.0);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double sheet_unkey(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
 template <bool MIXED>
 __device__ __forceinline__ void write_record1(void *mirror, int64_t i, double x) {
   if constexpr (MIXED)
     ((float *)mirror)[i] = -(float)x;
   else
-    ((double *)mirror)[i] = x;
+    ((long long *)mirror)[i] = sheet_key(x);
+}
+// Padding: at eps > 0 far away (FP32: x^2 overflows, so the term is d * rsqrt(inf) = 0;
+// FP64: rsqrt_nr saturates to 0 beyond the float range); at eps = 0 FP32 NaN (both
+// comparisons false) and FP64 the smallest key, which adds exactly +1 to every real
+// row (removed in the epilogue: n_jt TJ - N padding records per row).
+template <bool MIXED>
+__device__ __forceinline__ void write_pad1(void *mirror, int64_t i, double eps) {
+  if constexpr (MIXED)
+    ((float *)mirror)[i] = eps > 0.0 ? -3.0e19f : __int_as_float(0x7fc00000);
+  else
+    ((long long *)mirror)[i] = eps > 0.0 ? sheet_key(1.0e150) : (long long)0x8000000000000000ULL;
 }
 __device__ __forceinline__ double sheet_pad(double eps, bool mixed) {
   return eps > 0.0 ? (mixed ? 3.0e19 : 1.0e150) : __longlong_as_double(0x7FF8000000000000LL);
@@ -963,6 +984,9 @@ struct SheetMixed {
 };
 
 // ------------------------------------------------------------ forward 1D sheets FP64
+// Records are integer keys of x (sheet_key).  eps = 0: per pair the two comparisons
+// k_i > k_j and k_i < k_j on the ALU pipe, counted in integers per tile; eps > 0:
+// x from the key, d / sqrt(d^2 + eps) in FP64.
 template <int R_, int TJ_, int MODE>
 struct SheetF64 {
   static constexpr int THREADS = NT, MINB = 4;
@@ -973,55 +997,100 @@ struct SheetF64 {
   static constexpr int FMT = 0;
   __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
   struct State {
-    double x[R];
+    long long k[R];
     double accd[R][NACC];
   };
   __device__ static void total(const State &st, int r, double *out) { out[0] = st.accd[r][0]; }
   __device__ static void load(State &st, const void *mirror, int64_t i0) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-      st.x[r] = ((const double *)mirror)[i0 + row_of(r)];
+      st.k[r] = ((const long long *)mirror)[i0 + row_of(r)];
       st.accd[r][0] = 0.0;
     }
   }
-  __device__ static double term(double xi, double xj, double eps, bool smooth) {
-    const double d = xi - xj;
-    if (!smooth) return (double)(d > 0.0) - (double)(d < 0.0);
+  __device__ static int cmp(long long ki, long long kj) { return (int)(ki > kj) - (int)(ki < kj); }
+  __device__ static double smooth_term(double xi, long long kj, double eps) {
+    const double d = xi - sheet_unkey(kj);
     return d * rsqrt_nr(fma(d, d, eps));
   }
   template <bool DIAG>
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
-    const double *sm = (const double *)smb;
-    const bool smooth = a.epsd > 0.0;
-#pragma unroll 2
-    for (int k = 0; k < TJ; k++) {
-      const double xj = sm[k];
+    const long long *sm = (const long long *)smb;
+    if (a.epsd > 0.0) {
+      double x[R];
 #pragma unroll
-      for (int r = 0; r < R; r++) st.accd[r][0] += term(st.x[r], xj, a.epsd, smooth);
+      for (int r = 0; r < R; r++) x[r] = sheet_unkey(st.k[r]);
+#pragma unroll 2
+      for (int k = 0; k < TJ; k++) {
+        const long long kj = sm[k];
+#pragma unroll
+        for (int r = 0; r < R; r++) st.accd[r][0] += smooth_term(x[r], kj, a.epsd);
+      }
+    } else {
+      int acc[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) acc[r] = 0;
+#pragma unroll 4
+      for (int k = 0; k < TJ; k++) {
+        const long long kj = sm[k];
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] += cmp(st.k[r], kj);
+      }
+#pragma unroll
+      for (int r = 0; r < R; r++) st.accd[r][0] += (double)acc[r];
     }
   }
   __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, double *colsm) {
-    const double *sm = (const double *)smb;
-    const bool smooth = a.epsd > 0.0;
+    const long long *sm = (const long long *)smb;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (a.epsd > 0.0) {
+      double x[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) x[r] = sheet_unkey(st.k[r]);
 #pragma unroll 1
-    for (int k16 = 0; k16 < TJ / 16; k16++) {
-      double v[16];
+      for (int k16 = 0; k16 < TJ / 16; k16++) {
+        double v[16];
 #pragma unroll
-      for (int kk = 0; kk < 16; kk++) {
-        const double xj = sm[16 * k16 + kk];
-        double col = 0.0;
+        for (int kk = 0; kk < 16; kk++) {
+          const long long kj = sm[16 * k16 + kk];
+          double col = 0.0;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-          const double t = term(st.x[r], xj, a.epsd, smooth);
-          st.accd[r][0] += t;
-          col += t;
+          for (int r = 0; r < R; r++) {
+            const double t = smooth_term(x[r], kj, a.epsd);
+            st.accd[r][0] += t;
+            col += t;
+          }
+          v[kk] = col;
         }
-        v[kk] = col;
+        double sum = butterfly_sum<16, 16>(v, lane);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if ((lane & 1) == 0) colsm[w * TJ + 16 * k16 + (lane >> 1)] = sum;
       }
-      double sum = butterfly_sum<16, 16>(v, lane);
-      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-      if ((lane & 1) == 0) colsm[w * TJ + 16 * k16 + (lane >> 1)] = sum;
+    } else {
+      int acc[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) acc[r] = 0;
+#pragma unroll 1
+      for (int k16 = 0; k16 < TJ / 16; k16++) {
+        int v[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+          const long long kj = sm[16 * k16 + kk];
+          int col = 0;
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            const int t = cmp(st.k[r], kj);
+            acc[r] += t;
+            col += t;
+          }
+          v[kk] = col;
+        }
+        int sum = butterfly_sum<16, 16>(v, lane);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if ((lane & 1) == 0) colsm[w * TJ + 16 * k16 + (lane >> 1)] = (double)sum;
+      }
+#pragma unroll
+      for (int r = 0; r < R; r++) st.accd[r][0] += (double)acc[r];
     }
   }
 };
@@ -2080,12 +2149,17 @@ __device__ __forceinline__ void finish_tangent(const PairArgs &a, int64_t i, con
 
 template <class Pol, int MODEL, bool MIXED, int MODE>
 __device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const double *acc) {
-  if constexpr (MODE == STAGE_ADJOINT)
+  if constexpr (MODE == STAGE_ADJOINT) {
     finish_adjoint<MODEL, MIXED>(a, i, acc);
-  else if constexpr (MODE == STAGE_TANGENT)
+  } else if constexpr (MODE == STAGE_TANGENT) {
     finish_tangent<MODEL, MIXED>(a, i, acc);
-  else
+  } else if constexpr (MODEL == MD_SHEET1D && !MIXED) {
+    // FP64 sheets at eps = 0: each of the n_jt TJ - N padding records added +1
+    const double c0 = a.epsd > 0.0 ? acc[0] : acc[0] - (double)(a.n_jt * Pol::TJ - a.N);
+    finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, &c0);
+  } else {
     finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, acc);
+  }
 }
 
 }  // namespace
