@@ -598,7 +598,7 @@ def run_ours(args, w):
         sysm.get_state_device  # noqa: B018  (API presence)
         qn, pn = qh.numpy(), ph.numpy()
         lib.md_get_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data))
-        ke = K if model == 0 else max(1, min(K, 3))
+        ke = K  # the timed step count (after md_set_state the first step also primes the force)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         binding.check(lib.md_set_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data)), h)
@@ -738,7 +738,7 @@ def run_ensemble(args, w):
         for k in range(len(Ns)):
             qk, pk = ens.get_state(k)
             qh[offs[k]:offs[k + 1]], ph[offs[k]:offs[k + 1]] = qk, pk
-        ke = max(1, min(K, 3))
+        ke = K
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(len(Ns)):
