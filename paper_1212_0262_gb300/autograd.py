@@ -50,3 +50,16 @@ def rollout(q0, p0, eps, system: System, nsteps: int, observable: int = 0, check
     if not torch.is_tensor(eps):
         eps = torch.tensor(float(eps), dtype=torch.float64)
     return Rollout.apply(q0, p0, eps, system, nsteps, observable, checkpoint_every)
+
+
+def rollout_model(q0, p0, eps, model, nsteps: int, dt: float, observable: int = 0, precision: str = "fp64",
+                  checkpoint_every: int = 20):
+    """Rollout by model: a context of `model` with N taken from q0 (dim*N elements) and
+    time step dt is made for the call; the gradient flows to q0, p0 and eps."""
+    from . import system as S
+
+    m = S._model(model)
+    n = int(q0.numel()) // {2: 2, 3: 3}.get(m, 1)
+    e = float(eps.detach()) if torch.is_tensor(eps) else float(eps)
+    with System(m, n, e, float(dt), 0, precision=precision) as s:
+        return rollout(q0, p0, eps, s, nsteps, observable, checkpoint_every)

@@ -148,3 +148,22 @@ def test_reverse_stages_refuse_what_has_no_derivative():
         t, _, _ = _sys(model, 64)
         with pytest.raises(RuntimeError, match="HMF and Ring"):
             t.grad(3, 1, 2)
+
+
+@pytest.mark.parametrize("model", [1, 2, 3])
+def test_rollout_by_model_matches_md_grad(model):
+    """rollout_model(q0, p0, eps, model, nsteps, dt): the context is made for the call;
+    value and gradients equal md_grad on the same state."""
+    from paper_1212_0262_gb300.autograd import rollout_model
+
+    N = 300
+    s, q, p = _sys(model, N)
+    val, gq, gp, ge = s.grad(8, 0, 3)
+    q0 = torch.tensor(q, requires_grad=True)
+    p0 = torch.tensor(p, requires_grad=True)
+    eps = torch.tensor(EPS[model], dtype=torch.float64, requires_grad=True)
+    out = rollout_model(q0, p0, eps, model, 8, DT[model], 0, checkpoint_every=3)
+    out.backward()
+    assert out.item() == val
+    assert np.array_equal(q0.grad.numpy(), gq) and np.array_equal(p0.grad.numpy(), gp)
+    assert eps.grad.item() == ge
