@@ -113,7 +113,7 @@ def parse():
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
     dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "sheet1d": (20, 3), "ensemble": (20, 3),
-            "adjoint": (1, 0)}[a.workload]
+            "adjoint": (1, 3)}[a.workload]
     if a.steps is None:
         a.steps = dflt[0]
     if a.warmup is None:
