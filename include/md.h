@@ -143,7 +143,9 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "rsqrt_offload"    symmetric FP32 Ring kernel: 0 (default), 1 or 2 of the 8 pair-halves per
  *                      16x8 block take 1/sqrt on the FMA pipe (bit-pattern seed, two cubic
  *                      steps) instead of the SFU; measured slower on GB300, kept for study
- *   "sym_threads"      symmetric FP32 Ring kernel CTA shape: 128 (default), 256 or 768
+ *   "sym_threads"      symmetric FP32 Ring kernel CTA shape: 128 (default: 4 16-row blocks per
+ *                      warp, registers for 4 CTAs per SM), 256 or 768 (256 threads, 2 blocks
+ *                      per warp, registers for 2 or 3 CTAs per SM)
  *   "step_graphs"      md_step replays its steps after the first from captured CUDA
  *                      graphs of 8 steps (1, default) or launches every stage (0).
  * MD_EINVAL for an unknown key or value. */

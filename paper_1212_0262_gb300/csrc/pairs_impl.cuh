@@ -1642,7 +1642,7 @@ __device__ __forceinline__ void write_tc_pad(void *mirror, int64_t i) {
   for (int k = 0; k < 8; k++) m[k] = m[64 + k] = 0.f;
 }
 
-template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 3, int OFFR_ = 0>
+template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 4, int OFFR_ = 0>
 struct RingTC {
   static constexpr int OFFR = OFFR_;          // symmetric tiles: (m-block, half) items per n-block
                                               // whose rsqrt runs on the FMA pipe (rsqrt2_fma)
