@@ -685,9 +685,9 @@ struct GravF64 {
 // ------------------------------------------------------------ forward 3D FP32
 // f_i = -(1/N) sum_j r_ij s^(-3/2), s = |r_ij|^2 + eps; per pair 11 FP32 operations
 // and one rsqrt.  Accumulators 0, 1, 2 = x, y, z sums of r s^(-3/2).
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 4>
 struct Grav3DMixed {
-  static constexpr int THREADS = NT, MINB = 4;
+  static constexpr int THREADS = NT, MINB = MINB_;  // CTA size and CTAs per SM of the register budget
   using ColT = float;
   static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_GRAV3D, true, false>::value;
   static constexpr bool MASK = false;
@@ -895,9 +895,9 @@ struct Grav3DF64 {
 // (the FP32 difference of two floats is zero only for equal floats, so its sign is
 // their order), summed exactly (integers below 2^24 per tile); eps > 0:
 // d / sqrt(d^2 + eps) with one rsqrt.  One accumulator.
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 4>
 struct SheetMixed {
-  static constexpr int THREADS = NT, MINB = 4;
+  static constexpr int THREADS = NT, MINB = MINB_;  // CTA size and CTAs per SM of the register budget
   using ColT = float;
   static constexpr int R = R_, TJ = TJ_, NACC = 1, JB = RecordBytes<MD_SHEET1D, true, false>::value;
   static constexpr bool MASK = false;  // the self term is zero in both forms

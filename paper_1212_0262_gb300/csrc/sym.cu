@@ -305,7 +305,8 @@ int sym_dispatch(md_ctx *c, PairArgs a) {
     if constexpr (MIXED) return launch_sym<Grav3DMixed<4, 256, MODE>, MODEL, true, MODE>(c, a);
     else return launch_sym<Grav3DF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
   } else if constexpr (MODEL == MD_SHEET1D) {
-    if constexpr (MIXED) return launch_sym<SheetMixed<8, 256, MODE>, MODEL, true, MODE>(c, a);
+    // registers for 5 CTAs per SM (96, no spills): 1.4% faster than for 4 at N = 262,144
+    if constexpr (MIXED) return launch_sym<SheetMixed<8, 256, MODE, 5>, MODEL, true, MODE>(c, a);
     else return launch_sym<SheetF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
   } else if constexpr (!MIXED) {
     // 4 rows per thread: the column butterflies' FP64 adds are shared by twice the pairs
