@@ -816,6 +816,9 @@ def run_adjoint(args, w):
     N, nsteps, K = w["N"], 100, 20
     s = System(2, N, w["eps"], w["dt"], w["seed"], precision=args.prec)
     s.set_stream(stream)
+    for kv in args.tune:
+        k, v = kv.split("=")
+        s.set_tuning(k, int(v))
     for _ in range(args.warmup):
         s.grad(2, 0, 1)
     sampler = ClockSampler(device_uuid(local))

@@ -3,6 +3,7 @@
 // policies (tile bodies) and epilogues.  See pairs.cu for the method.
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "md_internal.cuh"
 
@@ -130,6 +131,17 @@ __device__ __forceinline__ void write_pad3(void *mirror, int64_t i) {
 inline bool grav_tc(const md_ctx *c) {
   return c->model == MD_GRAV2D && c->prec == MD_MIXED && c->pt.grav_tc && c->pt.r_mixed == 8 && !c->pt.rcp_off;
 }
+
+// CTAs per SM that the one-sided stream-K kernel's register budget is set for: a
+// policy's STREAMK_MINB when it declares one, else 1 (the compiler's choice).
+template <class P, class = void>
+struct StreamkMinBlocks {
+  static constexpr int value = 1;
+};
+template <class P>
+struct StreamkMinBlocks<P, std::void_t<decltype(P::STREAMK_MINB)>> {
+  static constexpr int value = P::STREAMK_MINB;
+};
 
 struct PairArgs {
   const void *mirror_in;
@@ -1170,8 +1182,9 @@ struct RingMixedAdj {
 
 // ------------------------------------------------------------ adjoint 2D FP32
 // accumulators: 0,1 = force (x,y); 2,3 = J v (x,y) without the -2/N factor; 4,5 = d/deps
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 1>
 struct GravMixedAdj {
+  static constexpr int STREAMK_MINB = MINB_;  // register budget of the one-sided kernel
   static constexpr int R = R_, TJ = TJ_, NACC = 6, JB = RecordBytes<MD_GRAV2D, true, true>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;  // rows finished per thread
