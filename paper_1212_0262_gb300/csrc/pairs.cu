@@ -442,13 +442,13 @@ int reverse_pair_launch(md_ctx *c, PairArgs a) {
   const bool mixed = c->prec == MD_MIXED;
   switch (c->model) {
   case MD_RING:
-    if (mixed) return launch_streamk<RingMixedAdj<4, 256, MODE>, MD_RING, true, MODE>(c, a);
+    if (mixed) return launch_streamk<RingMixedAdj<4, 256, MODE, 3>, MD_RING, true, MODE>(c, a);  // 160 registers
     return launch_streamk<RingF64Adj<2, 128, MODE>, MD_RING, false, MODE>(c, a);
   case MD_GRAV3D:
-    if (mixed) return launch_streamk<Grav3DMixedAdj<2, 256, MODE>, MD_GRAV3D, true, MODE>(c, a);
+    if (mixed) return launch_streamk<Grav3DMixedAdj<2, 256, MODE, 4>, MD_GRAV3D, true, MODE>(c, a);  // 128
     return launch_streamk<Grav3DF64Adj<2, 128, MODE>, MD_GRAV3D, false, MODE>(c, a);
   case MD_SHEET1D:
-    if (mixed) return launch_streamk<SheetMixedAdj<4, 256, MODE>, MD_SHEET1D, true, MODE>(c, a);
+    if (mixed) return launch_streamk<SheetMixedAdj<4, 256, MODE, 4>, MD_SHEET1D, true, MODE>(c, a);  // 124
     return launch_streamk<SheetF64Adj<2, 128, MODE>, MD_SHEET1D, false, MODE>(c, a);
   default:
     // registers for 5 CTAs per SM (96, no spills; 130 and 3 CTAs otherwise): 2% faster gradients

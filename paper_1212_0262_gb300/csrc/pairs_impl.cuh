@@ -1119,8 +1119,9 @@ struct SheetF64 {
 
 // ------------------------------------------------------------ adjoint Ring FP32
 // accumulators: 0 = sum S dd^-3/2 (force), 1 = sum G w (J v), 2 = sum S dd^-5/2 (d/deps)
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 1>
 struct RingMixedAdj {
+  static constexpr int STREAMK_MINB = MINB_;  // register budget of the one-sided kernel
   static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_RING, true, true>::value;
   static constexpr bool MASK = true;
   static constexpr int NR = R;  // rows finished per thread
@@ -1264,8 +1265,9 @@ struct GravMixedAdj {
 // ------------------------------------------------------------ adjoint 3D FP32
 // accumulators: 0-2 = force sums of r s^(-3/2); 3-5 = J w sums of w s^(-3/2) - 3 r (r.w) s^(-5/2)
 // (w = lambda_i - lambda_j); 6-8 = d/deps sums of r s^(-5/2)
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 1>
 struct Grav3DMixedAdj {
+  static constexpr int STREAMK_MINB = MINB_;  // register budget of the one-sided kernel
   static constexpr int R = R_, TJ = TJ_, NACC = 9, JB = RecordBytes<MD_GRAV3D, true, true>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;
@@ -1399,8 +1401,9 @@ struct Grav3DF64Adj {
 // ------------------------------------------------------------ adjoint sheets FP32 (eps > 0)
 // accumulators: 0 = force sum of d s^(-1/2); 1 = J w sum of s^(-3/2) w (times eps in the
 // epilogue); 2 = d/deps sum of d s^(-3/2); s = d^2 + eps
-template <int R_, int TJ_, int MODE>
+template <int R_, int TJ_, int MODE, int MINB_ = 1>
 struct SheetMixedAdj {
+  static constexpr int STREAMK_MINB = MINB_;  // register budget of the one-sided kernel
   static constexpr int R = R_, TJ = TJ_, NACC = 3, JB = RecordBytes<MD_SHEET1D, true, true>::value;
   static constexpr bool MASK = false;
   static constexpr int NR = R;
