@@ -105,6 +105,10 @@ void md_free(md_ctx *ctx);
  * context when ctx is NULL.  Never NULL; owned by the library. */
 const char *md_last_error(const md_ctx *ctx);
 
+/* Status code (MD_*) of the last failing call made by the calling thread (MD_OK if
+ * none has failed): for calls that return no status, such as md_init returning NULL. */
+int md_last_status(void);
+
 /* MD_FP64 or MD_MIXED.  Takes effect for the next md_step / md_force / md_grad. */
 int md_set_precision(md_ctx *ctx, int precision);
 

@@ -39,6 +39,7 @@ _SIGS = {
     "md_init": (_P, [_c.c_int, _c.c_int64, _c.c_double, _c.c_double, _c.c_uint64]),
     "md_free": (None, [_P]),
     "md_last_error": (_c.c_char_p, [_P]),
+    "md_last_status": (_c.c_int, []),
     "md_set_precision": (_c.c_int, [_P, _c.c_int]),
     "md_set_stream": (_c.c_int, [_P, _P]),
     "md_set_dt": (_c.c_int, [_P, _c.c_double]),

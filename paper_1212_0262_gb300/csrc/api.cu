@@ -21,6 +21,7 @@
 namespace {
 
 thread_local std::string g_err;
+thread_local int g_status = 0;  // status code of this thread's last failure
 std::mutex g_alloc_mu;
 void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
@@ -33,6 +34,7 @@ int fail_global(int code, const char *fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   g_err = buf;
+  g_status = code;
   return code;
 }
 
@@ -48,6 +50,7 @@ int set_err(md_ctx *c, int code, const char *fmt, ...) {
   va_end(ap);
   if (c) c->err = buf;
   g_err = buf;
+  g_status = code;
   return code;
 }
 
@@ -129,6 +132,8 @@ void yoshida_coefficients(double c[4]) {
 extern "C" {
 
 const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int md_last_status(void) { return g_status; }
 
 int md_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user) {
   if ((alloc == nullptr) != (free_fn == nullptr))

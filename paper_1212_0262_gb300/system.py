@@ -60,7 +60,7 @@ class System:
         self._dt = float(dt)
         h = lib.md_init(self.model, self.N, float(eps), float(dt), int(seed) & (2**64 - 1))
         if not h:
-            raise B.MDError(B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
+            raise B.MDError(lib.md_last_status() or B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
         self._h = ctypes.c_void_p(h)
         self.set_precision(precision)
 
@@ -218,7 +218,7 @@ class Ensemble:
         h = lib.md_batch_init(self.nsys, _ptr(self.models), _ptr(self.Ns), _ptr(self._eps), _ptr(self._dts),
                               _ptr(self._seeds))
         if not h:
-            raise B.MDError(B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
+            raise B.MDError(lib.md_last_status() or B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
         self._h = ctypes.c_void_p(h)
         self.set_precision(precision)
 

@@ -47,6 +47,7 @@ def test_invalid_arguments_fail_before_touching_the_device(libs):
                  (B.MD_HMF, 10, 0.0, float("inf"), 1)]:
         assert not lib.md_init(*args)
         assert lib.md_last_error(None)
+        assert lib.md_last_status() == B.MD_EINVAL
     assert lib.md_set_allocator(ctypes.c_void_p(1), None, None) == B.MD_EINVAL
     assert lib.md_set_precision(None, 0) == B.MD_EINVAL
     assert lib.md_step(None, 1) == B.MD_EINVAL
