@@ -261,11 +261,12 @@ int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(v
  *   stream: cudaStream_t the work is queued on (asynchronous; no host sync)
  * Allocates nothing: its scratch is one file-scope device array of about 1.6 MB
  * that every GPU loading libmd holds until the process exits.  The first call
- * on a device looks up that array's device address (make this first call before
- * any stream capture).  All calls share the array, which keeps the last call's
- * contents (the parts that must start at zero are cleared on the stream at each
- * call), so calls that overlap on the GPU -- on different streams, or from
- * different host threads -- race and give wrong results; serialise them. */
+ * on a device looks up that array's device address and creates an event (make this
+ * first call before any stream capture).  All calls share the array; each call waits
+ * on its stream for the previous call on the device (that event) and records it, so
+ * calls on different streams or from different host threads run one after another
+ * on the GPU.  Inside a stream capture the wait is left out: calls captured into
+ * graphs that may run concurrently must be ordered by the caller. */
 int md_potential_noalloc(int model, int64_t N, double eps, const double *q, double *V, void *stream);
 
 /* Wait for all work queued on the context's stream. */

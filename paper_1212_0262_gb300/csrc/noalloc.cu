@@ -34,10 +34,14 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 int g_nsm[kMaxDevices] = {};
+// Completion of the last call queued on each device: every call waits for it on its
+// own stream before touching the scratch, so calls on different streams or from
+// different threads run one after another on the GPU (an event holds no device memory).
+cudaEvent_t g_done[kMaxDevices] = {};
 
-// Once per device, with that device current: the scratch's device address.
+// Once per device, with that device current: the scratch's device address and the
+// ordering event.  The caller holds g_mu.
 int setup(int dev, double **addr, int *nsm) {
-  std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -49,6 +53,11 @@ int setup(int dev, double **addr, int *nsm) {
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
       set_err(nullptr, MD_ECUDA, "md_potential_noalloc: device attribute: %s", cudaGetErrorString(e));
+      return MD_ECUDA;
+    }
+    e = cudaEventCreateWithFlags(&g_done[dev], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      set_err(nullptr, MD_ECUDA, "md_potential_noalloc: event: %s", cudaGetErrorString(e));
       return MD_ECUDA;
     }
     g_addr[dev] = (double *)p;
@@ -77,9 +86,18 @@ extern "C" int md_potential_noalloc(int model, int64_t N, double eps, const doub
   if (dev < 0 || dev >= kMaxDevices) return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: device %d", dev);
   double *base = nullptr;
   int nsm = 0;
+  std::lock_guard<std::mutex> lk(g_mu);  // one call enqueues at a time, in host order
   int rc = setup(dev, &base, &nsm);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  // Under stream capture an event recorded outside it cannot be waited on: the
+  // captured graph's own order is the caller's to keep.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: %s", cudaGetErrorString(e));
+  const bool ordered = cap == cudaStreamCaptureStatusNone;
+  if (ordered && (e = cudaStreamWaitEvent(st, g_done[dev], 0)) != cudaSuccess)
+    return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: wait: %s", cudaGetErrorString(e));
   double *unit_sums = base;
   double2 *ag = (double2 *)(base + kUnitSums);
   double *partials = base + kUnitSums + kHalfAngles;
@@ -93,5 +111,7 @@ extern "C" int md_potential_noalloc(int model, int64_t N, double eps, const doub
   if (e != cudaSuccess) return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: memset: %s", cudaGetErrorString(e));
   rc = potential_with_scratch(st, nsm, kMaxCtas, model, N, eps, q, unit_sums, ag, partials, sums, ticket, V);
   if (rc) return set_err(nullptr, rc, "md_potential_noalloc: launch: %s", cudaGetErrorString(cudaGetLastError()));
+  if (ordered && (e = cudaEventRecord(g_done[dev], st)) != cudaSuccess)
+    return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: record: %s", cudaGetErrorString(e));
   return MD_OK;
 }

@@ -70,3 +70,54 @@ def test_noalloc_alternating_models_keep_agreeing():
         assert abs(v_dev.item() - va) <= 1e-12 * abs(va)
         assert _noalloc(1, 70, 0.01, qb_dev, v_dev, stream) == 0
         torch.cuda.synchronize()
+
+
+def test_noalloc_calls_on_two_streams_and_threads_do_not_race():
+    """Calls queued on two streams without any synchronisation between them, and from
+    two host threads, share the static scratch: each waits on the GPU for the previous
+    call, so every value equals md_energy's."""
+    import threading
+
+    cases = [(2, 65536, 1e-4, 11), (1, 4097, 0.01, 12)]
+    refs, qs = [], []
+    for model, N, eps, seed in cases:
+        q, p = inputs.default_state(model, N, seed)
+        with System(model, N, eps, 0.01, 1) as s:
+            s.set_state(q, p)
+            refs.append(s.energy()[1])
+        qs.append(torch.from_numpy(np.ascontiguousarray(q)).cuda())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out = torch.full((2, 16), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    for k in range(16):
+        for c, (model, N, eps, _) in enumerate(cases):
+            assert _noalloc(model, N, eps, qs[c], out[c, k:k + 1], streams[c]) == 0
+    torch.cuda.synchronize()
+    for c in range(2):
+        v = out[c].cpu().numpy()
+        assert np.all(np.abs(v - refs[c]) <= 1e-12 * abs(refs[c])), (c, v, refs[c])
+
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(c):
+        model, N, eps, _ = cases[c]
+        try:
+            for k in range(16):
+                rc = _noalloc(model, N, eps, qs[c], out[c, k:k + 1], streams[c])
+                if rc:
+                    errors.append((c, rc))
+        except Exception as e:  # reported below
+            errors.append((c, repr(e)))
+
+    ts = [threading.Thread(target=worker, args=(c,)) for c in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join(timeout=120)
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for c in range(2):
+        v = out[c].cpu().numpy()
+        assert np.all(np.abs(v - refs[c]) <= 1e-12 * abs(refs[c])), (c, v, refs[c])
