@@ -616,16 +616,23 @@ def run_ours(args, w):
         lib.md_get_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data))
         ke = K  # the timed step count (after md_set_state the first step also primes the force)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        tp = [time.perf_counter()]
         binding.check(lib.md_set_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data)), h)
+        tp.append(time.perf_counter())
         binding.check(lib.md_step(h, ke), h)
+        binding.check(lib.md_synchronize(h), h)
+        tp.append(time.perf_counter())
         kk, vv = ctypes.c_double(), ctypes.c_double()
         binding.check(lib.md_energy(h, ctypes.byref(kk), ctypes.byref(vv)), h) if model == 0 else None
+        tp.append(time.perf_counter())
         binding.check(lib.md_get_state(h, ctypes.c_void_p(qn.ctypes.data), ctypes.c_void_p(pn.ctypes.data)), h)
-        el = time.perf_counter() - t0
+        tp.append(time.perf_counter())
+        el = tp[-1] - tp[0]
         e2e = {"value": (N * ke if model == 0 else 3 * N * N * ke) / el, "unit": w["unit"],
                "h2d_bytes_per_step": 2 * 8 * n / ke, "d2h_bytes_per_step": (2 * 8 * n + (16 if model == 0 else 0)) / ke,
-               "steps": ke, "note": "md_set_state(host) + md_step + md_energy + md_get_state(host), wall clock"}
+               "steps": ke, "note": "md_set_state(host) + md_step + md_energy + md_get_state(host), wall clock",
+               "parts_ms": {k: 1e3 * (tp[i + 1] - tp[i]) for i, k in
+                            enumerate(("set_state", "step", "energy", "get_state"))}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
