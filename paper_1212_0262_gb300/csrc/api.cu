@@ -367,7 +367,7 @@ int middle_step(md_ctx *c, const double *k, double h) {
 
 StepGraphKey step_key_of(const md_ctx *c, double h) {
   StepGraphKey key;
-  memset(&key, 0, sizeof key);
+  memset((void *)&key, 0, sizeof key);  // padding bytes too: keys are compared with memcmp
   key.model = c->model;
   key.prec = c->prec;
   key.N = c->N;
