@@ -57,10 +57,27 @@ __global__ void half_angle_kernel(const double *__restrict__ q, int64_t N, doubl
   }
 }
 
+// m * s as a mantissa in [1, 2) and a power of two added to e: a positive normal m
+// times a positive normal s keeps an exact binary exponent, and rescaling by a
+// power of two is exact.  Integer-pipe work only, beside the FP64 multiply.
+__device__ __forceinline__ double mul_renorm(double m, double s, int &e) {
+  const double r = m * s;
+  const int hi = __double2hiint(r);
+  e += ((hi >> 20) & 0x7ff) - 1023;
+  return __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(r));
+}
+
 // One tile pair (ti <= tj) of the i<j potential sum.
 //  Ring: -(1/(2N)) sum d^(-1/2), d = sin^2((ti-tj)/2) + eps/2  (Eq. 1, with
 //        1 - cos d + eps = 2 d)
 //  2D:   (1/N) sum log(|r_ij|^2 + eps)                        (Eq. 3)
+// The 2D sum of logarithms of one thread's row of the tile is the logarithm of the
+// product of its s = |r|^2 + eps values: the product is kept as m 2^e (m in [1, 2),
+// renormalised after every factor, so it can neither overflow nor underflow while
+// every s is a normal double), and log m + e ln 2 replaces up to 256 logarithms.
+// Relative rounding of m: at most one unit roundoff per factor, i.e. about
+// 2.8e-14 absolute in the row's sum of 256 logarithms, the size of the rounding of
+// the sum of the logarithms themselves.
 // The prefactor is applied on the host.
 template <int MODEL>
 __global__ void __launch_bounds__(NT) potential_tiles_kernel(const double *__restrict__ q,
@@ -82,15 +99,21 @@ __global__ void __launch_bounds__(NT) potential_tiles_kernel(const double *__res
     int kbeg = 0;
     if (ti == tj) kbeg = threadIdx.x + 1;  // j > i inside the diagonal tile
     int kend = (int)((N - j0) < PT ? (N - j0) : PT);
-    for (int k = kbeg; k < kend; k++) {
-      const double2 o = sj[k];
-      if (MODEL == MD_RING) {
+    if constexpr (MODEL == MD_RING) {
+      for (int k = kbeg; k < kend; k++) {
+        const double2 o = sj[k];
         double sh = fma(me.x, o.y, -(me.y * o.x));
         s += rsqrt_nr(fma(sh, sh, epsd));
-      } else {
-        double dx = me.x - o.x, dy = me.y - o.y;
-        s += log(fma(dx, dx, fma(dy, dy, epsd)));
       }
+    } else {
+      double m = 1.0;
+      int e = 0;
+      for (int k = kbeg; k < kend; k++) {
+        const double2 o = sj[k];
+        const double dx = me.x - o.x, dy = me.y - o.y;
+        m = mul_renorm(m, fma(dx, dx, fma(dy, dy, epsd)), e);
+      }
+      s = log(m) + (double)e * 0.69314718055994530942;
     }
   }
   __shared__ double2 red[NT / 32];
@@ -132,7 +155,10 @@ __global__ void __launch_bounds__(NT) potential3d_tiles_kernel(const double *__r
 }
 
 // 1D sheets: one tile pair (ti <= tj) of sum_{i<j} |x_i - x_j| (eps = 0) or
-// sqrt((x_i - x_j)^2 + eps); the prefactor 1/N is applied at the end.
+// sqrt((x_i - x_j)^2 + eps); the prefactor 1/N is applied at the end.  The two
+// forms are separate instantiations: with the choice inside the loop the compiler
+// predicates the square root into every iteration of the eps = 0 sum.
+template <bool SOFT>
 __global__ void __launch_bounds__(NT) potential_sheet_tiles_kernel(const double *__restrict__ q, int64_t N,
                                                                     int ntiles, double eps, double *unit_sums) {
   const int ti = blockIdx.x, tj = blockIdx.y;
@@ -152,7 +178,10 @@ __global__ void __launch_bounds__(NT) potential_sheet_tiles_kernel(const double 
     const int kend = (int)((N - j0) < PT ? (N - j0) : PT);
     for (int k = kbeg; k < kend; k++) {
       const double d = x - sx[k];
-      s += eps > 0.0 ? sqrt(fma(d, d, eps)) : fabs(d);
+      if constexpr (SOFT)
+        s += sqrt(fma(d, d, eps));
+      else
+        s += fabs(d);
     }
   }
   __shared__ double2 red[NT / 32];
@@ -210,7 +239,10 @@ int potential_with_scratch(cudaStream_t st, int nsm, int grid_cap, int model, in
     } else if (model == MD_GRAV3D) {
       potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
     } else if (model == MD_SHEET1D) {
-      potential_sheet_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
+      if (eps > 0.0)
+        potential_sheet_tiles_kernel<true><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
+      else
+        potential_sheet_tiles_kernel<false><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, N, ntiles, eps, unit_sums);
     } else {
       potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, st>>>(q, nullptr, N, ntiles, eps, unit_sums);
     }
@@ -281,7 +313,10 @@ int pair_potential_fp64(md_ctx *c, double *d_out) {
   } else if (c->model == MD_GRAV3D) {
     potential3d_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
   } else if (c->model == MD_SHEET1D) {
-    potential_sheet_tiles_kernel<<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
+    if (c->eps > 0.0)
+      potential_sheet_tiles_kernel<true><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
+    else
+      potential_sheet_tiles_kernel<false><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, N, ntiles, c->eps, unit_sums);
   } else {
     potential_tiles_kernel<MD_GRAV2D><<<dim3(ntiles, ntiles), NT, 0, c->stream>>>(c->q, nullptr, N, ntiles, c->eps,
                                                                                   unit_sums);
