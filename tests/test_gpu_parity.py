@@ -160,6 +160,26 @@ def test_energy_parity(model, N):
     assert abs(V - Vo) <= 1e-12 * max(abs(Vo), 1.0), (V, Vo)
 
 
+@pytest.mark.parametrize("eps", [1e-3, 1e-14])
+def test_2d_potential_over_a_wide_range_of_separations(eps):
+    """The 2D potential takes each thread row's logarithms as the logarithm of a
+    renormalised product.  Radii log-uniform in [1e-7, 1e5] (factors s = r^2 + eps
+    over 24 decades, products far outside the double range) keep the bound, taken
+    against sum_{i<j} |log s_ij| / N since the logarithms have both signs."""
+    N = 3000
+    u = inputs.uniform(51, 0, 2 * N)
+    rad = 10.0 ** (-7.0 + 12.0 * u[:N])
+    ang = 2.0 * np.pi * u[N:]
+    q = np.concatenate([rad * np.cos(ang), rad * np.sin(ang)])
+    with System(2, N, eps, 0.01, 1, precision="fp64") as s:
+        s.set_state(q, np.zeros_like(q))
+        _, V = s.energy()
+    Vo = ora.potential(2, q, eps)
+    x, y = q[:N], q[N:]
+    scale = sum(np.abs(np.log((x[i] - x[i + 1:]) ** 2 + (y[i] - y[i + 1:]) ** 2 + eps)).sum() for i in range(N)) / N
+    assert abs(V - Vo) <= 1e-12 * scale, (V, Vo, scale)
+
+
 @pytest.mark.parametrize("model", [0, 1])
 def test_magnetization_parity(model):
     s, q, p = _sys(model, 10001)
