@@ -141,9 +141,10 @@ int md_set_eps(md_ctx *ctx, double eps);
  *                      FP64 (r_fp64 2): every unordered pair evaluated once and added to
  *                      both particles (Newton's third law; the paper evaluates both
  *                      orders, Sec. 3.2).  Needs column-partial storage of about
- *                      N^2 / 2^16 floats (FP32 Ring), N^2 / 2^18 floats (FP32 2D) or
- *                      N^2 / 2^16 doubles (FP64); above 4 GiB of it the one-sided kernel
- *                      runs.
+ *                      N^2 / 128 bytes (Ring, FP32 or FP64), N^2 / 256 (FP32 2D),
+ *                      N^2 / 64 (FP64 2D), 3 N^2 / 256 (FP32 3D) or N^2 / 512 (FP32
+ *                      sheets); above 16 GiB of it (N beyond about 1.48e6 for Ring,
+ *                      2.1e6 for FP32 2D) the one-sided kernel runs.
  *   "rsqrt_offload"    symmetric FP32 Ring kernel: 0 (default), 1 or 2 of the 8 pair-halves per
  *                      16x8 block take 1/sqrt on the FMA pipe (bit-pattern seed, two cubic
  *                      steps) instead of the SFU; measured slower on GB300, kept for study

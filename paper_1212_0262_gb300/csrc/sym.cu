@@ -43,7 +43,7 @@
 
 namespace {
 
-constexpr size_t kSymMaxColBytes = (size_t)4 << 30;
+constexpr size_t kSymMaxColBytes = (size_t)16 << 30;  // Ring and 2D at N = 1e6 fit
 
 struct SymArgs {
   int m;             // TI / TJ

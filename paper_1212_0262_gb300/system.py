@@ -126,6 +126,8 @@ class System:
         return q, p
 
     def set_state_device(self, q_ptr: int, p_ptr: int) -> None:
+        """Device-to-device copy queued on the context's stream: whatever writes q and p
+        must be ordered before it (the same stream through set_stream, or a synchronize)."""
         self._chk(B.load().md_set_state_device(self._h, ctypes.c_void_p(q_ptr), ctypes.c_void_p(p_ptr)))
 
     def get_state_device(self, q_ptr: int, p_ptr: int) -> None:

@@ -119,6 +119,25 @@ def test_hmf_meanfield_equals_pairwise(ora, N):
     assert abs(v_mf - v_pw) <= 1e-13 * max(1.0, N)
 
 
+@pytest.mark.parametrize("N,alpha", [(1, 0.3), (1001, 2.5e-3), (4096, 1.7e-3), (50_000, 1e-4)])
+def test_hmf_closed_form_magnetization_of_an_arithmetic_progression(ora, N, alpha):
+    """Eq. 7 for theta_i = alpha i: the geometric sum of e^{i alpha k} gives
+    M = e^{i alpha (N-1)/2} sin(alpha N/2) / (N sin(alpha/2)); the mean-field force of
+    Eq. 6 is then f_i = cos(theta_i) My - sin(theta_i) Mx (sign: particles are pulled
+    towards the direction of M).  The same closed form checks the GPU path at
+    particle counts past 2^31."""
+    q = alpha * np.arange(N, dtype=np.float64)
+    amp = math.sin(alpha * N / 2) / (N * math.sin(alpha / 2))
+    mx, my = math.cos(alpha * (N - 1) / 2) * amp, math.sin(alpha * (N - 1) / 2) * amp
+    ox, oy = ora.magnetization(q)
+    assert abs(ox - mx) < 1e-14 and abs(oy - my) < 1e-14
+    f = ora.force(ora.HMF, q)
+    assert np.max(np.abs(f - (np.cos(q) * my - np.sin(q) * mx))) < 1e-14
+    # towards M: a particle a quarter turn behind M is pulled forward
+    phi = math.atan2(my, mx)
+    assert ora.force(ora.HMF, np.append(q, phi - math.pi / 2))[-1] > 0
+
+
 @pytest.mark.parametrize("model,eps", [(0, 0.0), (1, 0.01), (1, 1.0), (2, 1e-3), (2, 0.5), (3, 1e-3), (3, 0.5),
                                        (4, 1e-3), (4, 0.5)])
 def test_force_is_minus_gradient_of_potential(ora, model, eps):
