@@ -149,9 +149,9 @@ def test_symmetric_ring_rsqrt_on_fma_pipe(N, off):
 
 
 def test_symmetric_falls_back_to_one_sided_beyond_the_column_cap():
-    """Ring N = 1,048,576 needs 7.6 GB of column partials, beyond the 4 GiB cap: the
+    """Ring N = 1,572,864 needs 19.3 GB of column partials, beyond the 16 GiB cap: the
     one-sided tensor-core kernel runs instead, with the same error bound."""
-    N = 1 << 20
+    N = 3 << 19
     s = System(1, N, 0.01, 0.05, 47, precision="mixed")
     assert s.force_kernel == 3  # one-sided, tensor-core products
     q, _ = s.get_state()
