@@ -109,7 +109,9 @@ def parse():
                     help="processes of the oracle legs (0 = every core of this process's affinity set)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--n", type=int, default=None, help="override N (profiling runs on smaller cases)")
+    ap.add_argument("--n", "--particles", dest="n", type=int, default=None,
+                    help="override N (profiling runs on smaller cases); --particles under torchrun, whose "
+                         "own parser takes --n for one of its options")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     a = ap.parse_args()
     dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "sheet1d": (20, 3), "ensemble": (20, 3),

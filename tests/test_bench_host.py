@@ -60,3 +60,18 @@ def test_oracle_gradient_leg_counts_both_passes(bench):
     u, el, d = bench.oracle_grad(w, 0.3, 1, nsteps=4, cores=2)
     n = int(d.split(" particles")[0].split()[-1])
     assert u == 2 * float(n) * n * (6 * 4 + 1) and el > 0 and d.startswith("2 processes")
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Two ranks launched as the multi-GPU bench is: rank 0 alone times the oracle and
+    prints the line; the other rank exits 0 without work."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "29613", "bench.py", "--impl", "reference",
+                        "--gpus", "2", "--workload", "ring", "--steps", "1", "--warmup", "0", "--cpu-cores", "2",
+                        "--particles", "2048"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
