@@ -26,6 +26,9 @@ namespace {
 
 constexpr int NT = kStreamThreads;
 constexpr int UNROLL = 2;  // double2 loads of theta and of p in flight per thread
+// Mixed sums: a thread adds at most kFlush angles' cosines and sines in FP32 before moving
+// them into its FP64 partial, so their rounding does not grow with N / (threads).
+constexpr int kFlush = 256;
 
 struct HmfArgs {
   double *q, *p;
@@ -127,7 +130,12 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
   const int64_t t0 = (int64_t)blockIdx.x * NT + threadIdx.x;
   double2 *q2 = reinterpret_cast<double2 *>(a.q);
   double2 *p2 = reinterpret_cast<double2 *>(a.p);
-  for (int64_t k = t0; k < npairs; k += UNROLL * G) {
+  // blocks of kFlush / 2 double2 pairs per thread; the FP32 sums move into FP64 after each
+  // block (a counter tested inside the loop instead made the stage a fifth slower)
+  const int64_t block = (int64_t)(kFlush / (2 * UNROLL)) * UNROLL * G;
+  for (int64_t kb = t0; kb < npairs; kb += block) {
+  const int64_t kend = kb + block < npairs ? kb + block : npairs;
+  for (int64_t k = kb; k < kend; k += UNROLL * G) {
     double2 qv[UNROLL], pv[UNROLL];
 #pragma unroll
     for (int u = 0; u < UNROLL; u++) {
@@ -150,6 +158,12 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
       }
     }
   }
+  if constexpr (MIXED && MODE == STAGE_KICK_DRIFT) {
+    acd += (double)acf;
+    asd += (double)asf;
+    acf = asf = 0.f;
+  }
+  }
   if ((a.N & 1) && t0 == 0) {
     int64_t i = a.N - 1;
     double th = a.q[i], pp = a.p[i];
@@ -158,9 +172,9 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
     if (MODE != STAGE_FORCE_ONLY) a.p[i] = pp;
   }
   if (MODE == STAGE_KICK_DRIFT) {
-    if (MIXED) {
-      acd = (double)acf;
-      asd = (double)asf;
+    if (MIXED) {  // the odd last particle, if any
+      acd += (double)acf;
+      asd += (double)asf;
     }
     grid_finish(acd, asd, a.partials, a.m_out, a.ticket);
   }
@@ -175,7 +189,10 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
   float acf = 0.f, asf = 0.f;
   double acd = 0.0, asd = 0.0;
   const int64_t G = (int64_t)gridDim.x * NT;
-  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < N; i += G) {
+  const int64_t block = (int64_t)kFlush * G;  // kFlush angles per thread, then the FP64 move
+  for (int64_t ib = (int64_t)blockIdx.x * NT + threadIdx.x; ib < N; ib += block) {
+  const int64_t iend = ib + block < N ? ib + block : N;
+  for (int64_t i = ib; i < iend; i += G) {
     double th = q[i];
     if (MIXED) {
       float s, c;
@@ -191,8 +208,10 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
     }
   }
   if (MIXED) {
-    acd = (double)acf;
-    asd = (double)asf;
+    acd += (double)acf;
+    asd += (double)asf;
+    acf = asf = 0.f;
+  }
   }
   grid_finish(acd, asd, partials, m_out, ticket);
 }
