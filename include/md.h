@@ -88,7 +88,9 @@ typedef struct md_ctx md_ctx;
 typedef struct md_batch md_batch;
 
 /* Create a system of N particles of `model` with softening eps (Ring, 2D, 3D: must
- * be > 0; sheets: >= 0; ignored for HMF but must be >= 0) and time step dt (Sec. 3, Eq. 4),
+ * be >= 1e-30; sheets: 0 or >= 1e-30; ignored for HMF but must be 0 or >= 1e-30; the
+ * floor keeps every softened square distance a normal FP32 number, the precision of
+ * the kernels' divisions and reciprocal seeds) and time step dt (Sec. 3, Eq. 4),
  * on the current CUDA device.  The state is drawn from `seed` with the model's
  * default recipe: water-bag theta~U[-1,1), p~U[-1.2,1.2) (HMF); theta~U[-pi,pi),
  * p~N(0,0.5^2) (Ring); uniform unit disk, p~N(0,0.3^2) per component (2D);
@@ -119,7 +121,7 @@ int md_set_stream(md_ctx *ctx, void *stream);
 /* Change the time step (Sec. 3, Eq. 4).  dt may be negative (backward flow). */
 int md_set_dt(md_ctx *ctx, double dt);
 
-/* Change the softening eps of Eqs. 1 and 3 (> 0 for Ring/2D, >= 0 for HMF). */
+/* Change the softening eps of Eqs. 1 and 3 (the values md_init accepts). */
 int md_set_eps(md_ctx *ctx, double eps);
 
 /* Tuning knobs of the kernels (defaults: r_mixed 8, r_fp64 2, ring_tc 1, symmetric 1,
@@ -258,8 +260,9 @@ int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(v
  *   N:     1 <= N <= 65536 (the size the static scratch holds); larger N is
  *          rejected with MD_EINVAL and a message in md_last_error(NULL)
  *   q:     device, dim*N doubles (layout as md_set_state), read only
- *   V:     device, one double, written
- *   stream: cudaStream_t the work is queued on (asynchronous; no host sync)
+ *   V:     device, one double, written (NaN or infinite if a position is)
+ *   stream: cudaStream_t the work is queued on (asynchronous; no host sync); it must
+ *          belong to the current device (MD_EINVAL otherwise)
  * Allocates nothing: its scratch is one file-scope device array of about 1.6 MB
  * that every GPU loading libmd holds until the process exits.  The first call
  * on a device looks up that array's device address and creates an event (make this
@@ -307,6 +310,12 @@ int md_batch_get_tuning(const md_batch *b, int *r, double *split, int *ctas_per_
  * leave every state unchanged, and keep the fastest.  *best_ms (may be NULL)
  * receives the fastest launch time.  Synchronous. */
 int md_batch_autotune(md_batch *b, double *best_ms);
+/* Forces of every system at its current positions, from one force-only launch of
+ * the kernels md_batch_step runs (same form, precision and tuning): f[s] is a host
+ * array of dim*N[s] doubles for system s, or NULL to skip that system (f itself
+ * must not be NULL).  Minus the gradient of Eq. 1 (Ring) or Eq. 3 (2D).  States are
+ * unchanged.  Synchronous. */
+int md_batch_force(md_batch *b, double *const *f);
 /* K[s], V[s] for every system (host arrays of nsys).  Synchronous. */
 int md_batch_energy(md_batch *b, double *K, double *V);
 /* Host state of system s (dim*N[s] doubles each). */

@@ -72,6 +72,7 @@ _SIGS = {
     "md_batch_set_tuning": (_c.c_int, [_P, _c.c_int, _c.c_double, _c.c_int]),
     "md_batch_get_tuning": (_c.c_int, [_P, _P, _P, _P]),
     "md_batch_autotune": (_c.c_int, [_P, _D]),
+    "md_batch_force": (_c.c_int, [_P, _P]),
     "md_batch_energy": (_c.c_int, [_P, _P, _P]),
     "md_batch_get_state": (_c.c_int, [_P, _c.c_int, _P, _P]),
     "md_batch_set_state": (_c.c_int, [_P, _c.c_int, _P, _P]),

@@ -180,8 +180,9 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
     return nullptr;
   }
   const bool eps0_ok = model == MD_HMF || model == MD_SHEET1D;  // models with no divergence at eps = 0
-  if (!is_finite(eps) || eps < 0.0 || (!eps0_ok && !(eps > 0.0))) {
-    fail_global(MD_EINVAL, "md_init: eps must be finite and %s, got %g", eps0_ok ? ">= 0" : "> 0", eps);
+  if (!eps_valid(model, eps)) {
+    fail_global(MD_EINVAL, "md_init: eps must be finite and %s %g, got %g", eps0_ok ? "0 or >=" : ">=", kEpsMin,
+                eps);
     return nullptr;
   }
   if (!is_finite(dt)) {

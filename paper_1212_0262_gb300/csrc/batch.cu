@@ -983,6 +983,22 @@ int md_batch_step(md_batch *b, int64_t nsteps) {
   return rc;
 }
 
+int md_batch_force(md_batch *b, double *const *f) {
+  if (!b) return set_err(nullptr, MD_EINVAL, "NULL batch");
+  if (!f) return berr(b, MD_EINVAL, "%s", "md_batch_force: NULL array of outputs");
+  int rc = stage(b, STAGE_FORCE_ONLY, 0.0, 0.0);  // every system, the launches md_batch_step runs
+  if (rc) return rc;
+  for (int s = 0; s < b->nsys; s++) {
+    md_ctx *c = b->ctx[s];
+    c->fsal_valid = false;  // c->f now holds this force, not a cached one of md_step
+    if (f[s])
+      B_CUDA(b, cudaMemcpyAsync(f[s], c->f, sizeof(double) * (size_t)(c->dim * c->N), cudaMemcpyDeviceToHost,
+                                b->stream));
+  }
+  B_CUDA(b, cudaStreamSynchronize(b->stream));
+  return MD_OK;
+}
+
 int md_batch_energy(md_batch *b, double *K, double *V) {
   if (!b) return set_err(nullptr, MD_EINVAL, "NULL batch");
   for (int s = 0; s < b->nsys; s++) {

@@ -60,10 +60,15 @@ __global__ void half_angle_kernel(const double *__restrict__ q, int64_t N, doubl
 // m * s as a mantissa in [1, 2) and a power of two added to e: a positive normal m
 // times a positive normal s keeps an exact binary exponent, and rescaling by a
 // power of two is exact.  Integer-pipe work only, beside the FP64 multiply.
-__device__ __forceinline__ double mul_renorm(double m, double s, int &e) {
+// A product that is not a normal double (a NaN or infinite factor, an overflow, or
+// a subnormal or zero factor) has the exponent field 0x7ff or 0; `odd` records it
+// so that the row falls back to the plain sum of logarithms.
+__device__ __forceinline__ double mul_renorm(double m, double s, int &e, unsigned &odd) {
   const double r = m * s;
   const int hi = __double2hiint(r);
-  e += ((hi >> 20) & 0x7ff) - 1023;
+  const int ex = (hi >> 20) & 0x7ff;
+  e += ex - 1023;
+  odd |= (unsigned)(ex - 1) >= 0x7feu;
   return __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(r));
 }
 
@@ -75,6 +80,9 @@ __device__ __forceinline__ double mul_renorm(double m, double s, int &e) {
 // product of its s = |r|^2 + eps values: the product is kept as m 2^e (m in [1, 2),
 // renormalised after every factor, so it can neither overflow nor underflow while
 // every s is a normal double), and log m + e ln 2 replaces up to 256 logarithms.
+// A row with a factor that is not a normal double (a non-finite position, or
+// coincident particles with a subnormal eps) sums its logarithms one by one, so a
+// NaN or infinite position gives a NaN or infinite V.
 // Relative rounding of m: at most one unit roundoff per factor, i.e. about
 // 2.8e-14 absolute in the row's sum of 256 logarithms, the size of the rounding of
 // the sum of the logarithms themselves.
@@ -108,12 +116,21 @@ __global__ void __launch_bounds__(NT) potential_tiles_kernel(const double *__res
     } else {
       double m = 1.0;
       int e = 0;
+      unsigned odd = 0u;
       for (int k = kbeg; k < kend; k++) {
         const double2 o = sj[k];
         const double dx = me.x - o.x, dy = me.y - o.y;
-        m = mul_renorm(m, fma(dx, dx, fma(dy, dy, epsd)), e);
+        m = mul_renorm(m, fma(dx, dx, fma(dy, dy, epsd)), e, odd);
       }
       s = log(m) + (double)e * 0.69314718055994530942;
+      if (odd) {  // a factor outside the normal range: NaN, inf or a tiny s stay exact per pair
+        s = 0.0;
+        for (int k = kbeg; k < kend; k++) {
+          const double2 o = sj[k];
+          const double dx = me.x - o.x, dy = me.y - o.y;
+          s += log(fma(dx, dx, fma(dy, dy, epsd)));
+        }
+      }
     }
   }
   __shared__ double2 red[NT / 32];

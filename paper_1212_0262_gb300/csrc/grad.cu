@@ -144,8 +144,8 @@ extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint
 extern "C" int md_set_eps(md_ctx *c, double eps) {
   if (!c) return set_err(nullptr, MD_EINVAL, "md_set_eps: NULL context");
   const bool eps0_ok = c->model == MD_HMF || c->model == MD_SHEET1D;
-  if (!(eps == eps) || eps - eps != 0.0 || eps < 0.0 || (!eps0_ok && !(eps > 0.0)))
-    return set_err(c, MD_EINVAL, "md_set_eps: eps must be finite and %s", eps0_ok ? ">= 0" : "> 0");
+  if (!eps_valid(c->model, eps))
+    return set_err(c, MD_EINVAL, "md_set_eps: eps must be finite and %s %g", eps0_ok ? "0 or >=" : ">=", kEpsMin);
   c->eps = eps;
   c->fsal_valid = false;    // the cached force depends on eps
   c->mirror_valid = false;  // and the sheet model's padding records do

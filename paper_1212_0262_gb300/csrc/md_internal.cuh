@@ -116,6 +116,20 @@ struct md_ctx {
 
 // ------------------------------------------------------------ host helpers --
 
+// Smallest positive softening accepted.  Every softened square distance
+// |r|^2 + eps (and the Ring's 1 - cos d + eps) is then at least this, a normal
+// number in FP32, the precision in which the FP32 pair kernels divide and the FP64
+// ones take the seeds of their reciprocals and reciprocal square roots.
+constexpr double kEpsMin = 1e-30;
+
+// eps is finite, >= 0, and either 0 (HMF, and the sheets' unsoftened force only)
+// or >= kEpsMin.
+inline bool eps_valid(int model, double eps) {
+  if (!(eps == eps) || eps - eps != 0.0 || eps < 0.0) return false;
+  if (eps == 0.0) return model == MD_HMF || model == MD_SHEET1D;
+  return eps >= kEpsMin;
+}
+
 int set_err(md_ctx *c, int code, const char *fmt, ...);
 int cuda_err(md_ctx *c, cudaError_t e, const char *what);
 void *dev_alloc(size_t bytes);

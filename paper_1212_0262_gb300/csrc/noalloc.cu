@@ -77,13 +77,22 @@ extern "C" int md_potential_noalloc(int model, int64_t N, double eps, const doub
     return set_err(nullptr, MD_EINVAL,
                    "md_potential_noalloc: N = %lld is outside [1, %lld], the size its static scratch holds",
                    (long long)N, (long long)kMaxN);
-  if (!(eps == eps) || eps < 0.0 || (model != MD_HMF && model != MD_SHEET1D && !(eps > 0.0)))
-    return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: bad eps %g", eps);
+  if (!eps_valid(model, eps))
+    return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: bad eps %g (finite; 0 only for HMF and sheets, else >= %g)",
+                   eps, kEpsMin);
   if (!q || !V) return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: NULL pointer");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: device %d", dev);
+  // the scratch address and the ordering event belong to the current device, so the
+  // stream must be one of its streams
+  int sdev = dev;
+  e = cudaStreamGetDevice((cudaStream_t)stream, &sdev);
+  if (e != cudaSuccess) return set_err(nullptr, MD_ECUDA, "md_potential_noalloc: stream device: %s", cudaGetErrorString(e));
+  if (sdev != dev)
+    return set_err(nullptr, MD_EINVAL, "md_potential_noalloc: the stream belongs to device %d, the current device is %d",
+                   sdev, dev);
   double *base = nullptr;
   int nsm = 0;
   std::lock_guard<std::mutex> lk(g_mu);  // one call enqueues at a time, in host order

@@ -266,6 +266,17 @@ class Ensemble:
         self._chk(B.load().md_batch_autotune(self._h, ctypes.byref(ms)))
         return ms.value
 
+    def force(self, systems=None):
+        """Forces of the listed systems (default: all) at their current positions, from
+        one force-only launch of the ensemble kernels; a dict system -> array."""
+        systems = range(self.nsys) if systems is None else [int(s) for s in systems]
+        out = {s: np.empty((2 if self.models[s] == 2 else 1) * int(self.Ns[s])) for s in systems}
+        ptrs = (ctypes.c_void_p * self.nsys)()
+        for s, a in out.items():
+            ptrs[s] = a.ctypes.data
+        self._chk(B.load().md_batch_force(self._h, ptrs))
+        return out
+
     def energy(self):
         k, v = np.empty(self.nsys), np.empty(self.nsys)
         self._chk(B.load().md_batch_energy(self._h, _ptr(k), _ptr(v)))

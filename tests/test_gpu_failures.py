@@ -102,3 +102,41 @@ def test_non_finite_state_is_reported(model):
         assert e.value.code == B.MD_ENONFINITE
         s.set_state(q, p)
         assert np.isfinite(sum(s.energy()))
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("model", [1, 2, 3, 4])
+def test_non_finite_position_is_reported(model, bad):
+    """A NaN or infinite position (not only momentum) makes V non-finite, so md_energy
+    answers MD_ENONFINITE; the 2D potential's renormalised product falls back to the
+    plain sum of logarithms on such a row instead of returning a finite number."""
+    N = 1000
+    eps = {1: 0.01, 2: 1e-3, 3: 1e-3, 4: 0.0}[model]
+    with System(model, N, eps, 0.01, 1) as s:
+        q, p = inputs.default_state(model, N, 5)
+        for i in (0, 517, N - 1):  # first row, a middle row, the last row of the last tile
+            qb = q.copy()
+            qb[i] = bad
+            s.set_state(qb, p)
+            with pytest.raises(MDError) as e:
+                s.energy()
+            assert e.value.code == B.MD_ENONFINITE, (i, str(e.value))
+        s.set_state(q, p)
+        assert np.isfinite(sum(s.energy()))
+
+
+def test_eps_below_the_floor_is_rejected():
+    """Softenings below 1e-30 (where a softened square distance could leave the normal
+    FP32 range the kernels divide in) are refused by md_init and md_set_eps."""
+    for model in (1, 2, 3):
+        with pytest.raises(MDError) as e:
+            System(model, 64, 1e-31, 0.01, 1)
+        assert e.value.code == B.MD_EINVAL
+    with System(2, 64, 1e-30, 0.01, 1) as s:
+        with pytest.raises(MDError):
+            s.set_eps(5e-324)
+        s.set_eps(1e-3)
+    with System(4, 64, 0.0, 0.01, 1) as s:
+        with pytest.raises(MDError):
+            s.set_eps(1e-40)
+        s.set_eps(0.0)

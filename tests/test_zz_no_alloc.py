@@ -2,17 +2,26 @@
 device memory (their GPU memory belongs to a host framework's caching
 allocator, or cudaMalloc's possible device synchronisation is not acceptable in
 their loop).  Its scratch is a static device array, so two calls in a row must
-both agree with md_energy's V, the entry point that allocates its scratch.
+both agree with md_energy's V, the entry point that allocates its scratch, and with
+the FP64 oracle's i<j pair sum (1e-12 relative).
 
 This file is collected last on purpose; it needs nothing from the other tests.
 """
 import ctypes
+import functools
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as ora
 from paper_1212_0262_gb300 import System, binding, inputs
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_potential(model, N, eps, seed):
+    q, _ = inputs.default_state(model, N, seed)
+    return ora.potential(model, q, eps)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +51,8 @@ def test_noalloc_potential_matches_md_energy_twice(model, N, eps):
         torch.cuda.synchronize()
         v = float(v_dev.item())
         assert abs(v - v_ref) <= 1e-12 * max(abs(v_ref), 1.0), (call, v, v_ref)
+    v_ora = _oracle_potential(model, N, eps, 500 + N)
+    assert abs(v - v_ora) <= 1e-12 * max(abs(v_ora), 1.0), (v, v_ora)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -121,3 +132,23 @@ def test_noalloc_calls_on_two_streams_and_threads_do_not_race():
     for c in range(2):
         v = out[c].cpu().numpy()
         assert np.all(np.abs(v - refs[c]) <= 1e-12 * abs(refs[c])), (c, v, refs[c])
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+@pytest.mark.parametrize("model", [1, 2, 3])
+def test_noalloc_potential_of_a_non_finite_position_is_not_finite(model, bad):
+    """A NaN or infinite coordinate gives a V that is not finite (never a finite number
+    that looks valid), and the next call on a good state is right again."""
+    N, eps = 1000, {1: 0.01, 2: 1e-3, 3: 1e-3}[model]
+    q, _ = inputs.default_state(model, N, 21)
+    qb = q.copy()
+    qb[333] = bad
+    stream = torch.cuda.current_stream()
+    v_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert _noalloc(model, N, eps, torch.from_numpy(qb).cuda(), v_dev, stream) == 0
+    torch.cuda.synchronize()
+    assert not np.isfinite(v_dev.item())
+    assert _noalloc(model, N, eps, torch.from_numpy(q).cuda(), v_dev, stream) == 0
+    torch.cuda.synchronize()
+    v_ora = _oracle_potential(model, N, eps, 21)
+    assert abs(v_dev.item() - v_ora) <= 1e-12 * max(abs(v_ora), 1.0)
