@@ -57,7 +57,6 @@ PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1), 4: (4, 0)}
 # per evaluated pair term, and whether each unordered pair is evaluated once.
 #   one-sided Ring: S and sin(d/2) (2 FMA + 2 MUL), dd (FMA), y^2, S y, acc (FMA) -> 8
 #   tensor-core Ring: S and sin(d/2) on the tensor cores -> 4
-#   tensor-core 2D: dx and dy on the tensor cores -> |r|^2 + eps (2 FMA), fx, fy -> 4
 #   one-sided 2D: dx, dy, |r|^2 + eps (2 FMA), fx, fy -> 6
 #   one-sided 3D: dx, dy, dz, |r|^2 + eps (3 FMA), y^3 (2 MUL), fx, fy, fz -> 11
 #   symmetric: + 1 (Ring) / 2 (2D) / 3 (3D) column accumulations per pair term, plus
@@ -68,9 +67,6 @@ PAIR_KERNELS = {
     (1, 5): ("sym_kernel<RingTC<4,256>>", 5.125, 1, True),
     (2, 2): ("streamk_kernel<GravMixed<8,256>>", 6, 1, False),
     (2, 4): ("sym_kernel<GravMixed<8,256>>", 8.25, 1, True),
-    # tensor-core 2D: dx and dy on the tensor cores; symmetric butterfly adds 7 per 32 terms
-    (2, 3): ("streamk_kernel<GravTC<4,256>>", 4, 1, False),
-    (2, 5): ("sym_kernel<GravTC<4,256>>", 6.22, 1, True),
     (3, 2): ("streamk_kernel<Grav3DMixed<4,256>>", 11, 1, False),
     (3, 4): ("sym_kernel<Grav3DMixed<4,256>>", 14.75, 1, True),
     # sheets at eps = 0: difference, two comparisons turned into +-1, accumulate (no SFU)
@@ -113,6 +109,10 @@ def parse():
                     help="override N (profiling runs on smaller cases); --particles under torchrun, whose "
                          "own parser takes --n for one of its options")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of K steps each; value is the median (HMF and ensemble workloads)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short Ring, 2D and ensemble runs added to the default (HMF) line")
     a = ap.parse_args()
     dflt = {"hmf": (1000, 10), "ring": (20, 3), "grav2d": (10, 3), "grav3d": (20, 3), "sheet1d": (20, 3), "ensemble": (20, 3),
             "adjoint": (1, 3)}[a.workload]
@@ -422,12 +422,129 @@ def run_reference(args, w):
 
 # ------------------------------------------------------------ our path ----
 
+def pair_timed_steps(lib, h, stream, flush, K):
+    """K integrator steps of a pair model as md_stage calls (the stage list of
+    md_step(K): 3K fused stages and the closing kick), L2 flushed before every step;
+    returns (total ms, per-stage ms) from CUDA events on the stream."""
+    import torch
+
+    from paper_1212_0262_gb300 import binding
+    from paper_1212_0262_gb300.system import stage_schedule
+
+    sched = stage_schedule(K)
+    elapsed_ms, stage_ms = 0.0, []
+    for s in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        sc = sched[3 * s:3 * s + 3] + ([sched[-1]] if s == K - 1 else [])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(sc) + 1)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for k, (b, d) in enumerate(sc):
+                binding.check(lib.md_stage(h, b, d), h)
+                ev[k + 1].record(stream)
+        ev[-1].synchronize()
+        ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(sc))]
+        stage_ms += ms
+        elapsed_ms += sum(ms)
+    return elapsed_ms, stage_ms
+
+
+def pipe_rates():
+    import numpy as np
+
+    from paper_1212_0262_gb300 import binding
+
+    rates = np.zeros(19)
+    binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 19)
+    return rates
+
+
+def pair_roofline(workload, model, N, kcode, prec, stage_ms, clocks, tuned):
+    """Roofline object of a pair-model run: algorithmic pair terms per stage over the
+    average stage time, against the pipe-bound rate of the kernel that ran (FP32 and
+    SFU operations per term for the FP32 kernels, FP64-pipe operations for the FP64
+    ones) at the SM clock sampled during the run; also the fraction at the maximum
+    clock."""
+    rates = pipe_rates()
+    avg_ms = sum(stage_ms) / len(stage_ms)
+    nsm = rates[0]
+    fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
+    sfu_rate = rates[5] if model in (1, 3) else rates[7]  # rsqrt (Ring, 3D) or rcp (2D)
+    kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
+    pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops) if sops else fp32_rate / fops
+    f64 = PAIR_KERNELS_FP64.get((model, kcode)) if prec == "fp64" else None
+    if f64:  # FP64 kernels: bound by the FP64 pipe (measured DFMA rate)
+        kname, dops, sym = f64
+        pairs_per_clk = rates[13] / dops
+    if prec == "fp64" and not f64:
+        return None  # FP64 sheets: sign counting, no stated pipe bound
+    mhz = clocks.get("sm_mhz") or rates[2]
+    max_mhz = clocks.get("sm_max_mhz") or rates[2]
+    peak = nsm * pairs_per_clk * mhz * 1e6
+    # algorithmic pair terms per force pass: N^2 ordered pairs, or N (N - 1) / 2
+    # unordered pairs when each is evaluated once
+    terms = N * (N - 1) / 2 if sym else float(N) * N
+    achieved = terms / (avg_ms * 1e-3)
+    # DRAM bytes per stage (pair and finish kernels) of the default symmetric FP32
+    # kernels, from the committed ncu record when the sources are unchanged
+    traffic = None
+    if prec == "mixed" and (model, kcode) in ((1, 5), (2, 4)) and not tuned:
+        traffic = recorded_traffic(f"{workload}_stage_sym_mixed",
+                                   ["paper_1212_0262_gb300/csrc/sym.cu",
+                                    "paper_1212_0262_gb300/csrc/pairs_impl.cuh",
+                                    "paper_1212_0262_gb300/csrc/md_internal.cuh"], float(N) * N)
+    return {"bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
+            "frac": achieved / peak, "frac_at_max_clock": achieved / (peak * max_mhz / mhz), "traffic": traffic,
+            "kernel": f"{kname}, {prec}",
+            "peak_derivation": ({"sms": nsm, "fp64_ops_per_sm_clk": rates[13], "fp64_ops_per_pair": f64[1],
+                                 "sm_mhz": mhz, "sm_max_mhz": max_mhz} if f64 else
+                                {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
+                                 "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
+                                 "sfu_ops_per_pair": sops, "sm_mhz": mhz, "sm_max_mhz": max_mhz}),
+            "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
+
+
+def secondary_pair(workload, K, W, local):
+    """A short run of one pair configuration in the default precision and kernels
+    (its own system, L2 flush, clock record and energy error), for the default line."""
+    import torch
+
+    from paper_1212_0262_gb300 import System, binding
+
+    w = WORKLOADS[workload]
+    model, N = w["model"], w["N"]
+    stream = torch.cuda.Stream()
+    lib = binding.load()
+    with System(model, N, w["eps"], w["dt"], w["seed"], precision="mixed") as s:
+        s.set_stream(stream)
+        e0 = sum(s.energy())
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        if W:
+            pair_timed_steps(lib, s._h, stream, flush, W)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(device_uuid(local))
+        l0 = s.launch_count
+        elapsed_ms, stage_ms = pair_timed_steps(lib, s._h, stream, flush, K)
+        torch.cuda.synchronize()
+        launches = s.launch_count - l0
+        clocks = sampler.stop()
+        e1 = sum(s.energy())
+        kcode = s.force_kernel
+        del flush
+    return {"workload": w["name"], "value": 3.0 * N * N * K / (elapsed_ms * 1e-3), "unit": w["unit"],
+            "steps": K, "warmup": W, "ms_per_step": elapsed_ms / K, "precision": "mixed",
+            "rel_energy_error": abs((e1 - e0) / e0), "energy_error_steps": W + K,
+            "roofline": pair_roofline(workload, model, N, kcode, "mixed", stage_ms, clocks, []),
+            "gpu_launches": launches, "clocks": clocks, "l2": "flushed (256 MB write) before every timed step"}
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
 
     from paper_1212_0262_gb300 import System, binding
-    from paper_1212_0262_gb300.system import stage_schedule
 
     ws, rank, local = dist_info()
     if ws > 1:
@@ -445,20 +562,11 @@ def run_ours(args, w):
         sysm.set_tuning(k, int(v))
     e0 = sum(sysm.energy())
 
-    sched = stage_schedule(K)
     lib = binding.load()
     h = sysm._h
-
-    def run_schedule(steps, events=None):
-        sc = stage_schedule(steps)
-        with torch.cuda.stream(stream):
-            if events is not None:
-                events[0].record(stream)
-            for k, (b, d) in enumerate(sc):
-                binding.check(lib.md_stage(h, b, d), h)
-                if events is not None:
-                    events[k + 1].record(stream)
-
+    flush = None
+    if model != 0:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     if W:
         if model == 0:
             # the timed region is md_step: capture its step graphs (both ping-pong
@@ -466,10 +574,7 @@ def run_ours(args, w):
             sysm.step(max(W, 9))
             sysm.step(max(W, 9) + 1)
         else:
-            run_schedule(W)
-    flush = None
-    if model != 0:
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+            pair_timed_steps(lib, h, stream, flush, W)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -477,41 +582,39 @@ def run_ours(args, w):
     sampler = ClockSampler(device_uuid(local))
     launches0 = sysm.launch_count
     stage_ms = []
+    repeats_ms = None
     if model == 0:
         # md_step(K) as a user calls it: 3K fused kick-drift stages (replayed from captured
-        # graphs after the first step) and the closing kick, timed with events on its stream
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            ev[0].record(stream)
-            sysm.step(K)
-            ev[1].record(stream)
-        ev[1].synchronize()
-        elapsed_ms = ev[0].elapsed_time(ev[1])
-    else:
-        # compute-bound kernels on L2-sized inputs: flush L2 between timed steps
-        elapsed_ms = 0.0
-        for s in range(K):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(s))
-            sc = sched[3 * s:3 * s + 3] + ([sched[-1]] if s == K - 1 else [])
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(sc) + 1)]
+        # graphs after the first step) and the closing kick, timed with events on its
+        # stream; `repeats` such regions, each bracketed by a synchronize (and a barrier
+        # under torchrun), the slowest rank's time per region, the median reported
+        repeats_ms = []
+        for _ in range(max(1, args.repeats)):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            if ws > 1:
+                torch.distributed.barrier()
             with torch.cuda.stream(stream):
                 ev[0].record(stream)
-                for k, (b, d) in enumerate(sc):
-                    binding.check(lib.md_stage(h, b, d), h)
-                    ev[k + 1].record(stream)
-            ev[-1].synchronize()
-            ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(len(sc))]
-            stage_ms += ms
-            elapsed_ms += sum(ms)
+                sysm.step(K)
+                ev[1].record(stream)
+            ev[1].synchronize()
+            t = torch.tensor([ev[0].elapsed_time(ev[1])], dtype=torch.float64, device=dev)
+            if ws > 1:
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            repeats_ms.append(float(t.item()))
+        elapsed_ms = sorted(repeats_ms)[len(repeats_ms) // 2]
+    else:
+        # compute-bound kernels on L2-sized inputs: flush L2 between timed steps
+        elapsed_ms, stage_ms = pair_timed_steps(lib, h, stream, flush, K)
     torch.cuda.synchronize()
-    launches = sysm.launch_count - launches0
+    launches = (sysm.launch_count - launches0) // (len(repeats_ms) if repeats_ms else 1)
     clocks = sampler.stop()
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    if repeats_ms is None:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        if ws > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
     torch.cuda.synchronize()
     t_en = time.perf_counter()
     e1 = sum(sysm.energy())
@@ -541,45 +644,7 @@ def run_ours(args, w):
     else:
         units_per_step = 3 * N * N
         value = ws * 3 * N * N * K / (elapsed_ms * 1e-3)
-        avg_ms = sum(stage_ms) / len(stage_ms)
-        rates = np.zeros(19)
-        binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 19)
-        nsm = rates[0]
-        fp32_rate = max(rates[1], rates[3])  # FP32 FMA ops per SM per clock
-        sfu_rate = rates[5] if model in (1, 3) else rates[7]  # rsqrt (Ring, 3D) or rcp (2D)
-        kcode = sysm.force_kernel
-        kname, fops, sops, sym = PAIR_KERNELS.get((model, kcode), (f"pair kernel {kcode}",) + PAIR_OPS[model] + (False,))
-        pairs_per_clk = min(fp32_rate / fops, sfu_rate / sops) if sops else fp32_rate / fops
-        f64 = PAIR_KERNELS_FP64.get((model, kcode)) if args.prec == "fp64" else None
-        if f64:  # FP64 kernels: bound by the FP64 pipe (measured DFMA rate)
-            kname, dops, sym = f64
-            pairs_per_clk = rates[13] / dops
-        mhz = clocks.get("sm_mhz") or rates[2]
-        peak = nsm * pairs_per_clk * mhz * 1e6
-        # algorithmic pair terms per force pass: N^2 ordered pairs, or N (N - 1) / 2
-        # unordered pairs when each is evaluated once
-        terms = N * (N - 1) / 2 if sym else N * N
-        achieved = terms / (avg_ms * 1e-3)
-        # DRAM bytes per stage (pair and finish kernels) of the default symmetric FP32
-        # kernels, from the committed ncu record when the sources are unchanged
-        traffic = None
-        if args.prec == "mixed" and (model, kcode) in ((1, 5), (2, 4)) and not args.tune:
-            traffic = recorded_traffic(f"{args.workload}_stage_sym_mixed",
-                                       ["paper_1212_0262_gb300/csrc/sym.cu",
-                                        "paper_1212_0262_gb300/csrc/pairs_impl.cuh",
-                                        "paper_1212_0262_gb300/csrc/md_internal.cuh"], float(N) * N)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                    "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
-                    "frac": achieved / peak, "traffic": traffic,
-                    "kernel": f"{kname}, {args.prec}",
-                    "peak_derivation": ({"sms": nsm, "fp64_ops_per_sm_clk": rates[13], "fp64_ops_per_pair": f64[1],
-                                         "sm_mhz": mhz} if f64 else
-                                        {"sms": nsm, "fp32_ops_per_sm_clk": fp32_rate,
-                                         "sfu_ops_per_sm_clk": sfu_rate, "fp32_ops_per_pair": fops,
-                                         "sfu_ops_per_pair": sops, "sm_mhz": mhz}),
-                    "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
-        if args.prec == "fp64" and not f64:
-            roofline = None  # FP64 sheets: sign counting, no stated pipe bound
+        roofline = pair_roofline(args.workload, model, N, sysm.force_kernel, args.prec, stage_ms, clocks, args.tune)
 
     # FP64 path on the same workload (few steps) and the matching mixed energy error
     extra = {}
@@ -590,7 +655,9 @@ def run_ours(args, w):
     if model != 0:
         extra["energy_pass"].update({"pairs": npairs, "pairs_per_s": npairs / (energy_ms * 1e-3)})
     if not args.no_fp64 and rank == 0:
-        ksh = 10 if model == 0 else 2
+        # HMF: 1 + 999 steps = T = 100 at dt = 0.1, the time the HMF configuration states
+        # its energy error at; the pair models: 1 + 2 steps
+        ksh = 999 if model == 0 else 2
         res = {}
         for prec in ("fp64", "mixed"):
             with System(model, N, w["eps"], w["dt"], w["seed"], precision=prec) as s2:
@@ -612,9 +679,12 @@ def run_ours(args, w):
                 res[prec] = {"value": units / (ms * 1e-3), "ms_per_step": ms / ksh,
                              "rel_energy_error": abs((e_b - e_a) / e_a), "steps": ksh + 1}
         extra["fp64_path"] = res["fp64"]
+        extra["mixed_path_long_run"] = res["mixed"]
+        T = res["mixed"]["steps"] * w["dt"]
         extra["energy_error"] = {"mixed_after_%d_steps" % (res["mixed"]["steps"]): res["mixed"]["rel_energy_error"],
                                  "fp64_after_%d_steps" % (res["fp64"]["steps"]): res["fp64"]["rel_energy_error"],
-                                 "mixed_timed_run": de_mixed, "timed_run_steps": W + K}
+                                 "T": T, "mixed_timed_run": de_mixed,
+                                 "timed_run_steps": W + K * (len(repeats_ms) if repeats_ms else 1)}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -660,6 +730,22 @@ def run_ours(args, w):
         cpu = {"value": units / el, "unit": w["unit"], "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": el, "single_core": {"value": u1 / e1, "sample": s1, "seconds": e1}}
 
+    # the other configurations, each a short driver-clocked run with its own clock
+    # record and roofline: Ring (N = 131,072), 2D forward (N = 262,144) and the ensemble
+    secondary = None
+    if rank == 0 and model == 0 and not args.no_secondary and not args.n:
+        sysm.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        # 20 / 10 / 10 steps: the closing kick-only stage of each timed call (a force
+        # pass not counted in the 3 N^2 per step) stays within 1.6-3% of the time
+        secondary = {"ring": secondary_pair("ring", 20, 3, local), "grav2d": secondary_pair("grav2d", 10, 3, local)}
+        ens, _, _, m = ensemble_measure("mixed", 10, 3, local, repeats=3)
+        ens.close()
+        m.pop("pairs_per_stage")
+        secondary["ensemble"] = dict(workload=WORKLOADS["ensemble"]["name"], unit=WORKLOADS["ensemble"]["unit"],
+                                     steps=10, warmup=3, precision="mixed", **m)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
@@ -672,7 +758,11 @@ def run_ours(args, w):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "rel_energy_error": de_mixed,
         }
+        if repeats_ms is not None:
+            line["repeats_ms"] = repeats_ms
         line.update(extra)
+        if secondary is not None:
+            line["secondary"] = secondary
         print(json.dumps(line), flush=True)
     sysm.close()
     if ws > 1:
@@ -691,61 +781,17 @@ def ensemble_spec(nsys=256, seed=1000):
     return models, Ns, eps, dts, seeds
 
 
-def run_ensemble(args, w):
-    import ctypes as _c
-
+def ensemble_roofline(ens, Ns, models, prec, avg_ms, clocks):
+    """Roofline of an ensemble stage: the algorithmic pair terms of all systems over
+    the average stage time, against the time-optimal rate for the mix of Ring and 2D
+    terms at the sampled SM clock (and at the maximum clock)."""
     import numpy as np
-    import torch
 
-    from paper_1212_0262_gb300 import Ensemble, binding
-
-    ws, rank, local = dist_info()
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    stream = torch.cuda.Stream()
-    models, Ns, eps, dts, seeds = ensemble_spec()
-    ens = Ensemble(models, Ns, eps, dts, seeds, precision=args.prec)
-    ens.set_stream(stream)
-    t0 = time.perf_counter()
-    tuned_ms = ens.autotune()
-    tune_s = time.perf_counter() - t0
-    K0, V0 = ens.energy()
-    K, W = args.steps, args.warmup
-    if W:
-        ens.step(W)
-    pairs_per_stage = float(np.sum(np.asarray(Ns, dtype=np.float64) ** 2))
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    sampler = ClockSampler(device_uuid(local))
-    l0 = ens.launch_count
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    ens.step(K)
-    b.record(stream)
-    b.synchronize()
-    launches = ens.launch_count - l0
-    clocks = sampler.stop()
-    ms = a.elapsed_time(b)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(t.item())
-    K1, V1 = ens.energy()
-    e0, e1 = K0 + V0, K1 + V1
-    de = np.abs((e1 - e0) / e0)
-    value = ws * 3 * pairs_per_stage * K / (ms * 1e-3)
-    nl = 3 * K + 1
-    avg_ms = ms / nl
-    rates = np.zeros(19)
-    binding.load_peaks().mdp_pipe_rates(rates.ctypes.data_as(_c.POINTER(_c.c_double)), 19)
+    rates = pipe_rates()
     nsm = rates[0]
     fp32 = max(rates[1], rates[3])
     # kernel form: r = 0 (mixed) evaluates every unordered pair of a system once
-    sym = args.prec == "mixed" and ens.tuning[0] == 0
+    sym = prec == "mixed" and ens.tuning[0] == 0
     kr = PAIR_KERNELS[(1, 5)] if sym else ("batch Ring part", PAIR_OPS[1][0], PAIR_OPS[1][1], False)
     kg = PAIR_KERNELS[(2, 4)] if sym else ("batch 2D part", PAIR_OPS[2][0], PAIR_OPS[2][1], False)
     per_clk_ring = min(fp32 / kr[1], rates[5] / kr[2])
@@ -754,19 +800,97 @@ def run_ensemble(args, w):
         w_ring = float(sum(n * (n - 1) / 2 for n, m in zip(Ns, models) if m == 1))
         w_2d = float(sum(n * (n - 1) / 2 for n, m in zip(Ns, models) if m == 2))
     else:
-        w_ring = float(sum(n * n for n, m in zip(Ns, models) if m == 1))
-        w_2d = pairs_per_stage - w_ring
+        w_ring = float(sum(float(n) * n for n, m in zip(Ns, models) if m == 1))
+        w_2d = float(sum(float(n) * n for n, m in zip(Ns, models) if m == 2))
     terms = w_ring + w_2d
     mhz = clocks.get("sm_mhz") or rates[2]
-    # time-optimal term rate for this mix of Ring and 2D terms
+    max_mhz = clocks.get("sm_max_mhz") or rates[2]
     peak = terms / (w_ring / (nsm * per_clk_ring * mhz * 1e6) + w_2d / (nsm * per_clk_2d * mhz * 1e6))
     achieved = terms / (avg_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
+            "frac": achieved / peak, "frac_at_max_clock": achieved / (peak * max_mhz / mhz), "traffic": None,
+            "kernel": ("batch_sym_pairs_kernel + batch_sym_finish_kernel (Ring tensor-core + 2D parts)"
+                       if sym else "batch_kernel (Ring + 2D parts)"),
+            "pair_terms_per_stage": terms, "avg_stage_ms": avg_ms, "sm_mhz": mhz, "sm_max_mhz": max_mhz}
+
+
+def ensemble_measure(prec, K, W, local, repeats=1, ws=1):
+    """The batched-ensemble workload: build, autotune, W warm-up steps, then `repeats`
+    timed regions of md_batch_step(K) (CUDA events on the ensemble's stream, each
+    bracketed by a synchronize and, under torchrun, a barrier; the slowest rank's time
+    per region, the median kept).  Returns (ensemble, spec, stream, measurement dict)."""
+    import numpy as np
+    import torch
+
+    from paper_1212_0262_gb300 import Ensemble
+
+    stream = torch.cuda.Stream()
+    models, Ns, eps, dts, seeds = ensemble_spec()
+    ens = Ensemble(models, Ns, eps, dts, seeds, precision=prec)
+    ens.set_stream(stream)
+    t0 = time.perf_counter()
+    tuned_ms = ens.autotune()
+    tune_s = time.perf_counter() - t0
+    K0, V0 = ens.energy()
+    if W:
+        ens.step(W)
+    pairs_per_stage = float(np.sum(np.asarray(Ns, dtype=np.float64) ** 2))
+    sampler = ClockSampler(device_uuid(local))
+    l0 = ens.launch_count
+    reps = []
+    for _ in range(max(1, repeats)):
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.step(K)
+        b.record(stream)
+        b.synchronize()
+        t = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        reps.append(float(t.item()))
+    launches = (ens.launch_count - l0) // len(reps)
+    clocks = sampler.stop()
+    ms = sorted(reps)[len(reps) // 2]
+    K1, V1 = ens.energy()
+    e0, e1 = K0 + V0, K1 + V1
+    de = np.abs((e1 - e0) / e0)
+    avg_ms = ms / (3 * K + 1)
+    m = {"value": ws * 3 * pairs_per_stage * K / (ms * 1e-3), "ms_per_step": ms / K, "repeats_ms": reps,
+         "roofline": ensemble_roofline(ens, Ns, models, prec, avg_ms, clocks),
+         "autotune": {"seconds": tune_s, "best_force_launch_ms": tuned_ms, "tuning": list(ens.tuning)},
+         "rel_energy_error": {"max": float(de.max()), "median": float(np.median(de)),
+                              "steps": W + K * len(reps)},
+         "gpu_launches": launches, "clocks": clocks, "pairs_per_stage": pairs_per_stage}
+    return ens, (models, Ns, eps, dts, seeds), stream, m
+
+
+def run_ensemble(args, w):
+    import ctypes as _c
+
+    import numpy as np
+    import torch
+
+    from paper_1212_0262_gb300 import binding
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    K, W = args.steps, args.warmup
+    ens, (models, Ns, eps, dts, seeds), stream, m = ensemble_measure(args.prec, K, W, local, args.repeats, ws)
+    pairs_per_stage = m["pairs_per_stage"]
 
     e2e = None
     if rank == 0 and not args.no_e2e:
         # every system's state from pinned host memory, the steps and every state
         # back, through the public ensemble API (wall clock)
-        dims = [2 if m == 2 else 1 for m in models]
+        dims = [2 if mm == 2 else 1 for mm in models]
         sizes = [d * int(n) for d, n in zip(dims, Ns)]
         offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         qh = torch.empty(int(offs[-1]), dtype=torch.float64, pin_memory=True).numpy()
@@ -800,21 +924,15 @@ def run_ensemble(args, w):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
-            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "metric": METRIC, "value": m["value"], "unit": w["unit"], "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 state / f32 pair arithmetic" if args.prec == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": w["name"], "systems": len(Ns), "sum_N": int(np.sum(Ns)),
                        "sum_N2": pairs_per_stage, "precision": args.prec,
                        "l2": "state and mirrors of all systems ~180 MB > L2"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "unordered pair terms/s" if sym else "pair-interactions/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": ("batch_sym_pairs_kernel + batch_sym_finish_kernel (Ring tensor-core + 2D parts)"
-                                    if sym else "batch_kernel (Ring + 2D parts)"),
-                         "pair_terms_per_stage": terms, "avg_stage_ms": avg_ms, "stages": nl},
-            "autotune": {"seconds": tune_s, "best_force_launch_ms": tuned_ms},
-            "rel_energy_error": {"max": float(de.max()), "median": float(np.median(de))},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": m["roofline"], "repeats_ms": m["repeats_ms"], "autotune": m["autotune"],
+            "rel_energy_error": m["rel_energy_error"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
         }
         print(json.dumps(line), flush=True)
     ens.close()

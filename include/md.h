@@ -131,14 +131,8 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
  *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = default: 4 for the FP32
  *                      sine/cosine stages, the occupancy limit otherwise)
- *   "rcp_offload"      2D FP32: every 8th pair of j's takes 1/x on the FMA pipe (0 or 8)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32
  *                      tensor-core products (0 off; 1 or 2: 4 or 2 16-row blocks per warp)
- *   "grav_tc"          2D FP32 forward stages: dx and dy from tensor-core products of an
- *                      exact three-way TF32 split of each coordinate (0 off; symmetric
- *                      kernel shape 1: 4 16-row blocks per warp, 128 threads; 2: 2 blocks,
- *                      256 threads; 3: as 1 with registers for 3 CTAs per SM).  Needs
- *                      r_mixed 8 and rcp_offload 0.
  *   "symmetric"        forward stages of Ring (FP32: with ring_tc 1) and 2D, FP32 and
  *                      FP64 (r_fp64 2): every unordered pair evaluated once and added to
  *                      both particles (Newton's third law; the paper evaluates both
@@ -147,12 +141,6 @@ int md_set_eps(md_ctx *ctx, double eps);
  *                      N^2 / 64 (FP64 2D), 3 N^2 / 256 (FP32 3D) or N^2 / 512 (FP32
  *                      sheets); above 16 GiB of it (N beyond about 1.48e6 for Ring,
  *                      2.1e6 for FP32 2D) the one-sided kernel runs.
- *   "rsqrt_offload"    symmetric FP32 Ring kernel: 0 (default), 1 or 2 of the 8 pair-halves per
- *                      16x8 block take 1/sqrt on the FMA pipe (bit-pattern seed, two cubic
- *                      steps) instead of the SFU; measured slower on GB300, kept for study
- *   "sym_threads"      symmetric FP32 Ring kernel CTA shape: 128 (default: 4 16-row blocks per
- *                      warp, registers for 4 CTAs per SM), 256 or 768 (256 threads, 2 blocks
- *                      per warp, registers for 2 or 3 CTAs per SM)
  *   "step_graphs"      md_step replays its steps after the first from captured CUDA
  *                      graphs of 8 steps (1, default) or launches every stage (0).
  * MD_EINVAL for an unknown key or value. */
@@ -163,9 +151,9 @@ int md_set_tuning(md_ctx *ctx, const char *key, int64_t value);
 #define MD_KERNEL_HMF 0          /* HMF mean-field stage (Sec. 3.1) */
 #define MD_KERNEL_PAIRS_FP64 1   /* FP64 all-pairs, every ordered pair */
 #define MD_KERNEL_PAIRS 2        /* FP32 all-pairs on the CUDA cores, every ordered pair */
-#define MD_KERNEL_PAIRS_TC 3     /* FP32 with tensor-core products (Ring, 2D), every ordered pair */
+#define MD_KERNEL_PAIRS_TC 3     /* FP32 with tensor-core products (Ring), every ordered pair */
 #define MD_KERNEL_PAIRS_SYM 4    /* FP32 on the CUDA cores, every unordered pair once */
-#define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 with tensor-core products (Ring, 2D), every unordered pair once */
+#define MD_KERNEL_PAIRS_TC_SYM 5 /* FP32 with tensor-core products (Ring), every unordered pair once */
 #define MD_KERNEL_PAIRS_FP64_SYM 6 /* FP64 all-pairs, every unordered pair once */
 int md_force_kernel(const md_ctx *ctx);
 
@@ -237,6 +225,18 @@ int md_grad(md_ctx *ctx, int observable, int64_t nsteps, int checkpoint_every,
  * MD_SHEET1D at eps = 0. */
 int md_tangent_step(md_ctx *ctx, int64_t nsteps, double *dq, double *dp);
 
+/* Largest-Lyapunov-exponent run on the device: the tangent (dq, dp) is normalised
+ * to unit FP64 length, then carried with the state through nsteps steps of
+ * md_tangent_step's linearised map, renormalised to unit length after every
+ * renorm_every steps (and after the last, shorter block); *sum_log receives the sum
+ * of the logarithms of the norms found at those renormalisations, so the estimate
+ * is *sum_log / (nsteps dt).  dq, dp: host arrays of dim*N, read (any non-zero
+ * vector) and overwritten with the final unit tangent.  The state advances nsteps
+ * steps.  The tangent stays in device memory between renormalisations (no host
+ * copies inside the run).  Uses the context's precision.  Synchronous.  MD_EINVAL
+ * for MD_SHEET1D at eps = 0. */
+int md_lyapunov(md_ctx *ctx, int64_t nsteps, int64_t renorm_every, double *dq, double *dp, double *sum_log);
+
 /* Route the library's device allocations through alloc(bytes, user) and
  * free(ptr, user) (for example a caching allocator of the host framework).
  * alloc returns NULL on failure, which the library reports as MD_ENOMEM; it must
@@ -272,6 +272,72 @@ int md_set_allocator(void *(*alloc)(size_t bytes, void *user), void (*free_fn)(v
  * on the GPU.  Inside a stream capture the wait is left out: calls captured into
  * graphs that may run concurrently must be ordered by the caller. */
 int md_potential_noalloc(int model, int64_t N, double eps, const double *q, double *V, void *stream);
+
+/* ----- row shards: one system split by rows among several ranks ----- */
+/* The paper's two-GPU schemes generalised to P ranks.  HMF (Sec. 3.1, last
+ * paragraph): every rank advances its own particles and the partial magnetizations
+ * (sum cos, sum sin) of all ranks are added, in rank order, before every stage.
+ * Ring and 2D (Sec. 3.2, Fig. 2 and its two-GPU stage list): every rank evaluates
+ * the forces on its own rows against all N positions (every ordered pair, the
+ * one-sided kernels) and, after every drift, the new positions of each rank are
+ * copied to all others.
+ *
+ * Protocol.  Each rank has one context from md_shard_init.  md_shard_begin writes
+ * the rank's own segment of its exchange buffer from its state; then, and after
+ * every md_shard_stage, every rank's segment must be copied into the same byte
+ * range of every other rank's exchange buffer (md_shard_buffer gives the buffer and
+ * the segment) before the next md_shard_stage or md_shard_force: md_shard_exchange
+ * does this for ranks held by one process; a multi-process transport copies the
+ * same byte ranges.  md_shard_step runs whole steps of Eq. 4 with the exchange after
+ * every stage.  md_step, md_stage, md_force, md_energy, md_magnetization, md_grad
+ * and md_tangent_step answer MD_ESTATE on a shard context; md_get_state /
+ * md_set_state (and the _device forms) read and write the rank's own rows
+ * (dim * n_rows doubles, layout as for a whole system); after md_set_state,
+ * md_set_ic or md_set_precision call md_shard_begin (and exchange) again. */
+
+/* Rows [*lo, *hi) of rank `rank` of `nranks` for a system of N particles of
+ * `model` (MD_HMF, MD_RING, MD_GRAV2D): lo = floor(N rank / nranks) rounded down to
+ * a multiple of 1024 rows for Ring and 2D (whole mirror groups and i-tiles), of 1 for
+ * HMF.  MD_EINVAL if a rank would get no rows or nranks is outside [1, 64]. */
+int md_shard_range(int model, int64_t N, int rank, int nranks, int64_t *lo, int64_t *hi);
+
+/* Context for rank `rank`'s rows of the system md_init(model, N, eps, dt, seed)
+ * would make: its state is those rows of the same initial state (same counters).
+ * Ring / 2D hold the whole N-particle position mirror besides their rows' state.
+ * Returns NULL on failure (md_last_error(NULL)).  Free with md_free. */
+md_ctx *md_shard_init(int model, int64_t N, double eps, double dt, uint64_t seed, int rank, int nranks);
+
+/* Write this rank's segment of its exchange buffer from its current state
+ * (asynchronous, on the context's stream). */
+int md_shard_begin(md_ctx *ctx);
+
+/* One fused stage over the rank's rows: force from the exchanged buffer, kick
+ * p += b dt f, drift q += d dt p (d = 0: kick only), then this rank's segment of the
+ * exchange buffer for the next stage.  Asynchronous.  MD_ESTATE before
+ * md_shard_begin. */
+int md_shard_stage(md_ctx *ctx, double b, double d);
+
+/* The device exchange buffer of ctx for the stage that comes next (it alternates
+ * between two buffers) and this rank's segment in it: bytes [*seg_offset,
+ * *seg_offset + *seg_bytes).  HMF: 16 bytes (sum cos, sum sin) per rank; Ring / 2D:
+ * the position records of the rank's rows (the last rank's also the padding). */
+int md_shard_buffer(md_ctx *ctx, void **buf, size_t *seg_offset, size_t *seg_bytes);
+
+/* Exchange between the nranks contexts ctx[0..nranks-1] (ctx[r] must be rank r of
+ * the same system) held by this process, on the same or different devices: every
+ * rank's stream waits for every other rank's last stage (an event) and copies the
+ * other ranks' segments into its own buffer (cudaMemcpyAsync).  Asynchronous. */
+int md_shard_exchange(md_ctx *const *ctx, int nranks);
+
+/* nsteps >= 0 integration steps of Sec. 3 (Eq. 4 constants, merged kicks as md_step)
+ * on all nranks shards of one system held by this process, with md_shard_exchange
+ * after every stage; calls md_shard_begin and exchanges first when needed.
+ * Asynchronous. */
+int md_shard_step(md_ctx *const *ctx, int nranks, int64_t nsteps);
+
+/* Forces on the rank's rows at the current (exchanged) positions into host
+ * f[dim * n_rows], at the context's precision.  Synchronous. */
+int md_shard_force(md_ctx *ctx, double *f);
 
 /* Wait for all work queued on the context's stream. */
 int md_synchronize(md_ctx *ctx);

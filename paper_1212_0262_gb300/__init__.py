@@ -8,9 +8,9 @@ hand-written sm_103a CUDA kernels behind the C ABI of include/md.h.
 """
 from . import binding
 from .binding import MDError
-from .system import Ensemble, System
+from .system import Ensemble, ShardGroup, System, shard_range
 
 HMF, RING, GRAV2D, GRAV3D, SHEET1D = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 
-__all__ = ["binding", "MDError", "System", "Ensemble", "HMF", "RING", "GRAV2D", "GRAV3D", "SHEET1D", "FP64", "MIXED"]
+__all__ = ["binding", "MDError", "System", "Ensemble", "ShardGroup", "shard_range", "HMF", "RING", "GRAV2D", "GRAV3D", "SHEET1D", "FP64", "MIXED"]

@@ -60,8 +60,17 @@ _SIGS = {
     "md_magnetization": (_c.c_int, [_P, _D, _D]),
     "md_grad": (_c.c_int, [_P, _c.c_int, _c.c_int64, _c.c_int, _P, _P, _D, _D]),
     "md_tangent_step": (_c.c_int, [_P, _c.c_int64, _P, _P]),
+    "md_lyapunov": (_c.c_int, [_P, _c.c_int64, _c.c_int64, _P, _P, _D]),
     "md_set_allocator": (_c.c_int, [_P, _P, _P]),
     "md_potential_noalloc": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_double, _P, _P, _P]),
+    "md_shard_range": (_c.c_int, [_c.c_int, _c.c_int64, _c.c_int, _c.c_int, _P, _P]),
+    "md_shard_init": (_P, [_c.c_int, _c.c_int64, _c.c_double, _c.c_double, _c.c_uint64, _c.c_int, _c.c_int]),
+    "md_shard_begin": (_c.c_int, [_P]),
+    "md_shard_stage": (_c.c_int, [_P, _c.c_double, _c.c_double]),
+    "md_shard_buffer": (_c.c_int, [_P, _P, _P, _P]),
+    "md_shard_exchange": (_c.c_int, [_P, _c.c_int]),
+    "md_shard_step": (_c.c_int, [_P, _c.c_int, _c.c_int64]),
+    "md_shard_force": (_c.c_int, [_P, _P]),
     "md_synchronize": (_c.c_int, [_P]),
     "md_launch_count": (_c.c_int64, [_P]),
     "md_batch_init": (_P, [_c.c_int, _P, _P, _P, _P, _P]),

@@ -21,7 +21,7 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", I
                 "--expt-relaxed-constexpr"]
 
 LIBS = {
-    "libmd.so": ["api.cu", "hmf.cu", "pairs.cu", "sym.cu", "energy.cu", "ic.cu", "grad.cu", "tangent.cu", "batch.cu", "noalloc.cu"],
+    "libmd.so": ["api.cu", "hmf.cu", "pairs.cu", "sym.cu", "energy.cu", "ic.cu", "grad.cu", "tangent.cu", "batch.cu", "noalloc.cu", "shard.cu"],
     "libmdpeaks.so": ["peaks.cu"],
 }
 

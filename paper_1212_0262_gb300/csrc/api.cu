@@ -127,66 +127,29 @@ void yoshida_coefficients(double c[4]) {
   c[3] = w0;               // D1
 }
 
-// ------------------------------------------------------------------ ABI ---
-
-extern "C" {
-
-const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
-
-int md_last_status(void) { return g_status; }
-
-int md_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user) {
-  if ((alloc == nullptr) != (free_fn == nullptr))
-    return fail_global(MD_EINVAL, "md_set_allocator: give both alloc and free, or neither");
-  std::lock_guard<std::mutex> lk(g_alloc_mu);
-  g_alloc = alloc;
-  g_free = free_fn;
-  g_alloc_user = user;
-  return MD_OK;
-}
-
-void md_free(md_ctx *c) {
-  if (!c) return;
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  dev_free(c->q);
-  dev_free(c->p);
-  dev_free(c->f);
-  dev_free(c->hmf_partials);
-  dev_free(c->hmf_m);
-  dev_free(c->hmf_ticket);
-  dev_free(c->hmf_cs);
-  dev_free(c->mirror[0]);
-  dev_free(c->mirror[1]);
-  dev_free(c->sk_slots);
-  dev_free(c->sk_tickets);
-  dev_free(c->sym_rowfull);
-  dev_free(c->sym_colslot);
-  dev_free(c->sym_chunks);
-  destroy_step_graphs(c);
-  dev_free(c->red);
-  dev_free(c->gw);
-  if (c->host_scalars) cudaFreeHost(c->host_scalars);
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  delete c;
-}
-
-md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
+md_ctx *create_context(int model, int64_t N, int64_t n_total, int64_t row0, double eps, double dt, uint64_t seed,
+                       const char *who) {
   if (model != MD_HMF && model != MD_RING && model != MD_GRAV2D && model != MD_GRAV3D && model != MD_SHEET1D) {
-    fail_global(MD_EINVAL, "md_init: unknown model %d", model);
+    fail_global(MD_EINVAL, "%s: unknown model %d", who, model);
     return nullptr;
   }
-  if (N < 1 || N > (int64_t)1 << 40) {
-    fail_global(MD_EINVAL, "md_init: N must be in [1, 2^40], got %lld", (long long)N);
+  if (n_total < 1 || n_total > (int64_t)1 << 40) {
+    fail_global(MD_EINVAL, "%s: N must be in [1, 2^40], got %lld", who, (long long)n_total);
+    return nullptr;
+  }
+  if (N < 1 || row0 < 0 || row0 + N > n_total) {
+    fail_global(MD_EINVAL, "%s: rows [%lld, %lld) outside [0, %lld)", who, (long long)row0, (long long)(row0 + N),
+                (long long)n_total);
     return nullptr;
   }
   const bool eps0_ok = model == MD_HMF || model == MD_SHEET1D;  // models with no divergence at eps = 0
   if (!eps_valid(model, eps)) {
-    fail_global(MD_EINVAL, "md_init: eps must be finite and %s %g, got %g", eps0_ok ? "0 or >=" : ">=", kEpsMin,
+    fail_global(MD_EINVAL, "%s: eps must be finite and %s %g, got %g", who, eps0_ok ? "0 or >=" : ">=", kEpsMin,
                 eps);
     return nullptr;
   }
   if (!is_finite(dt)) {
-    fail_global(MD_EINVAL, "md_init: dt must be finite");
+    fail_global(MD_EINVAL, "%s: dt must be finite", who);
     return nullptr;
   }
   md_ctx *c = new (std::nothrow) md_ctx();
@@ -197,6 +160,8 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
   c->model = model;
   c->dim = model == MD_GRAV2D ? 2 : model == MD_GRAV3D ? 3 : 1;
   c->N = N;
+  c->n_total = n_total;
+  c->row0 = row0;
   c->eps = eps;
   c->dt = dt;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -246,9 +211,64 @@ md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
   return c;
 }
 
+// ------------------------------------------------------------------ ABI ---
+
+extern "C" {
+
+const char *md_last_error(const md_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int md_last_status(void) { return g_status; }
+
+int md_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail_global(MD_EINVAL, "md_set_allocator: give both alloc and free, or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_user = user;
+  return MD_OK;
+}
+
+void md_free(md_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  dev_free(c->q);
+  dev_free(c->p);
+  dev_free(c->f);
+  dev_free(c->hmf_partials);
+  dev_free(c->hmf_m);
+  dev_free(c->hmf_ticket);
+  dev_free(c->hmf_cs);
+  dev_free(c->mirror[0]);
+  dev_free(c->mirror[1]);
+  dev_free(c->sk_slots);
+  dev_free(c->sk_tickets);
+  dev_free(c->sym_rowfull);
+  dev_free(c->sym_colslot);
+  dev_free(c->sym_chunks);
+  destroy_step_graphs(c);
+  dev_free(c->red);
+  dev_free(c->gw);
+  dev_free(c->shard_sums);
+  if (c->shard_event) cudaEventDestroy(c->shard_event);
+  if (c->host_scalars) cudaFreeHost(c->host_scalars);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+md_ctx *md_init(int model, int64_t N, double eps, double dt, uint64_t seed) {
+  return create_context(model, N, N, 0, eps, dt, seed, "md_init");
+}
+
 #define CHECK_CTX(c)                                              \
   do {                                                            \
     if (!(c)) return fail_global(MD_EINVAL, "NULL context");      \
+  } while (0)
+// calls that need the whole system's state, not one row shard's
+#define CHECK_WHOLE(c, what)                                                                          \
+  do {                                                                                                \
+    if ((c)->shard)                                                                                   \
+      return set_err((c), MD_ESTATE, "%s: not defined on a row shard (use the md_shard_* calls)", what); \
   } while (0)
 
 int md_set_precision(md_ctx *c, int prec) {
@@ -282,12 +302,8 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   else if (k == "r_fp64" && (value == 2 || value == 4)) c->pt.r_fp64 = (int)value;
   else if (k == "pair_ctas_per_sm" && value >= 0 && value <= 32) c->pt.ctas_per_sm = (int)value;
   else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
-  else if (k == "rcp_offload" && (value == 0 || value == 8)) c->pt.rcp_off = (int)value;
   else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
-  else if (k == "grav_tc" && value >= 0 && value <= 3) c->pt.grav_tc = (int)value;
   else if (k == "symmetric" && (value == 0 || value == 1)) c->pt.symmetric = (int)value;
-  else if (k == "rsqrt_offload" && value >= 0 && value <= 2) c->pt.rsqrt_off = (int)value;
-  else if (k == "sym_threads" && (value == 128 || value == 256 || value == 768)) c->pt.sym_threads = (int)value;
   else if (k == "step_graphs" && (value == 0 || value == 1)) c->use_graphs = value != 0;
   else return set_err(c, MD_EINVAL, "unknown tuning key or value: %s=%lld", key, (long long)value);
   return MD_OK;
@@ -302,6 +318,7 @@ static int invalidate(md_ctx *c) {
   c->fsal_valid = false;
   c->hmf_m_valid = false;
   c->mirror_valid = false;
+  c->shard_primed = false;
   return MD_OK;
 }
 
@@ -343,6 +360,7 @@ int md_get_state_device(md_ctx *c, double *q, double *p) {
 
 int md_step(md_ctx *c, int64_t nsteps) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_step");
   if (nsteps < 0) return set_err(c, MD_EINVAL, "md_step: nsteps < 0");
   return integrate(c, nsteps);
 }
@@ -491,6 +509,7 @@ void md_yoshida(double *c4) {
 
 int md_stage(md_ctx *c, double b, double d) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_stage");
   if (!is_finite(b) || !is_finite(d)) return set_err(c, MD_EINVAL, "md_stage: non-finite coefficient");
   const double h = c->dt;
   if (c->model == MD_HMF)
@@ -509,6 +528,7 @@ int md_stage(md_ctx *c, double b, double d) {
 
 int md_force_device(md_ctx *c, double *f) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_force");
   if (!f) return set_err(c, MD_EINVAL, "md_force_device: NULL output");
   if (c->model == MD_HMF) return hmf_stage(c, STAGE_FORCE_ONLY, 0.0, 0.0, f);
   return pair_stage(c, STAGE_FORCE_ONLY, 0.0, 0.0, f);
@@ -516,6 +536,7 @@ int md_force_device(md_ctx *c, double *f) {
 
 int md_force(md_ctx *c, double *f) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_force");
   if (!f) return set_err(c, MD_EINVAL, "md_force: NULL output");
   int rc = md_force_device(c, c->f);
   if (rc) return rc;
@@ -531,6 +552,7 @@ int md_force(md_ctx *c, double *f) {
 
 int md_energy(md_ctx *c, double *K, double *V) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_energy");
   int rc;
   double *d = c->hmf_m + 8;  // device scalars [8..11]
   if ((rc = kinetic_fp64(c, d))) return rc;
@@ -564,6 +586,7 @@ int md_energy(md_ctx *c, double *K, double *V) {
 
 int md_magnetization(md_ctx *c, double *mx, double *my) {
   CHECK_CTX(c);
+  CHECK_WHOLE(c, "md_magnetization");
   if (c->model != MD_HMF && c->model != MD_RING)
     return set_err(c, MD_EINVAL, "md_magnetization: defined for the HMF and Ring models only");
   double *d = c->hmf_m + 12;

@@ -744,7 +744,6 @@ int refresh_mirrors(md_batch *b) {
   for (md_ctx *c : b->ctx) {
     c->prec = b->prec;
     c->pt.ring_tc = sym;  // symmetric form: tensor-core Ring records; one-sided: interleaved
-    c->pt.grav_tc = 0;    // 2D parts read interleaved records
     c->mirror_cur = b->cur;
     int rc = mirror_refresh(c);
     if (rc) return berr(b, rc, "%s", c->err.c_str());

@@ -297,6 +297,15 @@ int kinetic_fp64(md_ctx *c, double *d_out) {
   return MD_OK;
 }
 
+// Deterministic FP64 (1/2) sum of x[i]^2 over x[0..n) into device *d_out.
+int half_sumsq_fp64(md_ctx *c, const double *x, int64_t n, double *d_out) {
+  int g = grid_sum(c, n);
+  if (g > c->hmf_grid_max) g = c->hmf_grid_max;
+  sum_kernel<true><<<g, NT, 0, c->stream>>>(x, n, c->hmf_partials, d_out, c->hmf_ticket);
+  MD_LAUNCHED(c);
+  return MD_OK;
+}
+
 // Deterministic FP64 sum of x[0..n) into device *d_out.
 int sum_fp64(md_ctx *c, const double *x, int64_t n, double *d_out) {
   int g = grid_sum(c, n);

@@ -19,6 +19,7 @@
 extern "C" int md_grad(md_ctx *c, int observable, int64_t nsteps, int checkpoint_every, double *grad_q,
                        double *grad_p, double *grad_eps, double *value) {
   if (!c) return set_err(nullptr, MD_EINVAL, "md_grad: NULL context");
+  if (c->shard) return set_err(c, MD_ESTATE, "md_grad: not defined on a row shard (use the md_shard_* calls)");
   if (observable != MD_OBS_KINETIC && observable != MD_OBS_MAGNETIZATION)
     return set_err(c, MD_EINVAL, "md_grad: unknown observable %d", observable);
   if (c->model == MD_SHEET1D && !(c->eps > 0.0))

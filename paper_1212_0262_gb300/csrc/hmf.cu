@@ -42,6 +42,7 @@ struct HmfArgs {
   double *fout;  // STAGE_FORCE_ONLY output
   double2 *cs;   // FP64 path: (cos, sin) of the current angles, rewritten by drifts
   int rev;       // sweep the particles from the top end down
+  int nsum;      // row shard: m_in holds nsum (sum cos, sum sin) pairs, one per rank
 };
 
 // One particle of a stage.  MIXED: FP64 state update, FP32 sine/cosine of the
@@ -119,9 +120,17 @@ __device__ __forceinline__ void grid_finish(double sc, double ss, double *partia
   }
 }
 
-template <bool MIXED, int MODE>
+// SHARD: the magnetization is the sum of every rank's pair in m_in, added in rank
+// order (the same value on every rank), over the whole system's N (invN).
+template <bool MIXED, int MODE, bool SHARD = false>
 __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
-  const double mx = a.m_in[0] * a.invN, my = a.m_in[1] * a.invN;
+  double sx = a.m_in[0], sy = a.m_in[1];
+  if constexpr (SHARD)
+    for (int r = 1; r < a.nsum; r++) {
+      sx += a.m_in[2 * r];
+      sy += a.m_in[2 * r + 1];
+    }
+  const double mx = sx * a.invN, my = sy * a.invN;
   const float mxf = (float)mx, myf = (float)my, dtf = (float)a.drift;
   float acf = 0.f, asf = 0.f;
   double acd = 0.0, asd = 0.0;
@@ -250,6 +259,7 @@ int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
   // the lines the previous one wrote last, which are still in L2 (dirty lines that
   // are overwritten before eviction are never written back either).
   a.rev = c->hmf_rev;
+  a.nsum = 1;
   c->hmf_rev ^= 1;
   auto kern = hmf_stage_kernel<MIXED, MODE>;
   // Mixed stages: 4 CTAs of 256 threads per SM measured fastest on GB300 at N = 5e7
@@ -312,6 +322,82 @@ int hmf_prime(md_ctx *c) {
   c->hmf_m_valid = true;
   c->hmf_m_prec = c->prec;
   return MD_OK;
+}
+
+// ------------------------------------------------------------ row shards ---
+//
+// A row shard (md_shard_*) holds rows [row0, row0 + N) of a system of n_total
+// particles.  Its stages read the magnetization from every rank's partial sums
+// (shard_sums[cur][rank], in rank order) and write the sums of their own new angles
+// to shard_sums[1 - cur][rank]; the exchange between stages copies the other ranks'
+// pairs in (Sec. 3.1, last paragraph: partial magnetizations per GPU, summed).
+
+int hmf_shard_prime(md_ctx *c) {
+  const size_t sums_bytes = sizeof(double) * 4 * (size_t)c->shard_nranks;
+  if (!c->shard_sums) {
+    c->shard_sums = (double *)dev_alloc(sums_bytes);
+    if (!c->shard_sums) return set_err(c, MD_ENOMEM, "HMF shard sums: %zu bytes", sums_bytes);
+  }
+  MD_CUDA(c, cudaMemsetAsync(c->shard_sums, 0, sums_bytes, c->stream));
+  c->shard_cur = 0;
+  double *out = c->shard_sums + 2 * c->shard_rank;
+  if (c->prec == MD_MIXED) {
+    auto kern = hmf_sums_kernel<true>;
+    int g = grid_for(c, (const void *)kern, c->N);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr);
+  } else {
+    const size_t need = sizeof(double2) * (size_t)c->N;
+    if (need > c->hmf_cs_bytes) {
+      dev_free(c->hmf_cs);
+      c->hmf_cs = (double *)dev_alloc(need);
+      c->hmf_cs_bytes = c->hmf_cs ? need : 0;
+      if (!c->hmf_cs) return set_err(c, MD_ENOMEM, "HMF (cos, sin) buffer: %zu bytes", need);
+    }
+    auto kern = hmf_sums_kernel<false>;
+    int g = grid_for(c, (const void *)kern, c->N);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs);
+  }
+  MD_LAUNCHED(c);
+  c->hmf_m_valid = false;  // md_step's own sums are not kept on a shard
+  return MD_OK;
+}
+
+namespace {
+template <bool MIXED, int MODE>
+int launch_shard_stage(md_ctx *c, double kick, double drift, double *fout) {
+  const int P = c->shard_nranks;
+  HmfArgs a;
+  a.q = c->q;
+  a.p = c->p;
+  a.N = c->N;
+  a.invN = 1.0 / (double)c->n_total;
+  a.m_in = c->shard_sums + 2 * P * c->shard_cur;
+  a.nsum = P;
+  a.kick = kick;
+  a.drift = drift;
+  a.partials = c->hmf_partials;
+  a.m_out = c->shard_sums + 2 * (P * (1 - c->shard_cur) + c->shard_rank);
+  a.ticket = c->hmf_ticket;
+  a.fout = fout;
+  a.cs = (double2 *)c->hmf_cs;
+  a.rev = c->hmf_rev;
+  c->hmf_rev ^= 1;
+  auto kern = hmf_stage_kernel<MIXED, MODE, true>;
+  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1, MIXED ? 4 : 0);
+  kern<<<g, NT, 0, c->stream>>>(a);
+  MD_LAUNCHED(c);
+  if (MODE == STAGE_KICK_DRIFT) c->shard_cur = 1 - c->shard_cur;
+  return MD_OK;
+}
+}  // namespace
+
+int hmf_shard_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
+  const bool mixed = c->prec == MD_MIXED;
+  if (mode == STAGE_FORCE_ONLY)
+    return mixed ? launch_shard_stage<true, STAGE_FORCE_ONLY>(c, 0.0, 0.0, fout)
+                 : launch_shard_stage<false, STAGE_FORCE_ONLY>(c, 0.0, 0.0, fout);
+  return mixed ? launch_shard_stage<true, STAGE_KICK_DRIFT>(c, kick, drift, nullptr)
+               : launch_shard_stage<false, STAGE_KICK_DRIFT>(c, kick, drift, nullptr);
 }
 
 int hmf_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {

@@ -36,7 +36,8 @@ __device__ __forceinline__ double gauss(uint64_t seed, uint64_t k) {
 
 struct IcArgs {
   double *q, *p;
-  int64_t N;
+  int64_t N;         // rows held (leading dimension of q and p)
+  int64_t Ng, row0;  // the whole system's size and the global index of row 0 (counters)
   int kind;
   uint64_t seed;
   double a0, a1, a2, a3;  // recipe parameters (widths and offsets precomputed on the host)
@@ -47,7 +48,7 @@ __global__ void ic_kernel(IcArgs a) {
   const int64_t N = a.N;
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
-    const uint64_t ui = (uint64_t)i, un = (uint64_t)N;
+    const uint64_t ui = (uint64_t)(a.row0 + i), un = (uint64_t)a.Ng;
     switch (a.kind) {
     case MD_IC_WATERBAG:  // a0 = th width, a1 = th_lo, a2 = p width, a3 = p_lo
       a.q[i] = affine(u01(a.seed, ui), a.a0, a.a1);
@@ -100,6 +101,8 @@ int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed) {
   a.q = c->q;
   a.p = c->p;
   a.N = c->N;
+  a.Ng = c->n_total;
+  a.row0 = c->row0;
   a.kind = kind;
   a.seed = seed;
   a.a0 = a.a1 = a.a2 = a.a3 = 0.0;
@@ -159,5 +162,6 @@ int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed) {
   c->fsal_valid = false;
   c->hmf_m_valid = false;
   c->mirror_valid = false;
+  c->shard_primed = false;
   return MD_OK;
 }

@@ -20,15 +20,8 @@ struct PairTuning {
   int r_mixed = 8;    // i-particles per thread, FP32 pair path
   int r_fp64 = 2;     // i-particles per thread, FP64 pair path
   int tj = 256;       // j-tile (particles staged in shared memory per unit)
-  int rcp_off = 0;    // 2D FP32: every rcp_off-th pair of j's takes 1/x on the FMA pipe (0: never)
   int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
-  int grav_tc = 0;    // 2D FP32: coordinate differences from tensor-core MMAs (exact 3-way TF32 split);
-                      // symmetric kernel: 1: 4 m-blocks per warp, 128 threads; 2: 2 m-blocks, 256 threads;
-                      // 3: as 1 with registers capped for 3 CTAs per SM
   int symmetric = 1;  // forward stages: each unordered pair once (Newton's third law)
-  int rsqrt_off = 0;  // symmetric Ring kernel: items of 8 per n-block with the rsqrt on the FMA pipe
-  int sym_threads = 128;  // symmetric Ring kernel: 128 threads, 4 m-blocks per warp; 256: 2 m-blocks;
-                          // 768: 256 threads with registers capped for 3 CTAs per SM
   int ctas_per_sm = 0;  // 0: occupancy-derived
 };
 
@@ -112,7 +105,25 @@ struct md_ctx {
   StepGraphKey step_key[2];
   int64_t step_graph_launches[2] = {0, 0};
   bool use_graphs = true;
+
+  // Row shard (md_shard_*): the state holds rows [row0, row0 + N) of a system of
+  // n_total particles split among shard_nranks ranks (n_total == N, row0 == 0 for a
+  // whole system).  Ring / 2D keep the whole position mirror (n_total records); HMF
+  // keeps every rank's (sum cos, sum sin) in shard_sums[2][nranks][2] (ping-pong).
+  bool shard = false;
+  int shard_rank = 0, shard_nranks = 1;
+  int64_t n_total = 0, row0 = 0;
+  double *shard_sums = nullptr;
+  int shard_cur = 0;
+  bool shard_primed = false;       // this rank's segment of the exchange buffer is written
+  int shard_prec = -1;             // precision the shard was primed in
+  cudaEvent_t shard_event = nullptr;
 };
+
+constexpr int kMaxShards = 64;
+// Ring / 2D row shards start on multiples of this many rows (whole mirror record
+// groups and whole i-tiles of every pair kernel).
+constexpr int64_t kShardRowAlign = 1024;
 
 // ------------------------------------------------------------ host helpers --
 
@@ -202,11 +213,27 @@ int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc);       // stream-K s
 bool sym_applies(const md_ctx *c);
 int sym_pair_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
 
+// pairs.cu / hmf.cu: row shards (md_shard_*).  *_shard_prime writes this rank's segment of
+// the exchange buffer from its state; *_shard_stage runs one fused stage over the shard's
+// rows (STAGE_KICK_DRIFT, drift 0 allowed, or STAGE_FORCE_ONLY into fout); *_shard_segment
+// gives the exchange buffer and this rank's byte range in it.
+int pair_shard_prime(md_ctx *c);
+int pair_shard_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
+int pair_shard_segment(md_ctx *c, void **buf, size_t *off, size_t *bytes);
+int hmf_shard_prime(md_ctx *c);
+int hmf_shard_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
+
+// api.cu: a context for rows [row0, row0 + n_local) of a system of n_total particles
+// (the whole system when n_local == n_total), state drawn with the global counters.
+md_ctx *create_context(int model, int64_t n_local, int64_t n_total, int64_t row0, double eps, double dt,
+                       uint64_t seed, const char *who);
+
 // energy.cu
 int kinetic_fp64(md_ctx *c, double *d_out);                       // (1/2) sum p^2 into device out
 int pair_potential_fp64(md_ctx *c, double *d_out);                // i<j sum of Eq. 1 / Eq. 3
 int reduce_scratch(md_ctx *c, size_t bytes);
 int sum_fp64(md_ctx *c, const double *x, int64_t n, double *d_out);  // deterministic sum into device out
+int half_sumsq_fp64(md_ctx *c, const double *x, int64_t n, double *d_out);  // (1/2) sum x^2 into device out
 
 // ic.cu
 int ic_draw(md_ctx *c, int kind, const double *params, uint64_t seed);

@@ -43,7 +43,9 @@ namespace {
 
 // ============================================================ skeleton =====
 
-template <class Pol, int MODEL, bool MIXED, int MODE>
+// SHARD: the i-tiles cover the rows [a.row0, a.row0 + a.nrow) of a row shard (a.n_it
+// tiles of them) against every j of the global mirror; a.row0 is a multiple of TI.
+template <class Pol, int MODEL, bool MIXED, int MODE, bool SHARD = false>
 __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kernel(PairArgs a) {
   constexpr int R = Pol::R, TJ = Pol::TJ, NACC = Pol::NACC;
   constexpr int TILE_BYTES = TJ * Pol::JB;
@@ -68,7 +70,8 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
   typename Pol::State st;
   int64_t it = u0 / a.n_jt, jt = u0 % a.n_jt;
   bool row_from_start = (jt == 0);
-  int64_t i0 = it * TI;  // tile base; each thread's rows come from Pol::row_of
+  const int64_t ibase = SHARD ? a.row0 : 0;
+  int64_t i0 = ibase + it * TI;  // tile base; each thread's rows come from Pol::row_of
   Pol::load(st, a.mirror_in, i0);
   prefetch(0, jt);
 
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
     }
     __syncthreads();
     const int64_t j0 = jt * TJ;
-    const bool diag = Pol::MASK && (j0 < it * TI + TI) && (it * TI < j0 + TJ);
+    const bool diag = Pol::MASK && (j0 < i0 + TI) && (i0 < j0 + TJ);
     if (diag)
       Pol::template tile<true>(st, sbuf[buf], a, i0, j0);
     else
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
           double ex[NACC];
           Pol::total(st, r, ex);
           const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-          if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(a, i0 + lr, ex);
+          if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, ex);
         }
       } else {
         // partial coverage: publish, and let the last contributor finish
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
 #pragma unroll
           for (int r = 0; r < Pol::NR; r++) {
             const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE>(a, i0 + lr, tot[r]);
+            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, tot[r]);
           }
           if (threadIdx.x == 0) a.tickets[it] = 0u;
         }
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
         it++;
         jt = 0;
         row_from_start = true;
-        i0 = it * TI;
+        i0 = ibase + it * TI;
         Pol::load(st, a.mirror_in, i0);
       }
     }
@@ -244,19 +247,19 @@ __global__ void kick_drift_cached_kernel(double *__restrict__ q, double *__restr
 bool ring_tc(const md_ctx *c) { return c->model == MD_RING && c->prec == MD_MIXED && c->pt.ring_tc; }
 
 
-// Mirror record format of the forward stages: 0 interleaved, 1 Ring and 2 2D
-// tensor-core fragments.
-int mirror_format(const md_ctx *c) { return ring_tc(c) ? 1 : grav_tc(c) ? 2 : 0; }
+// Mirror record format of the forward stages: 0 interleaved, 1 Ring tensor-core
+// fragments.
+int mirror_format(const md_ctx *c) { return ring_tc(c) ? 1 : 0; }
 
 int64_t padded(int64_t N) { return (N + kPadMultiple - 1) / kPadMultiple * kPadMultiple; }
 
 int ensure_mirrors(md_ctx *c, bool adj) {
-  const int64_t Np = padded(c->N);
+  const int64_t Np = padded(c->n_total);  // a row shard keeps the whole system's mirror
   // the FP64 record bounds the FP32 one
   const size_t per = c->model == MD_RING      ? (adj ? 48 : 64)  // Ring forward: tensor-core record
                      : c->model == MD_GRAV3D  ? (adj ? 64 : 32)
                      : c->model == MD_SHEET1D ? (adj ? 16 : 8)
-                                              : (adj ? 32 : 64);  // 2D forward: tensor-core record
+                                              : (adj ? 32 : 16);
   const size_t need = (size_t)Np * per;
   if (need > c->mirror_bytes) {
     for (int b = 0; b < 2; b++) {
@@ -322,9 +325,9 @@ int dispatch_forward(md_ctx *c, PairArgs a) {
         return launch_streamk<RingTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
       }
       return launch_streamk<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
-    } else if (grav_tc(c)) return launch_streamk<GravTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
-    else if (c->pt.rcp_off == 8) return launch_streamk<GravMixed<8, 256, MODE, 8>, MODEL, MIXED, MODE>(c, a);
-    else return launch_streamk<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    } else {
+      return launch_streamk<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    }
   } else {
     if (c->pt.r_fp64 == 4) {
       if constexpr (MODEL == MD_RING) return launch_streamk<RingF64<4, 128, MODE>, MODEL, MIXED, MODE>(c, a);
@@ -367,13 +370,95 @@ int refresh(md_ctx *c, const double *lp) {
     else
       mirror_kernel<MD_SHEET1D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1, c->eps);
   } else {
-    if (mixed && !ADJ && grav_tc(c))
-      mirror_kernel<MD_GRAV2D, true, false, 2><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
-    else if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
+    if (mixed) mirror_kernel<MD_GRAV2D, true, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
     else mirror_kernel<MD_GRAV2D, false, ADJ, 0><<<blocks, threads, 0, c->stream>>>(c->q, lp, c->N, Np, m0, m1);
   }
   MD_LAUNCHED(c);
   return MD_OK;
+}
+
+// ------------------------------------------------------------ row shards ---
+//
+// A row shard (md_shard_*) owns rows [row0, row0 + N) of a system of n_total
+// particles and keeps the whole position mirror: its stages evaluate the forces on
+// its own rows against every j (the one-sided kernel, every ordered pair, as in the
+// paper's two-GPU scheme of Sec. 3.2, Fig. 2) and write the new records of its own
+// rows; the records of the other rows arrive by the exchange between stages.
+// Policies: the default one-sided shape of each model and precision.
+
+// Records of the shard's rows (global index row0 + i) into m0, and the padding
+// records past n_total into both buffers.
+template <int MODEL, bool MIXED, int FMT>
+__global__ void shard_mirror_kernel(const double *__restrict__ q, int64_t n, int64_t row0, int64_t n_total,
+                                    int64_t Npad, void *m0, void *m1) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  const int64_t work = n + (Npad - n_total);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < work; i += G) {
+    if (i < n) {
+      const double y = MODEL == MD_GRAV2D ? q[n + i] : 0.0;
+      write_record_fmt<MODEL, MIXED, false, FMT>(m0, row0 + i, q[i], y, 0.0, 0.0);
+    } else {
+      const int64_t g = n_total + (i - n);
+      write_pad_fmt<MODEL, MIXED, false, FMT>(m0, g);
+      write_pad_fmt<MODEL, MIXED, false, FMT>(m1, g);
+    }
+  }
+}
+
+template <class Pol, int MODEL, bool MIXED, int MODE>
+int launch_streamk_shard(md_ctx *c, PairArgs a) {
+  constexpr int64_t TI = (int64_t)NT * Pol::R;
+  static_assert(kPadMultiple % TI == 0, "shard rows start on whole i-tiles");
+  auto kern = streamk_kernel<Pol, MODEL, MIXED, MODE, true>;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, 0);
+  if (occ < 1) occ = 1;
+  if (c->pt.ctas_per_sm > 0 && c->pt.ctas_per_sm < occ) occ = c->pt.ctas_per_sm;
+  a.N = c->n_total;
+  a.row0 = c->row0;
+  a.nrow = c->N;
+  a.n_it = (c->N + TI - 1) / TI;
+  a.n_jt = (c->n_total + Pol::TJ - 1) / Pol::TJ;
+  a.U = a.n_it * a.n_jt;
+  int64_t P = (int64_t)c->nsm * occ;
+  if (P > a.U) P = a.U;
+  a.P = (int)P;
+  int rc = ensure_pair_buffers(c, (int)TI, a.P, Pol::NACC);
+  if (rc) return rc;
+  a.mirror_in = c->mirror[c->mirror_cur];
+  a.mirror_out = c->mirror[1 - c->mirror_cur];
+  a.q = c->q;
+  a.p = c->p;
+  a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;
+  a.slots = c->sk_slots;
+  a.tickets = c->sk_tickets;
+  kern<<<a.P, NT, 0, c->stream>>>(a);
+  MD_LAUNCHED(c);
+  if (MODE == STAGE_KICK_DRIFT) c->mirror_cur = 1 - c->mirror_cur;
+  return MD_OK;
+}
+
+template <int MODEL, bool MIXED, int MODE>
+int dispatch_shard(md_ctx *c, PairArgs a) {
+  if constexpr (MODEL == MD_RING) {
+    if constexpr (MIXED) {
+      if (c->pt.ring_tc) return launch_streamk_shard<RingTC<4, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+      return launch_streamk_shard<RingMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    } else {
+      return launch_streamk_shard<RingF64<2, 128, MODE>, MODEL, MIXED, MODE>(c, a);
+    }
+  } else {
+    if constexpr (MIXED) return launch_streamk_shard<GravMixed<8, 256, MODE>, MODEL, MIXED, MODE>(c, a);
+    else return launch_streamk_shard<GravF64<2, 128, MODE>, MODEL, MIXED, MODE>(c, a);
+  }
+}
+
+// Record format and bytes per particle of a shard's mirror.
+int shard_format(const md_ctx *c) { return (c->model == MD_RING && c->prec == MD_MIXED && c->pt.ring_tc) ? 1 : 0; }
+size_t shard_record_bytes(const md_ctx *c) {
+  const bool mixed = c->prec == MD_MIXED;
+  if (c->model == MD_RING) return mixed ? (shard_format(c) == 1 ? 64 : 16) : 32;
+  return mixed ? 8 : 16;
 }
 
 }  // namespace
@@ -499,9 +584,7 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
     if (mixed) kick_drift_cached_kernel<MD_SHEET1D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_SHEET1D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   } else {
-    if (mixed && grav_tc(c))
-      kick_drift_cached_kernel<MD_GRAV2D, true, 2><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
-    else if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
+    if (mixed) kick_drift_cached_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
     else kick_drift_cached_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->p, c->f, c->N, kick, drift, mo);
   }
   MD_LAUNCHED(c);
@@ -509,11 +592,70 @@ int kick_drift_cached(md_ctx *c, double kick, double drift) {
   return MD_OK;
 }
 
+int pair_shard_prime(md_ctx *c) {
+  if (c->model != MD_RING && c->model != MD_GRAV2D)
+    return set_err(c, MD_EINVAL, "row shards: Ring, 2D and HMF systems only");
+  int rc = ensure_mirrors(c, false);
+  if (rc) return rc;
+  const int64_t Np = padded(c->n_total);
+  const int threads = 256;
+  const int64_t work = c->N + (Np - c->n_total);
+  const int64_t blocks = std::min<int64_t>((work + threads - 1) / threads, (int64_t)c->nsm * 16);
+  c->mirror_cur = 0;
+  void *m0 = c->mirror[0], *m1 = c->mirror[1];
+  const bool mixed = c->prec == MD_MIXED;
+  if (c->model == MD_RING) {
+    if (mixed && shard_format(c) == 1)
+      shard_mirror_kernel<MD_RING, true, 1><<<blocks, threads, 0, c->stream>>>(c->q, c->N, c->row0, c->n_total, Np, m0, m1);
+    else if (mixed)
+      shard_mirror_kernel<MD_RING, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->N, c->row0, c->n_total, Np, m0, m1);
+    else
+      shard_mirror_kernel<MD_RING, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->N, c->row0, c->n_total, Np, m0, m1);
+  } else {
+    if (mixed)
+      shard_mirror_kernel<MD_GRAV2D, true, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->N, c->row0, c->n_total, Np, m0, m1);
+    else
+      shard_mirror_kernel<MD_GRAV2D, false, 0><<<blocks, threads, 0, c->stream>>>(c->q, c->N, c->row0, c->n_total, Np, m0, m1);
+  }
+  MD_LAUNCHED(c);
+  c->mirror_valid = false;  // holds only this shard's rows until the exchange; md_step's refresh must not trust it
+  c->mirror_fmt = shard_format(c);
+  return MD_OK;
+}
+
+int pair_shard_stage(md_ctx *c, int mode, double kick, double drift, double *fout) {
+  if (shard_format(c) != c->mirror_fmt)
+    return set_err(c, MD_ESTATE, "row shard: the record format changed (ring_tc); call md_shard_begin again");
+  PairArgs a{};
+  a.kick = kick;
+  a.drift = drift;
+  a.fout = fout;
+  const bool mixed = c->prec == MD_MIXED;
+  const bool fo = mode == STAGE_FORCE_ONLY;
+  if (c->model == MD_RING) {
+    if (mixed) return fo ? dispatch_shard<MD_RING, true, STAGE_FORCE_ONLY>(c, a) : dispatch_shard<MD_RING, true, STAGE_KICK_DRIFT>(c, a);
+    return fo ? dispatch_shard<MD_RING, false, STAGE_FORCE_ONLY>(c, a) : dispatch_shard<MD_RING, false, STAGE_KICK_DRIFT>(c, a);
+  }
+  if (mixed) return fo ? dispatch_shard<MD_GRAV2D, true, STAGE_FORCE_ONLY>(c, a) : dispatch_shard<MD_GRAV2D, true, STAGE_KICK_DRIFT>(c, a);
+  return fo ? dispatch_shard<MD_GRAV2D, false, STAGE_FORCE_ONLY>(c, a) : dispatch_shard<MD_GRAV2D, false, STAGE_KICK_DRIFT>(c, a);
+}
+
+int pair_shard_segment(md_ctx *c, void **buf, size_t *off, size_t *bytes) {
+  static_assert(kPadMultiple == kShardRowAlign, "shard boundaries fall on whole mirror groups and i-tiles");
+  const size_t rb = shard_record_bytes(c);
+  // the last rank's segment also holds the padding records past n_total
+  const int64_t hi = c->shard_rank == c->shard_nranks - 1 ? padded(c->n_total) : c->row0 + c->N;
+  *buf = c->mirror[c->mirror_cur];
+  *off = (size_t)c->row0 * rb;
+  *bytes = (size_t)(hi - c->row0) * rb;
+  return MD_OK;
+}
+
 extern "C" int md_force_kernel(const md_ctx *c) {
   if (!c) return -1;
   if (c->model == MD_HMF) return MD_KERNEL_HMF;
   if (c->prec != MD_MIXED) return sym_applies(c) ? MD_KERNEL_PAIRS_FP64_SYM : MD_KERNEL_PAIRS_FP64;
-  const bool tc = (ring_tc(c) && c->pt.r_mixed != 4) || grav_tc(c);
+  const bool tc = ring_tc(c) && c->pt.r_mixed != 4;
   if (sym_applies(c)) return tc ? MD_KERNEL_PAIRS_TC_SYM : MD_KERNEL_PAIRS_SYM;
   return tc ? MD_KERNEL_PAIRS_TC : MD_KERNEL_PAIRS;
 }

@@ -126,12 +126,6 @@ __device__ __forceinline__ void write_pad3(void *mirror, int64_t i) {
     write_record3<false>(mirror, i, 1.0e150, 1.0e150, 1.0e150);
 }
 
-// The 2D FP32 forward path takes its coordinate differences from the tensor cores
-// (the default tile shape only: r_mixed 8, every reciprocal on the SFU).
-inline bool grav_tc(const md_ctx *c) {
-  return c->model == MD_GRAV2D && c->prec == MD_MIXED && c->pt.grav_tc && c->pt.r_mixed == 8 && !c->pt.rcp_off;
-}
-
 // CTAs per SM that the one-sided stream-K kernel's register budget is set for: a
 // policy's STREAMK_MINB when it declares one, else its MINB (the budget of its symmetric
 // form), else 1 (the compiler's choice).  Budgeted, the one-sided FP32 kernels run 3-5%
@@ -169,6 +163,10 @@ struct PairArgs {
   double *lq, *lp;   // lambda_q, lambda_p (dim*N)
   double *epsacc;    // per-particle accumulated d O / d eps terms (N)
   double undo;       // kick coefficient (times dt) removed from p
+  // row shard (md_shard_*): the i-tiles cover global rows [row0, row0 + nrow) and the
+  // state arrays q, p, fout hold those rows only (leading dimension nrow); the
+  // mirror and N stay global
+  int64_t row0, nrow;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -396,46 +394,8 @@ struct RingMixed {
   }
 };
 
-// 1/s for two floats on the FMA pipe instead of the SFU: a bit-pattern seed
-// (0x7EF311C0 - bits(s), whose worst relative error over a binade is 5.1%,
-// found by direct search) and two cubic steps y <- y (1 + e + e^2), e = 1 - s y
-// (written with e' = s y - 1), each cubing the relative error: 5e-2 -> 1.3e-4
-// -> 1.1e-7.  Valid for normal positive s; +inf gives 0 like the SFU.
-__device__ __forceinline__ float2 rcp2_fma(float2 s) {
-  float2 y = make_float2(__uint_as_float(0x7EF311C0u - __float_as_uint(s.x)),
-                         __uint_as_float(0x7EF311C0u - __float_as_uint(s.y)));
-  const float2 m1 = f2(-1.f);
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const float2 e = __ffma2_rn(s, y, m1);
-    y = __ffma2_rn(y, __ffma2_rn(e, e, make_float2(-e.x, -e.y)), y);
-  }
-  if (isinf(s.x)) y.x = 0.f;  // padding records: 1/inf = 0 (the steps above give NaN there)
-  if (isinf(s.y)) y.y = 0.f;
-  return y;
-}
-
-// 1/sqrt(d) for two positive normal floats on the FMA pipe instead of the SFU: a
-// bit-pattern seed 0x5F376440 - (bits(d) >> 1) (worst relative error 3.4% over
-// two binades, found by direct search) and two cubically convergent steps
-// y <- y (1 + e/2 + 3 e^2 / 8), e = 1 - d y^2 (written with e' = d y^2 - 1):
-// 3.4e-2 -> 1.0e-4 -> 1.4e-7, about one FP32 ulp like rsqrt.approx.
-__device__ __forceinline__ float2 rsqrt2_fma(float2 d) {
-  float2 y = make_float2(__uint_as_float(0x5F376440u - (__float_as_uint(d.x) >> 1)),
-                         __uint_as_float(0x5F376440u - (__float_as_uint(d.y) >> 1)));
-  const float2 one = f2(1.f), m1 = f2(-1.f), mhalf = f2(-0.5f), c38 = f2(0.375f);
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const float2 e = __ffma2_rn(__fmul2_rn(d, y), y, m1);
-    y = __fmul2_rn(y, __ffma2_rn(e, __ffma2_rn(e, c38, mhalf), one));
-  }
-  return y;
-}
-
 // ------------------------------------------------------------ forward 2D FP32
-// OFF > 0: every OFF-th pair of j's takes its reciprocals from rcp2_fma, which
-// moves work from the SFU (the binding pipe of this kernel) to the FMA pipe.
-template <int R_, int TJ_, int MODE, int OFF = 0, int MINB_ = 4>
+template <int R_, int TJ_, int MODE, int MINB_ = 4>
 struct GravMixed {
   static constexpr int THREADS = NT, MINB = MINB_;  // CTA size and CTAs per SM of the register budget
   using ColT = float;                           // column partials of the symmetric form
@@ -444,7 +404,6 @@ struct GravMixed {
   static constexpr int NR = R;  // rows finished per thread
   static constexpr int FMT = 0;  // mirror record format
   __device__ static int row_of(int r) { return r * NT + (int)threadIdx.x; }
-  static_assert(OFF == 0 || (TJ / 2) % OFF == 0, "offload period must divide the tile");
   struct State {
     float2 x[R], y[R], fx[R], fy[R];
     CompSum cs[R][NACC];
@@ -468,7 +427,7 @@ struct GravMixed {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
-    auto body = [&](int k, bool fma_rcp) {
+    auto body = [&](int k) {
       const float4 X = sm[k];
       const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
 #pragma unroll
@@ -476,20 +435,13 @@ struct GravMixed {
         float2 dx = __fadd2_rn(st.x[r], nx);
         float2 dy = __fadd2_rn(st.y[r], ny);
         float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
-        float2 inv = fma_rcp ? rcp2_fma(s) : make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+        float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
         st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
         st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
       }
     };
-    if constexpr (OFF == 0) {
 #pragma unroll 2
-      for (int k = 0; k < TJ / 2; k++) body(k, false);
-    } else {
-      for (int k0 = 0; k0 < TJ / 2; k0 += OFF) {
-#pragma unroll
-        for (int kk = 0; kk < OFF; kk++) body(k0 + kk, kk == OFF - 1);
-      }
-    }
+    for (int k = 0; k < TJ / 2; k++) body(k);
 #pragma unroll
     for (int r = 0; r < R; r++) {
       csum_add2(st.cs[r][0], st.fx[r]);
@@ -503,7 +455,6 @@ struct GravMixed {
   // minus that sum).  Eight j's at a time: per lane 16 partial sums (4 j-pairs x
   // 2 components), reduced over the warp by a butterfly.
   __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
-    static_assert(OFF == 0, "the symmetric variant keeps every reciprocal on the SFU");
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1668,10 +1619,8 @@ __device__ __forceinline__ void write_tc_pad(void *mirror, int64_t i) {
   for (int k = 0; k < 8; k++) m[k] = m[64 + k] = 0.f;
 }
 
-template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 4, int OFFR_ = 0>
+template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 4>
 struct RingTC {
-  static constexpr int OFFR = OFFR_;          // symmetric tiles: (m-block, half) items per n-block
-                                              // whose rsqrt runs on the FMA pipe (rsqrt2_fma)
   static constexpr int THREADS = THREADS_;    // CTA size (the one-sided skeletons use NT)
   static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget is set for
   using ColT = float;                         // column partials of the symmetric form
@@ -1794,7 +1743,7 @@ struct RingTC {
             const float2 S = make_float2(dS[2 * h], dS[2 * h + 1]);
             const float2 sh = make_float2(dH[2 * h], dH[2 * h + 1]);
             const float2 d = __ffma2_rn(sh, sh, he);
-            const float2 y = (2 * r + h < OFFR) ? rsqrt2_fma(d) : make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+            const float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
             const float2 qq = __fmul2_rn(S, y);
             const float2 y2 = __fmul2_rn(y, y);
             st.acc[r][h] = __ffma2_rn(qq, y2, st.acc[r][h]);
@@ -1818,203 +1767,11 @@ struct RingTC {
   }
 };
 
-// ------------------------------------------------------------ forward 2D FP32, tensor cores
-// The coordinate differences dx = x_i - x_j, dy = y_i - y_j of a 16 x 8 block of
-// pairs are one m16n8k8 TF32 product each.  An FP32 coordinate is split exactly
-// into three TF32 parts, x = h + m + l (h = x rounded to TF32, m = the rest rounded
-// to TF32, l = what is left, at most 3 significant bits), laid along K:
-//   A row i:  [h_i, m_i, l_i, 1, 1, 1, 0, 0]
-//   B col j:  [1, 1, 1, -h_j, -m_j, -l_j, 0, 0]
-// so the product is x_i - x_j with exact TF32 products, rounded once more by the
-// FP32 accumulation.  What is left per pair on the FMA pipe is s = dx^2 + dy^2 + eps
-// (2 FFMA) and the force sums (2 FFMA per side), with one rcp on the SFU: the
-// subtraction of the plain kernel moves to the tensor pipe.
-// Record of the 8 particles of an n-block: per lane (g, t) of the B fragment the
-// pair (B[t][g], B[t+4][g]) for x, then for y (64 floats later): 512 bytes.
-
-__device__ __forceinline__ void tf32_split3(float x, float &h, float &m, float &l) {
-  h = __uint_as_float(tf32_rn(x));
-  const float r = x - h;  // exact
-  m = __uint_as_float(tf32_rn(r));
-  l = r - m;  // exact, and a TF32 value
-}
-
-__device__ __forceinline__ void write_tc2_record(void *mirror, int64_t i, float x, float y) {
-  float *m = (float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
-  float xh, xm, xl, yh, ym, yl;
-  tf32_split3(x, xh, xm, xl);
-  tf32_split3(y, yh, ym, yl);
-  float2 *X = (float2 *)m, *Y = (float2 *)(m + 64);
-  X[0] = make_float2(1.f, -xm);
-  X[1] = make_float2(1.f, -xl);
-  X[2] = make_float2(1.f, 0.f);
-  X[3] = make_float2(-xh, 0.f);
-  Y[0] = make_float2(1.f, -ym);
-  Y[1] = make_float2(1.f, -yl);
-  Y[2] = make_float2(1.f, 0.f);
-  Y[3] = make_float2(-yh, 0.f);
-}
-
-// padding: far away (|r|^2 overflows to inf, so 1/s = 0 and the term vanishes)
-__device__ __forceinline__ void write_tc2_pad(void *mirror, int64_t i) { write_tc2_record(mirror, i, 3.0e19f, 3.0e19f); }
-
-template <int RM_, int TJ_, int MODE, int THREADS_ = NT, int MINB_ = 2>
-struct GravTC {
-  static constexpr int THREADS = THREADS_;    // CTA size (the one-sided skeletons use NT)
-  static constexpr int MINB = MINB_;          // resident CTAs per SM the register budget is set for
-  using ColT = float;                         // column partials of the symmetric form
-  static constexpr int RM = RM_;              // 16-row m-blocks per warp
-  static constexpr int R = RM / 2 > 0 ? RM / 2 : 1;  // TI = THREADS * R = 16 RM rows per warp
-  static constexpr int TJ = TJ_, NACC = 2, JB = 64;
-  static constexpr bool MASK = true;
-  static constexpr int NR = 2 * RM;           // rows g and g+8 of each m-block
-  static constexpr int FMT = 2;               // 2D tensor-core fragment records
-  static_assert(THREADS * R == 16 * RM * (THREADS / 32), "tile rows: warps x RM m-blocks x 16");
-  static_assert(TJ % 16 == 0, "two n-blocks per column reduction");
-  __device__ static int mrow(int rr) {        // row offset in the tile of item rr = 2 r + h
-    const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
-    return w * 16 * RM + 16 * (rr >> 1) + g + 8 * (rr & 1);
-  }
-  __device__ static int row_of(int rr) { return (threadIdx.x & 3) == 0 ? mrow(rr) : -1; }
-  struct State {
-    unsigned aX[RM][4], aY[RM][4];
-    float2 acc[RM][2][2];  // [m-block][row g / g+8][x, y], columns 2t and 2t+1
-    CompSum cs[RM][2][2];
-  };
-  __device__ static void total(const State &st, int rr, double *out) {
-#pragma unroll
-    for (int d = 0; d < 2; d++) {
-      double v = csum_total(st.cs[rr >> 1][rr & 1][d]);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      v += __shfl_xor_sync(0xffffffffu, v, 2);
-      out[d] = v;
-    }
-  }
-  __device__ static void load(State &st, const void *mirror, int64_t i0) {
-    const int t = threadIdx.x & 3;
-#pragma unroll
-    for (int r = 0; r < RM; r++) {
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int64_t i = i0 + mrow(2 * r + h);
-        const float *m = (const float *)mirror + (i >> 3) * 128 + (i & 7) * 8;
-        // A row: [h, m, l, 1, 1, 1, 0, 0]; the record holds -m at 1, -l at 3, -h at 6
-        const float xa = (t == 0) ? -m[6] : (t == 1) ? -m[1] : (t == 2) ? -m[3] : 1.f;
-        const float ya = (t == 0) ? -m[70] : (t == 1) ? -m[65] : (t == 2) ? -m[67] : 1.f;
-        const float hi = (t < 2) ? 1.f : 0.f;  // A[row][t + 4]
-        st.aX[r][h] = __float_as_uint(xa);
-        st.aX[r][2 + h] = __float_as_uint(hi);
-        st.aY[r][h] = __float_as_uint(ya);
-        st.aY[r][2 + h] = __float_as_uint(hi);
-#pragma unroll
-        for (int d = 0; d < 2; d++) {
-          st.acc[r][h][d] = f2(0.f);
-          st.cs[r][h][d] = CompSum{0.f, 0.f};
-        }
-      }
-    }
-  }
-  __device__ static void flush(State &st) {
-#pragma unroll
-    for (int r = 0; r < RM; r++)
-#pragma unroll
-      for (int h = 0; h < 2; h++)
-#pragma unroll
-        for (int d = 0; d < 2; d++) {
-          csum_add2(st.cs[r][h][d], st.acc[r][h][d]);
-          st.acc[r][h][d] = f2(0.f);
-        }
-  }
-  template <bool DIAG>
-  __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
-    const float *sm = (const float *)smb;
-    const float2 e2 = f2((float)a.epsd);
-    const int lane = threadIdx.x & 31, t = lane & 3;
-#pragma unroll 2
-    for (int k = 0; k < TJ / 8; k++) {
-      const float2 bx = *(const float2 *)(sm + k * 128 + lane * 2);
-      const float2 by = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
-#pragma unroll
-      for (int r = 0; r < RM; r++) {
-        float dX[4], dY[4];
-        mma_tf32(dX, st.aX[r], __float_as_uint(bx.x), __float_as_uint(bx.y));
-        mma_tf32(dY, st.aY[r], __float_as_uint(by.x), __float_as_uint(by.y));
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-          const float2 dx = make_float2(dX[2 * h], dX[2 * h + 1]);  // row g + 8h, columns 2t, 2t+1
-          const float2 dy = make_float2(dY[2 * h], dY[2 * h + 1]);
-          const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
-          float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
-          if (DIAG) {
-            const int64_t i = i0 + mrow(2 * r + h), j = j0 + 8 * k + 2 * t;
-            if (i == j) inv.x = 0.f;
-            if (i == j + 1) inv.y = 0.f;
-          }
-          st.acc[r][h][0] = __ffma2_rn(dx, inv, st.acc[r][h][0]);
-          st.acc[r][h][1] = __ffma2_rn(dy, inv, st.acc[r][h][1]);
-        }
-      }
-    }
-    flush(st);
-  }
-  // Off-diagonal block of the Newton's-third-law variant: the i-rows as in tile<>,
-  // and for every j the sums over this warp's 16 RM rows of the same terms, into
-  // colsm[(warp TJ + j) 2 + component].  Per lane and n-block the columns 2t, 2t+1
-  // are summed over the lane's rows; two n-blocks at a time (8 values per lane)
-  // are then reduced over the 8 lanes g by a butterfly.
-  __device__ static void tile_sym(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
-    const float *sm = (const float *)smb;
-    const float2 e2 = f2((float)a.epsd);
-    const int lane = threadIdx.x & 31, t = lane & 3, w = threadIdx.x >> 5;
-#pragma unroll 1
-    for (int k2 = 0; k2 < TJ / 16; k2++) {
-      float v[8];
-#pragma unroll
-      for (int kk = 0; kk < 2; kk++) {
-        const int k = 2 * k2 + kk;
-        const float2 bx = *(const float2 *)(sm + k * 128 + lane * 2);
-        const float2 by = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
-        float2 cx = f2(0.f), cy = f2(0.f);
-#pragma unroll
-        for (int r = 0; r < RM; r++) {
-          float dX[4], dY[4];
-          mma_tf32(dX, st.aX[r], __float_as_uint(bx.x), __float_as_uint(bx.y));
-          mma_tf32(dY, st.aY[r], __float_as_uint(by.x), __float_as_uint(by.y));
-#pragma unroll
-          for (int h = 0; h < 2; h++) {
-            const float2 dx = make_float2(dX[2 * h], dX[2 * h + 1]);
-            const float2 dy = make_float2(dY[2 * h], dY[2 * h + 1]);
-            const float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
-            const float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
-            st.acc[r][h][0] = __ffma2_rn(dx, inv, st.acc[r][h][0]);
-            st.acc[r][h][1] = __ffma2_rn(dy, inv, st.acc[r][h][1]);
-            cx = __ffma2_rn(dx, inv, cx);
-            cy = __ffma2_rn(dy, inv, cy);
-          }
-        }
-        v[4 * kk + 0] = cx.x;
-        v[4 * kk + 1] = cx.y;
-        v[4 * kk + 2] = cy.x;
-        v[4 * kk + 3] = cy.y;
-      }
-      // lane (g, t) ends with value g = 4 kk + 2 component + column parity
-      const float sum = butterfly_sum<8, 16>(v, lane);
-      const int vn = lane >> 2;
-      const int j = 8 * (2 * k2 + (vn >> 2)) + 2 * t + (vn & 1);
-      colsm[(w * TJ + j) * 2 + ((vn >> 1) & 1)] = sum;
-    }
-    flush(st);
-  }
-};
-
 // Record writers by format: FMT 0 = interleaved FP32 / FP64 records above,
-// FMT 1 = Ring tensor-core fragment records, FMT 2 = 2D tensor-core fragment
-// records (FP32 forward stages only).
+// FMT 1 = Ring tensor-core fragment records (FP32 forward stages only).
 template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __device__ __forceinline__ void write_record_fmt(void *mirror, int64_t i, double x, double y, double vx, double vy) {
-  if constexpr (FMT == 2) {
-    write_tc2_record(mirror, i, (float)x, (float)y);
-  } else if constexpr (FMT == 1) {
+  if constexpr (FMT == 1) {
     const float r = (float)reduce_2pi(x);
     float s, c, a, g;
     sincos_small(r, &s, &c);
@@ -2026,9 +1783,7 @@ __device__ __forceinline__ void write_record_fmt(void *mirror, int64_t i, double
 }
 template <int MODEL, bool MIXED, bool ADJ, int FMT>
 __device__ __forceinline__ void write_pad_fmt(void *mirror, int64_t i) {
-  if constexpr (FMT == 2)
-    write_tc2_pad(mirror, i);
-  else if constexpr (FMT == 1)
+  if constexpr (FMT == 1)
     write_tc_pad(mirror, i);
   else
     write_pad<MODEL, MIXED, ADJ>(mirror, i);
@@ -2037,10 +1792,13 @@ __device__ __forceinline__ void write_pad_fmt(void *mirror, int64_t i) {
 // ============================================================ epilogues ====
 
 // Forward stages: kick, drift, new mirror record (or the force alone).
-template <int MODEL, bool MIXED, int MODE, int FMT>
+template <int MODEL, bool MIXED, int MODE, int FMT, bool SHARD = false>
 __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, const double *acc) {
   constexpr int D = dim_of<MODEL>();
-  if (i >= a.N) return;
+  // state index and leading dimension: global ones, or the shard's local rows
+  const int64_t li = SHARD ? i - a.row0 : i;
+  const int64_t ld = SHARD ? a.nrow : a.N;
+  if (li >= ld) return;
   const double scale = MODEL == MD_RING ? -1.0 / (8.0 * (double)a.N)
                        : MODEL == MD_GRAV3D ? -1.0 / (double)a.N
                                             : -2.0 / (double)a.N;
@@ -2049,18 +1807,18 @@ __device__ __forceinline__ void finish_forward(const PairArgs &a, int64_t i, con
   for (int d = 0; d < D; d++) f[d] = MODEL == MD_SHEET1D ? -acc[d] / (double)a.N : scale * acc[d];
   if constexpr (MODE == STAGE_FORCE_ONLY) {
 #pragma unroll
-    for (int d = 0; d < D; d++) a.fout[d * a.N + i] = f[d];
+    for (int d = 0; d < D; d++) a.fout[d * ld + li] = f[d];
     return;
   } else {
 #pragma unroll
     for (int d = 0; d < D; d++) {
-      const double pp = fma(a.kick, f[d], a.p[d * a.N + i]);
-      a.p[d * a.N + i] = pp;
+      const double pp = fma(a.kick, f[d], a.p[d * ld + li]);
+      a.p[d * ld + li] = pp;
       if (MODE == STAGE_KICK_DRIFT) {
-        x[d] = fma(a.drift, pp, a.q[d * a.N + i]);
-        a.q[d * a.N + i] = x[d];
+        x[d] = fma(a.drift, pp, a.q[d * ld + li]);
+        a.q[d * ld + li] = x[d];
       } else {
-        a.fout[d * a.N + i] = f[d];
+        a.fout[d * ld + li] = f[d];
       }
     }
   }
@@ -2173,7 +1931,7 @@ __device__ __forceinline__ void finish_tangent(const PairArgs &a, int64_t i, con
   if (a.drift != 0.0) write_adjoint_record<MODEL, MIXED>(a.mirror_out, i, x, v);
 }
 
-template <class Pol, int MODEL, bool MIXED, int MODE>
+template <class Pol, int MODEL, bool MIXED, int MODE, bool SHARD = false>
 __device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const double *acc) {
   if constexpr (MODE == STAGE_ADJOINT) {
     finish_adjoint<MODEL, MIXED>(a, i, acc);
@@ -2182,9 +1940,9 @@ __device__ __forceinline__ void finish(const PairArgs &a, int64_t i, const doubl
   } else if constexpr (MODEL == MD_SHEET1D && !MIXED) {
     // FP64 sheets at eps = 0: each of the n_jt TJ - N padding records added +1
     const double c0 = a.epsd > 0.0 ? acc[0] : acc[0] - (double)(a.n_jt * Pol::TJ - a.N);
-    finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, &c0);
+    finish_forward<MODEL, MIXED, MODE, Pol::FMT, SHARD>(a, i, &c0);
   } else {
-    finish_forward<MODEL, MIXED, MODE, Pol::FMT>(a, i, acc);
+    finish_forward<MODEL, MIXED, MODE, Pol::FMT, SHARD>(a, i, acc);
   }
 }
 

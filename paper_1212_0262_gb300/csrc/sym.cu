@@ -313,15 +313,7 @@ int sym_dispatch(md_ctx *c, PairArgs a) {
     if constexpr (MODEL == MD_RING) return launch_sym<RingF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
     else return launch_sym<GravF64<4, 128, MODE>, MODEL, false, MODE>(c, a);
   } else if constexpr (MODEL == MD_RING) {
-    if (c->pt.sym_threads == 256) return launch_sym<RingTC<2, 256, MODE, 256, 2>, MODEL, true, MODE>(c, a);
-    if (c->pt.sym_threads == 768) return launch_sym<RingTC<2, 256, MODE, 256, 3>, MODEL, true, MODE>(c, a);
-    if (c->pt.rsqrt_off == 1) return launch_sym<RingTC<4, 256, MODE, NT, 3, 1>, MODEL, true, MODE>(c, a);
-    if (c->pt.rsqrt_off == 2) return launch_sym<RingTC<4, 256, MODE, NT, 3, 2>, MODEL, true, MODE>(c, a);
     return launch_sym<RingTC<4, 256, MODE>, MODEL, true, MODE>(c, a);
-  } else if (grav_tc(c)) {
-    if (c->pt.grav_tc == 2) return launch_sym<GravTC<2, 256, MODE, 256, 2>, MODEL, true, MODE>(c, a);
-    if (c->pt.grav_tc == 3) return launch_sym<GravTC<4, 256, MODE, NT, 3>, MODEL, true, MODE>(c, a);
-    return launch_sym<GravTC<4, 256, MODE>, MODEL, true, MODE>(c, a);
   } else {
     return launch_sym<GravMixed<8, 256, MODE>, MODEL, true, MODE>(c, a);
   }
@@ -355,8 +347,8 @@ bool sym_applies(const md_ctx *c) {
     if (!c->pt.ring_tc || c->pt.ring_tc == 2 || c->pt.r_mixed == 4) return false;
     TI = 256, TJ = 256, colbytes = 4;
   } else if (c->model == MD_GRAV2D) {
-    if (c->pt.rcp_off || c->pt.r_mixed == 4) return false;
-    TI = grav_tc(c) ? 256 : 1024, TJ = 256, colbytes = 4;
+    if (c->pt.r_mixed == 4) return false;
+    TI = 1024, TJ = 256, colbytes = 4;
   } else {
     return false;
   }

@@ -181,25 +181,19 @@ class System:
         return dq, dp
 
     def lyapunov(self, nsteps: int, renorm_every: int = 10, seed: int = 0, dt: float | None = None) -> float:
-        """Largest Lyapunov exponent estimate: a seeded random tangent vector carried
-        along nsteps steps (advancing the state), renormalised every renorm_every
-        steps; the mean log growth rate per unit time."""
+        """Largest Lyapunov exponent estimate (md_lyapunov): a seeded random tangent
+        vector carried along nsteps steps (advancing the state), renormalised on the
+        device every renorm_every steps; the mean log growth rate per unit time."""
         from . import inputs
 
         n = self.dim * self.N
         d = inputs.uniform(seed, 0, 2 * n) - 0.5
-        d /= np.linalg.norm(d)
-        dq, dp = d[:n], d[n:]
-        total, done = 0.0, 0
-        while done < nsteps:
-            k = min(renorm_every, nsteps - done)
-            dq, dp = self.tangent_step(k, dq, dp)
-            norm = float(np.sqrt(np.dot(dq, dq) + np.dot(dp, dp)))
-            total += np.log(norm)
-            dq, dp = dq / norm, dp / norm
-            done += k
+        dq, dp = np.ascontiguousarray(d[:n]), np.ascontiguousarray(d[n:])
+        total = ctypes.c_double()
+        self._chk(B.load().md_lyapunov(self._h, int(nsteps), int(renorm_every), _ptr(dq), _ptr(dp),
+                                       ctypes.byref(total)))
         step_dt = dt if dt is not None else self._dt
-        return total / (nsteps * step_dt)
+        return total.value / (nsteps * step_dt)
 
     @property
     def launch_count(self) -> int:
@@ -295,3 +289,131 @@ class Ensemble:
     @property
     def launch_count(self) -> int:
         return int(B.load().md_batch_launch_count(self._h))
+
+
+def shard_range(model, N: int, rank: int, nranks: int):
+    """Rows [lo, hi) of rank `rank` of `nranks` (md_shard_range)."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    B.check(B.load().md_shard_range(_model(model), int(N), int(rank), int(nranks), ctypes.byref(lo),
+                                    ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+class ShardGroup:
+    """One system split by rows among `nranks` shard contexts held by this process
+    (md_shard_*): the paper's multi-GPU schemes (Sec. 3.1 last paragraph, Sec. 3.2
+    Fig. 2) with the exchange done by md_shard_exchange.  `devices` (optional) puts
+    rank r's context on device devices[r]; by default all ranks share the current
+    device."""
+
+    def __init__(self, model, N: int, eps: float, dt: float, seed: int, nranks: int, precision="fp64",
+                 devices=None):
+        import torch
+
+        lib = B.load()
+        self.model, self.N, self.nranks = _model(model), int(N), int(nranks)
+        self.dim = {2: 2, 3: 3}.get(self.model, 1)
+        self.ranges = [shard_range(self.model, self.N, r, self.nranks) for r in range(self.nranks)]
+        self._ctx = (ctypes.c_void_p * self.nranks)()
+        prev = torch.cuda.current_device() if devices else None
+        try:
+            for r in range(self.nranks):
+                if devices:
+                    torch.cuda.set_device(devices[r])
+                h = lib.md_shard_init(self.model, self.N, float(eps), float(dt), int(seed) & (2**64 - 1), r,
+                                      self.nranks)
+                if not h:
+                    self.close()
+                    raise B.MDError(lib.md_last_status() or B.MD_EINVAL, (lib.md_last_error(None) or b"").decode())
+                self._ctx[r] = h
+        finally:
+            if devices:
+                torch.cuda.set_device(prev)
+        self.set_precision(precision)
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None) is not None:
+            for r in range(self.nranks):
+                if self._ctx[r]:
+                    B.load().md_free(ctypes.c_void_p(self._ctx[r]))
+                    self._ctx[r] = None
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _h(self, r):
+        return ctypes.c_void_p(self._ctx[r])
+
+    def _chk(self, rc: int, r: int = 0) -> None:
+        B.check(rc, self._h(r))
+
+    def set_precision(self, precision) -> None:
+        for r in range(self.nranks):
+            self._chk(B.load().md_set_precision(self._h(r), _prec(precision)), r)
+
+    def set_tuning(self, key: str, value: int) -> None:
+        for r in range(self.nranks):
+            self._chk(B.load().md_set_tuning(self._h(r), key.encode(), int(value)), r)
+
+    def begin(self) -> None:
+        """md_shard_begin on every rank, then the exchange."""
+        lib = B.load()
+        for r in range(self.nranks):
+            self._chk(lib.md_shard_begin(self._h(r)), r)
+        self._chk(lib.md_shard_exchange(self._ctx, self.nranks))
+
+    def step(self, nsteps: int = 1) -> None:
+        self._chk(B.load().md_shard_step(self._ctx, self.nranks, int(nsteps)))
+
+    def stage(self, b: float, d: float) -> None:
+        """One fused stage on every rank, then the exchange (md_shard_begin first when needed)."""
+        lib = B.load()
+        for r in range(self.nranks):
+            self._chk(lib.md_shard_stage(self._h(r), float(b), float(d)), r)
+        self._chk(lib.md_shard_exchange(self._ctx, self.nranks))
+
+    def force(self) -> np.ndarray:
+        """Forces on all N particles (layout of md_force), each rank's rows from its shard."""
+        f = np.empty((self.dim, self.N))
+        for r, (lo, hi) in enumerate(self.ranges):
+            fr = np.empty(self.dim * (hi - lo))
+            self._chk(B.load().md_shard_force(self._h(r), _ptr(fr)), r)
+            f[:, lo:hi] = fr.reshape(self.dim, hi - lo)
+        return f.reshape(-1)
+
+    def get_state(self):
+        q, p = np.empty((self.dim, self.N)), np.empty((self.dim, self.N))
+        for r, (lo, hi) in enumerate(self.ranges):
+            n = self.dim * (hi - lo)
+            qr, pr = np.empty(n), np.empty(n)
+            self._chk(B.load().md_get_state(self._h(r), _ptr(qr), _ptr(pr)), r)
+            q[:, lo:hi], p[:, lo:hi] = qr.reshape(self.dim, -1), pr.reshape(self.dim, -1)
+        return q.reshape(-1), p.reshape(-1)
+
+    def set_state(self, q, p) -> None:
+        """Every rank's rows of the whole-system arrays q, p (then begin and exchange)."""
+        q, p = _f64(q).reshape(self.dim, self.N), _f64(p).reshape(self.dim, self.N)
+        for r, (lo, hi) in enumerate(self.ranges):
+            qr, pr = np.ascontiguousarray(q[:, lo:hi]), np.ascontiguousarray(p[:, lo:hi])
+            self._chk(B.load().md_set_state(self._h(r), _ptr(qr), _ptr(pr)), r)
+        self.begin()
+
+    def buffer(self, r: int):
+        """(device pointer, segment offset, segment bytes) of rank r's exchange buffer."""
+        buf, off, nb = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_size_t()
+        self._chk(B.load().md_shard_buffer(self._h(r), ctypes.byref(buf), ctypes.byref(off), ctypes.byref(nb)), r)
+        return buf.value, off.value, nb.value
+
+    def synchronize(self) -> None:
+        for r in range(self.nranks):
+            self._chk(B.load().md_synchronize(self._h(r)), r)

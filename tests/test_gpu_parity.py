@@ -225,17 +225,6 @@ def test_full_size_sampled_force_parity(model, N, eps, prec):
     s.close()
 
 
-@pytest.mark.parametrize("N", [33, 1000, 4097])
-def test_mixed_2d_force_with_fma_pipe_reciprocals(N):
-    """The 2D kernel variant that takes 1/8 of its reciprocals on the FMA pipe
-    (bit-pattern seed + two cubic Newton steps) keeps the mixed error bound."""
-    s, q, p = _sys(2, N, "mixed")
-    s.set_tuning("rcp_offload", 8)
-    f = s.force()
-    err, scale, _ = _force_err(2, q, f)
-    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
-
-
 @pytest.mark.parametrize("tc", [1, 2])
 @pytest.mark.parametrize("N", [1, 2, 33, 1000, 4097])
 def test_ring_tensor_core_force_error_bound(N, tc):

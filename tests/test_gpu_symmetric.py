@@ -120,34 +120,6 @@ def test_symmetric_full_size_sampled_force_parity(model, N, eps):
     s.close()
 
 
-@pytest.mark.parametrize("threads", [128, 256, 768])
-@pytest.mark.parametrize("N", [1, 255, 257, 1000, 4097])
-def test_symmetric_ring_cta_shapes(N, threads):
-    """The symmetric Ring kernel with 128-thread CTAs (4 m-blocks per warp) and
-    256-thread CTAs (2 m-blocks per warp; registers for 2 or 3 CTAs per SM)."""
-    s, q, _ = _sym(1, N)
-    s.set_tuning("sym_threads", threads)
-    f = s.force()
-    fo = ora.force(1, q, EPS[1])
-    scale = ora.force_abs(1, q, EPS[1])
-    err = np.abs(f - fo)
-    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
-
-
-@pytest.mark.parametrize("off", [1, 2])
-@pytest.mark.parametrize("N", [1, 257, 1000, 4097])
-def test_symmetric_ring_rsqrt_on_fma_pipe(N, off):
-    """Part of the reciprocal square roots from rsqrt2_fma (bit-pattern seed and two
-    cubic steps) instead of the SFU: same error bound."""
-    s, q, _ = _sym(1, N)
-    s.set_tuning("rsqrt_offload", off)
-    f = s.force()
-    fo = ora.force(1, q, EPS[1])
-    scale = ora.force_abs(1, q, EPS[1])
-    err = np.abs(f - fo)
-    assert np.all(err <= 2e-5 * scale + 1e-300), (err / np.maximum(scale, 1e-300)).max()
-
-
 def test_symmetric_falls_back_to_one_sided_beyond_the_column_cap():
     """Ring N = 1,572,864 needs 19.3 GB of column partials, beyond the 16 GiB cap: the
     one-sided tensor-core kernel runs instead, with the same error bound."""

@@ -55,3 +55,36 @@ def test_lyapunov_estimate_is_positive_and_stable_hmf():
         with System(0, 5000, 0.0, 0.1, 3) as s:
             vals.append(s.lyapunov(400, every, seed=1))
     assert vals[0] > 0.0 and abs(vals[0] - vals[1]) <= 1e-6 * abs(vals[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("model", [0, 1, 2, 3])
+def test_device_lyapunov_equals_the_host_renormalisation_loop(model, prec):
+    """md_lyapunov (tangent kept on the device, renormalised there) against the same
+    estimate made on the host around md_tangent_step (pinned above to central
+    differences of the oracle): the same state afterwards, bit for bit, and the same
+    sum of log norms to rounding; 37 steps in blocks of 10 (a shorter last block)."""
+    N, nsteps, every = 500, 37, 10
+    q0, p0 = inputs.default_state(model, N, 4)
+    n = q0.size
+    d = inputs.uniform(3, 0, 2 * n) - 0.5
+    with System(model, N, EPS[model], DT[model], 1, precision=prec) as a:
+        a.set_state(q0, p0)
+        lam = a.lyapunov(nsteps, every, seed=3)
+        qa, pa = a.get_state()
+    with System(model, N, EPS[model], DT[model], 1, precision=prec) as b:
+        b.set_state(q0, p0)
+        v = d / np.linalg.norm(d)
+        dq, dp = v[:n], v[n:]
+        total, done = 0.0, 0
+        while done < nsteps:
+            k = min(every, nsteps - done)
+            dq, dp = b.tangent_step(k, dq, dp)
+            norm = float(np.sqrt(np.dot(dq, dq) + np.dot(dp, dp)))
+            total += np.log(norm)
+            dq, dp = dq / norm, dp / norm
+            done += k
+        qb, pb = b.get_state()
+    assert np.array_equal(qa, qb) and np.array_equal(pa, pb)
+    ref = total / (nsteps * DT[model])
+    assert abs(lam - ref) <= 1e-9 * abs(ref), (lam, ref)
