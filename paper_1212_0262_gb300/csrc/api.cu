@@ -199,6 +199,11 @@ md_ctx *create_context(int model, int64_t N, int64_t n_total, int64_t row0, doub
     md_free(c);
     return nullptr;
   }
+  if (model == MD_HMF && hmf_sincos_table(c) != MD_OK) {
+    g_err = c->err;
+    md_free(c);
+    return nullptr;
+  }
   const int kind = model == MD_HMF || model == MD_SHEET1D ? MD_IC_WATERBAG
                    : model == MD_RING                    ? MD_IC_RING
                    : model == MD_GRAV2D                  ? MD_IC_DISK

@@ -28,6 +28,8 @@
 namespace {
 
 constexpr int kGraphSteps = 10;  // even: three mirror flips per step keep the parity
+// Record bytes of the systems one wave of the Newton's-third-law pair phase works on.
+constexpr int64_t kWaveRecordBytes = 32ll << 20;
 
 struct SysDesc {
   double *q, *p, *f;
@@ -50,6 +52,7 @@ struct PartArgs {
   double *slots;
   unsigned *tickets;
   // symmetric form
+  int waves;         // virtual CTAs per physical CTA: P = waves x grid, CTA c runs c, grid + c, ...
   int m;             // TI / TJ of the part
   int64_t nfin;      // finish CTAs of the part
   double *rowfull;   // [rows][NACC][TI]
@@ -409,10 +412,13 @@ constexpr int sym_smem_bytes() {
 
 // One launch per part, each sized by its own occupancy (the parts' systems are
 // disjoint, so the launches simply follow each other on the stream).
+// The part's P = waves x gridDim.x stream-K ranges are virtual CTAs: CTA c runs c,
+// gridDim.x + c, ... in turn, so at any time all CTAs work in the same 1/waves of the
+// unit list (the same few systems), whose j-records then stay in L2.
 template <class Pol>
 __global__ void __launch_bounds__(NT, Pol::MINB) batch_sym_pairs_kernel(PartArgs part) {
   __shared__ __align__(16) unsigned char smem[sym_smem_bytes<Pol>()];
-  batch_sym_pairs<Pol>(part, blockIdx.x, smem);
+  for (int w = 0; w < part.waves; w++) batch_sym_pairs<Pol>(part, (int64_t)w * gridDim.x + blockIdx.x, smem);
 }
 
 template <class PolR, class PolG, int MODE>
@@ -453,6 +459,7 @@ struct md_batch {
   // unit / row layout uploaded for tile shapes and form (layout_key)
   int64_t layout_key[5] = {-1, -1, -1, -1, -1};
   int64_t Ur = 0, Ug = 0, rows_r = 0, rows_g = 0, nfin_r = 0, nfin_g = 0;
+  int64_t rec_bytes_r = 0, rec_bytes_g = 0;  // forward-record bytes of each part's systems
   int nr = 0;
   int mirror_sym = -1;  // form the mirrors were written for (Ring records differ)
   double *rowfull = nullptr;  // Newton's-third-law form: row partials, column partials, chunk sums
@@ -496,6 +503,7 @@ void drop_graphs(md_batch *b) {
 int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym, std::vector<SysDesc> &hs) {
   hs.clear();
   b->Ur = b->Ug = b->rows_r = b->rows_g = b->nfin_r = b->nfin_g = 0;
+  b->rec_bytes_r = b->rec_bytes_g = 0;
   b->nr = 0;
   for (int pass = 0; pass < 2; pass++) {
     const int want = pass == 0 ? MD_RING : MD_GRAV2D;
@@ -524,6 +532,8 @@ int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym
       U += sym ? sym_rowstart(d.n_it, d.n_jt, (int)m) : d.n_it * d.n_jt;
       rows += d.n_it;
       nfin += d.n_it * d.nc;
+      // forward records: Ring tensor-core fragments (symmetric form) or interleaved FP32
+      (pass == 0 ? b->rec_bytes_r : b->rec_bytes_g) += c->N * (pass == 0 ? (sym ? 64 : 16) : 8);
       hs.push_back(d);
       if (pass == 0) b->nr++;
     }
@@ -615,8 +625,17 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   auto kern_r = batch_sym_pairs_kernel<PolR>;
   auto kern_g = batch_sym_pairs_kernel<PolG>;
   const int occ_r = occupancy(b, (const void *)kern_r), occ_g = occupancy(b, (const void *)kern_g);
-  const int64_t Pr = std::min<int64_t>((int64_t)b->nsm * occ_r, b->Ur);
-  const int64_t Pg = std::min<int64_t>((int64_t)b->nsm * occ_g, b->Ug);
+  const int64_t Gr = std::min<int64_t>((int64_t)b->nsm * occ_r, b->Ur);
+  const int64_t Gg = std::min<int64_t>((int64_t)b->nsm * occ_g, b->Ug);
+  // waves: the part's j-records over about a quarter of L2 (129 MB), at least 16 units
+  // per virtual CTA
+  auto waves_of = [&](int64_t rec_bytes, int64_t U, int64_t G) -> int {
+    int64_t w = (rec_bytes + kWaveRecordBytes - 1) / kWaveRecordBytes;
+    if (w > U / (16 * (G > 0 ? G : 1))) w = U / (16 * (G > 0 ? G : 1));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(w, 16));
+  };
+  const int Wr = waves_of(b->rec_bytes_r, b->Ur, Gr), Wg = waves_of(b->rec_bytes_g, b->Ug, Gg);
+  const int64_t Pr = Gr * Wr, Pg = Gg * Wg;  // virtual CTAs
   const size_t slot_r = (size_t)Pr * 2 * NAr * TIr, slot_g = (size_t)Pg * 2 * NAg * TIg;
   const size_t row_r = (size_t)b->rows_r * NAr * TIr, row_g = (size_t)b->rows_g * NAg * TIg;
   const size_t col_r = (size_t)b->Ur * PolR::TJ * NAr, col_g = (size_t)b->Ug * PolG::TJ * NAg;
@@ -632,6 +651,7 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ar.nsys = b->nr;
   ar.U = b->Ur;
   ar.P = (int)Pr;
+  ar.waves = Wr;
   ar.m = (int)(TIr / PolR::TJ);
   ar.nfin = b->nfin_r;
   ar.slots = b->slots;
@@ -643,6 +663,7 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ag.nsys = b->nsys - b->nr;
   ag.U = b->Ug;
   ag.P = (int)Pg;
+  ag.waves = Wg;
   ag.m = (int)(TIg / PolG::TJ);
   ag.nfin = b->nfin_g;
   ag.slots = b->slots + slot_r;
@@ -653,12 +674,12 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ar.cur = ag.cur = b->cur;
   ar.b = ag.b = bc;
   ar.d = ag.d = dc;
-  if (Pr > 0) {
-    kern_r<<<(int)Pr, NT, 0, b->stream>>>(ar);
+  if (Gr > 0) {
+    kern_r<<<(int)Gr, NT, 0, b->stream>>>(ar);
     b->launches++;
   }
-  if (Pg > 0) {
-    kern_g<<<(int)Pg, NT, 0, b->stream>>>(ag);
+  if (Gg > 0) {
+    kern_g<<<(int)Gg, NT, 0, b->stream>>>(ag);
     b->launches++;
   }
   batch_sym_finish_kernel<PolR, PolG, MODE><<<(unsigned)(b->nfin_r + b->nfin_g), kFinishThreadsB, 0, b->stream>>>(ar, ag);

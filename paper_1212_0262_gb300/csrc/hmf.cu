@@ -20,15 +20,83 @@
 // Reduction: per-thread sums, warp shuffles and a block tree give one FP64
 // partial per CTA; the last CTA to finish (atomic ticket, no waiting) adds the
 // partials in CTA order, so the result is deterministic.
+#include <math.h>
+
+#include <mutex>
+
 #include "md_internal.cuh"
 
 namespace {
+
+constexpr int kMaxDevicesTab = 64;
 
 constexpr int NT = kStreamThreads;
 constexpr int UNROLL = 2;  // double2 loads of theta and of p in flight per thread
 // Mixed sums: a thread adds at most kFlush angles' cosines and sines in FP32 before moving
 // them into its FP64 partial, so their rounding does not grow with N / (threads).
 constexpr int kFlush = 256;
+
+// ------------------------------------------------ FP64 sine and cosine ------
+//
+// Table-driven argument reduction (Tang, "Table-driven implementation of the
+// exponential function", ACM TOMS 15, 1989; used for sine and cosine by Gal and
+// Bachelis, ACM TOMS 17, 1991): theta = k h + r with h = pi/2048, k the nearest
+// integer to theta / h and |r| <= h/2 (1 + 1e-5) < 7.7e-4, then
+//   sin(theta) = S_k (1 + cm) + C_k sr,   cos(theta) = C_k (1 + cm) - S_k sr
+// with (S_k, C_k) = (sin, cos)(k h) from a 4096-entry FP64 table (k mod 4096) and
+//   sr = sin r = r - r^3 / 6                    (first omitted term r^5/5! < 2.3e-18)
+//   cm = cos r - 1 = r^2 (-1/2 + r^2 / 24)      (first omitted term r^6/6! < 3e-22)
+// k comes from the 1.5 * 2^52 rounding constant (its integer in the low mantissa bits),
+// and r = theta - k h from two FMAs with h split into h1 = fl(h) and h2 = fl(h - h1)
+// (each FMA forms k h_i exactly and rounds once; h - h1 - h2 is below 2e-36).
+// 13 FP64 operations instead of a full range reduction and two longer polynomials;
+// |theta| >= 2^30 (where k's rounding leaves |r| less tightly bounded), infinities and
+// NaN (found from the exponent bits, on the integer pipe) use sincos.  The table
+// (64 KB) sits in dynamic shared memory of the kernels that use it.
+constexpr int kTabN = 4096;
+constexpr int kTabBytes = kTabN * (int)sizeof(double2);
+constexpr double kTabH1 = 0x1.921fb54442d18p-10;  // pi / 2048 rounded to double
+constexpr double kTabH2 = 0x1.1a62633145c07p-64;  // pi / 2048 - kTabH1
+constexpr double kTabInvH = 0x1.45f306dc9c883p+9; // 2048 / pi
+constexpr double kRint = 6755399441055744.0;      // 1.5 * 2^52
+
+__device__ double2 g_sincos_tab[kTabN];  // (sin, cos)(k pi / 2048), k = 0 .. 4095
+
+__device__ __forceinline__ void sincos_tab(double th, const double2 *__restrict__ tab, double *sp, double *cp) {
+  if (((__double2hiint(th) >> 20) & 0x7ff) >= 1023 + 30) {  // |theta| >= 2^30, inf or NaN
+    sincos(th, sp, cp);
+    return;
+  }
+  const double m = fma(th, kTabInvH, kRint);
+  const int idx = __double2loint(m) & (kTabN - 1);
+  const double k = m - kRint;
+  const double r = fma(-k, kTabH2, fma(-k, kTabH1, th));
+  const double r2 = r * r;
+  const double sr = fma(r2 * r, -1.0 / 6.0, r);
+  const double cm = r2 * fma(r2, 1.0 / 24.0, -0.5);
+  const double2 t = tab[idx];
+  *sp = fma(t.x, cm, fma(t.y, sr, t.x));
+  *cp = fma(t.y, cm, fma(-t.x, sr, t.y));
+}
+
+// The table into shared memory (every thread of the CTA takes part).
+__device__ __forceinline__ void load_sincos_tab(double2 *sm) {
+  for (int k = threadIdx.x; k < kTabN; k += blockDim.x) sm[k] = g_sincos_tab[k];
+  __syncthreads();
+}
+
+// c 2^52 rounded to the nearest integer (halves up in magnitude), for |c| <= 1, from
+// the bits of c with integer instructions only; 0 for zero, subnormal or non-finite c.
+// The FP64 stages add their cosines and sines in this fixed point (exactly, on the
+// integer pipe) and move the per-thread sums into FP64 every kFlush angles.
+__device__ __forceinline__ long long fix52(double c) {
+  const long long b = __double_as_longlong(c);
+  const int e = (int)(b >> 52) & 0x7ff;
+  const int sh = 1023 - e;  // c 2^52 = significand >> sh
+  const long long m = (b & 0x000fffffffffffffLL) | 0x0010000000000000LL;
+  const long long v = (sh < 0 || sh > 53) ? 0LL : (m + ((1LL << sh) >> 1)) >> sh;
+  return b < 0 ? -v : v;
+}
 
 struct HmfArgs {
   double *q, *p;
@@ -50,7 +118,8 @@ struct HmfArgs {
 template <bool MIXED, int MODE>
 __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfArgs &a, float mxf,
                                              float myf, double mx, double my, float dtf, float &acf,
-                                             float &asf, double &acd, double &asd, int64_t i) {
+                                             float &asf, long long &aci, long long &asi, int64_t i,
+                                             const double2 *tab) {
   if (MIXED) {
     // Only the kick and the drift use the FP64 pipe (two DFMA per particle):
     // range reduction and float<->double conversions move bits on the integer
@@ -73,7 +142,8 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
     }
   } else {
     const double2 cs = a.cs[i];
-    double f = __dsub_rn(__dmul_rn(cs.x, my), __dmul_rn(cs.y, mx));
+    // two rounded products, so that the self-interaction of a lone particle cancels exactly
+    const double f = __dsub_rn(__dmul_rn(cs.x, my), __dmul_rn(cs.y, mx));
     if (MODE == STAGE_FORCE_ONLY) {
       a.fout[i] = f;
       return;
@@ -82,10 +152,10 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
     if (MODE == STAGE_KICK_DRIFT) {
       th = fma(a.drift, pp, th);
       double s, c;
-      sincos(th, &s, &c);
+      sincos_tab(th, tab, &s, &c);
       a.cs[i] = make_double2(c, s);
-      acd += c;
-      asd += s;
+      aci += fix52(c);
+      asi += fix52(s);
     }
   }
 }
@@ -131,8 +201,11 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
       sy += a.m_in[2 * r + 1];
     }
   const double mx = sx * a.invN, my = sy * a.invN;
+  extern __shared__ double2 tab[];  // FP64 kick-drift stages: the sine/cosine table (kTabBytes)
+  if constexpr (!MIXED && MODE == STAGE_KICK_DRIFT) load_sincos_tab(tab);
   const float mxf = (float)mx, myf = (float)my, dtf = (float)a.drift;
   float acf = 0.f, asf = 0.f;
+  long long aci = 0, asi = 0;
   double acd = 0.0, asd = 0.0;
   const int64_t npairs = a.N >> 1;
   const int64_t G = (int64_t)gridDim.x * NT;
@@ -160,8 +233,8 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
       const int64_t kk = k + u * G;
       const int64_t ix = a.rev ? npairs - 1 - kk : kk;
       if (kk < npairs) {
-        hmf_particle<MIXED, MODE>(qv[u].x, pv[u].x, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, 2 * ix);
-        hmf_particle<MIXED, MODE>(qv[u].y, pv[u].y, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, 2 * ix + 1);
+        hmf_particle<MIXED, MODE>(qv[u].x, pv[u].x, a, mxf, myf, mx, my, dtf, acf, asf, aci, asi, 2 * ix, tab);
+        hmf_particle<MIXED, MODE>(qv[u].y, pv[u].y, a, mxf, myf, mx, my, dtf, acf, asf, aci, asi, 2 * ix + 1, tab);
         if (MODE == STAGE_KICK_DRIFT) q2[ix] = qv[u];
         if (MODE != STAGE_FORCE_ONLY) p2[ix] = pv[u];
       }
@@ -172,11 +245,16 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
     asd += (double)asf;
     acf = asf = 0.f;
   }
+  if constexpr (!MIXED && MODE == STAGE_KICK_DRIFT) {
+    acd += (double)aci * 0x1p-52;
+    asd += (double)asi * 0x1p-52;
+    aci = asi = 0;
+  }
   }
   if ((a.N & 1) && t0 == 0) {
     int64_t i = a.N - 1;
     double th = a.q[i], pp = a.p[i];
-    hmf_particle<MIXED, MODE>(th, pp, a, mxf, myf, mx, my, dtf, acf, asf, acd, asd, i);
+    hmf_particle<MIXED, MODE>(th, pp, a, mxf, myf, mx, my, dtf, acf, asf, aci, asi, i, tab);
     if (MODE == STAGE_KICK_DRIFT) a.q[i] = th;
     if (MODE != STAGE_FORCE_ONLY) a.p[i] = pp;
   }
@@ -184,6 +262,9 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
     if (MIXED) {  // the odd last particle, if any
       acd += (double)acf;
       asd += (double)asf;
+    } else {
+      acd += (double)aci * 0x1p-52;
+      asd += (double)asi * 0x1p-52;
     }
     grid_finish(acd, asd, a.partials, a.m_out, a.ticket);
   }
@@ -191,10 +272,15 @@ __global__ void __launch_bounds__(NT) hmf_stage_kernel(HmfArgs a) {
 
 // (sum cos, sum sin) of the given angles.  MIXED: FP32 sine/cosine after FP64
 // range reduction, FP32 per-thread sums; otherwise FP64 throughout.
+// FP64: use_tab selects the table-driven sine and cosine of the FP64 stages (the table
+// in kTabBytes of dynamic shared memory) over sincos; cs_out (may be NULL) also gets
+// (cos, sin) of every angle.
 template <bool MIXED>
 __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__ q, int64_t N,
                                                       double *partials, double *m_out, unsigned *ticket,
-                                                      double2 *cs_out) {
+                                                      double2 *cs_out, int use_tab) {
+  extern __shared__ double2 tab[];
+  if (!MIXED && use_tab) load_sincos_tab(tab);  // use_tab is the same for the whole grid
   float acf = 0.f, asf = 0.f;
   double acd = 0.0, asd = 0.0;
   const int64_t G = (int64_t)gridDim.x * NT;
@@ -210,7 +296,10 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
       asf += s;
     } else {
       double s, c;
-      sincos(th, &s, &c);
+      if (use_tab)
+        sincos_tab(th, tab, &s, &c);
+      else
+        sincos(th, &s, &c);
       if (cs_out) cs_out[i] = make_double2(c, s);
       acd += c;
       asd += s;
@@ -227,9 +316,9 @@ __global__ void __launch_bounds__(NT) hmf_sums_kernel(const double *__restrict__
 
 // Grid of a streaming kernel: CTAs per SM = the occupancy limit, or `cap` when
 // given (0: none), or the tuning key when set.
-int grid_for(md_ctx *c, const void *kern, int64_t work_items, int cap = 0) {
+int grid_for(md_ctx *c, const void *kern, int64_t work_items, int cap = 0, size_t dyn_smem = 0) {
   int lim = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lim, kern, NT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lim, kern, NT, dyn_smem);
   int occ = (cap > 0 && cap < lim) ? cap : lim;
   if (c->ht.ctas_per_sm > 0) occ = c->ht.ctas_per_sm < lim ? c->ht.ctas_per_sm : lim;
   int64_t g = (int64_t)c->nsm * (occ > 0 ? occ : 1);
@@ -262,16 +351,42 @@ int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
   a.nsum = 1;
   c->hmf_rev ^= 1;
   auto kern = hmf_stage_kernel<MIXED, MODE>;
+  const size_t dyn = (!MIXED && MODE == STAGE_KICK_DRIFT) ? kTabBytes : 0;
   // Mixed stages: 4 CTAs of 256 threads per SM measured fastest on GB300 at N = 5e7
   // (0.252 ms per stage; 0.269 at 3, 0.307 at 2 and 0.271 at 5, the register limit).
-  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1, MIXED ? 4 : 0);
-  kern<<<g, NT, 0, c->stream>>>(a);
+  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1, MIXED ? 4 : 0, dyn);
+  kern<<<g, NT, dyn, c->stream>>>(a);
   MD_LAUNCHED(c);
   if (MODE == STAGE_KICK_DRIFT) c->hmf_cur = 1 - c->hmf_cur;
   return MD_OK;
 }
 
 }  // namespace
+
+// The sine/cosine table of this device, once per device (made on the host in long
+// double, rounded to double).
+int hmf_sincos_table(md_ctx *c) {
+  static std::mutex mu;
+  static bool done[kMaxDevicesTab] = {};
+  if (c->device < 0 || c->device >= kMaxDevicesTab) return set_err(c, MD_EINVAL, "device %d", c->device);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[c->device]) return MD_OK;
+  static double2 t[kTabN];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < kTabN; k++) {
+    const long double x = (long double)k * pi / (long double)(kTabN / 2);
+    t[k] = make_double2((double)sinl(x), (double)cosl(x));
+  }
+  MD_CUDA(c, cudaMemcpyToSymbol(g_sincos_tab, t, sizeof t));
+  // the kernels that hold the table in dynamic shared memory (64 KB, above the 48 KB default)
+  MD_CUDA(c, cudaFuncSetAttribute(hmf_stage_kernel<false, STAGE_KICK_DRIFT, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes));
+  MD_CUDA(c, cudaFuncSetAttribute(hmf_stage_kernel<false, STAGE_KICK_DRIFT, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes));
+  MD_CUDA(c, cudaFuncSetAttribute(hmf_sums_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes));
+  done[c->device] = true;
+  return MD_OK;
+}
 
 // FP64 (sum cos, sum sin) of q[0..N) into device out2, with caller-supplied
 // partials (>= grid_cap doubles x 2) and a zeroed ticket.
@@ -284,13 +399,15 @@ void hmf_sums_raw(cudaStream_t st, int nsm, int grid_cap, const double *q, int64
   if (g > need) g = need;
   if (g > grid_cap) g = grid_cap;
   if (g < 1) g = 1;
-  hmf_sums_kernel<false><<<(int)g, NT, 0, st>>>(q, N, partials, out2, ticket, nullptr);
+  hmf_sums_kernel<false><<<(int)g, NT, 0, st>>>(q, N, partials, out2, ticket, nullptr, 0);
 }
 
 int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2) {
+  int rc = hmf_sincos_table(c);  // HMF contexts have it already; Ring ones (md_magnetization) may not
+  if (rc) return rc;
   auto kern = hmf_sums_kernel<false>;
-  int g = grid_for(c, (const void *)kern, c->N);
-  kern<<<g, NT, 0, c->stream>>>(q, c->N, c->hmf_partials, d_out2, c->hmf_ticket, nullptr);
+  int g = grid_for(c, (const void *)kern, c->N, 0, kTabBytes);
+  kern<<<g, NT, kTabBytes, c->stream>>>(q, c->N, c->hmf_partials, d_out2, c->hmf_ticket, nullptr, 1);
   MD_LAUNCHED(c);
   return MD_OK;
 }
@@ -303,7 +420,7 @@ int hmf_prime(md_ctx *c) {
   if (c->prec == MD_MIXED) {
     auto kern = hmf_sums_kernel<true>;
     int g = grid_for(c, (const void *)kern, c->N);
-    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr, 0);
     MD_LAUNCHED(c);
   } else {
     // FP64: the sums and the (cos, sin) buffer the FP64 stages read
@@ -315,8 +432,8 @@ int hmf_prime(md_ctx *c) {
       if (!c->hmf_cs) return set_err(c, MD_ENOMEM, "HMF (cos, sin) buffer: %zu bytes", need);
     }
     auto kern = hmf_sums_kernel<false>;
-    int g = grid_for(c, (const void *)kern, c->N);
-    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs);
+    int g = grid_for(c, (const void *)kern, c->N, 0, kTabBytes);
+    kern<<<g, NT, kTabBytes, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs, 1);
     MD_LAUNCHED(c);
   }
   c->hmf_m_valid = true;
@@ -344,7 +461,7 @@ int hmf_shard_prime(md_ctx *c) {
   if (c->prec == MD_MIXED) {
     auto kern = hmf_sums_kernel<true>;
     int g = grid_for(c, (const void *)kern, c->N);
-    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr);
+    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, nullptr, 0);
   } else {
     const size_t need = sizeof(double2) * (size_t)c->N;
     if (need > c->hmf_cs_bytes) {
@@ -354,8 +471,8 @@ int hmf_shard_prime(md_ctx *c) {
       if (!c->hmf_cs) return set_err(c, MD_ENOMEM, "HMF (cos, sin) buffer: %zu bytes", need);
     }
     auto kern = hmf_sums_kernel<false>;
-    int g = grid_for(c, (const void *)kern, c->N);
-    kern<<<g, NT, 0, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs);
+    int g = grid_for(c, (const void *)kern, c->N, 0, kTabBytes);
+    kern<<<g, NT, kTabBytes, c->stream>>>(c->q, c->N, c->hmf_partials, out, c->hmf_ticket, (double2 *)c->hmf_cs, 1);
   }
   MD_LAUNCHED(c);
   c->hmf_m_valid = false;  // md_step's own sums are not kept on a shard
@@ -383,8 +500,9 @@ int launch_shard_stage(md_ctx *c, double kick, double drift, double *fout) {
   a.rev = c->hmf_rev;
   c->hmf_rev ^= 1;
   auto kern = hmf_stage_kernel<MIXED, MODE, true>;
-  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1, MIXED ? 4 : 0);
-  kern<<<g, NT, 0, c->stream>>>(a);
+  const size_t dyn = (!MIXED && MODE == STAGE_KICK_DRIFT) ? kTabBytes : 0;
+  int g = grid_for(c, (const void *)kern, (c->N + 1) / 2 / UNROLL + 1, MIXED ? 4 : 0, dyn);
+  kern<<<g, NT, dyn, c->stream>>>(a);
   MD_LAUNCHED(c);
   if (MODE == STAGE_KICK_DRIFT) c->shard_cur = 1 - c->shard_cur;
   return MD_OK;
