@@ -111,6 +111,9 @@ def parse():
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed regions of K steps each; value is the median (HMF and ensemble workloads)")
+    ap.add_argument("--shards", type=int, default=0,
+                    help="time the row-shard path instead: the system split among this many shard "
+                         "contexts on this GPU, md_shard_step with an exchange after every stage")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the short Ring, 2D and ensemble runs added to the default (HMF) line")
     a = ap.parse_args()
@@ -1031,8 +1034,58 @@ def run_adjoint(args, w):
     s.close()
 
 
+def run_shards(args, w):
+    """The row-shard path (md_shard_*) on one GPU: the workload's system split among
+    `--shards` contexts, K steps of md_shard_step (every stage of every rank, then the
+    exchange of every rank's segment), wall-clock timed between device synchronizes.
+    Reports the throughput and the exchanged bytes per step beside the whole-system
+    one-sided kernel timed the same way."""
+    import torch
+
+    from paper_1212_0262_gb300 import ShardGroup, System
+
+    model, N, K, W, P = w["model"], w["N"], args.steps, args.warmup, args.shards
+    units = N if model == 0 else 3.0 * N * N
+
+    def timed(step):
+        step(W)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(K)
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0)
+
+    sampler = ClockSampler(device_uuid(0))
+    with ShardGroup(model, N, w["eps"], w["dt"], w["seed"], P, precision=args.prec) as g:
+        ms = timed(g.step)
+        seg = [g.buffer(r)[2] for r in range(P)]
+    clocks = sampler.stop()
+    with System(model, N, w["eps"], w["dt"], w["seed"], precision=args.prec) as s:
+        if model != 0:
+            s.set_tuning("symmetric", 0)  # every ordered pair, as the shards
+        ms_whole = timed(s.step)
+    # every stage copies each rank's segment into the P - 1 other buffers
+    xbytes = 3 * (P - 1) * sum(seg)
+    print(json.dumps({
+        "metric": METRIC, "value": units * K / (ms * 1e-3), "unit": w["unit"], "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else "f64 state / f32 " + ("sin,cos" if model == 0 else "pair arithmetic"),
+        "data": "synthetic",
+        "config": {"workload": w["name"] + f", split by rows among {P} shard contexts on one GPU",
+                   "precision": args.prec, "shards": P, "parallelism": f"row shards x{P} (one GPU)"},
+        "whole_system": {"value": units * K / (ms_whole * 1e-3), "ms_per_step": ms_whole / K,
+                         "kernel": "one-sided (every ordered pair)" if model else "HMF fused stage"},
+        "exchange_bytes_per_step": xbytes, "segment_bytes": seg, "clocks": clocks,
+        "note": "wall clock around K steps of md_shard_step (and of md_step for the whole system) between "
+                "device synchronizes; on one GPU the shards share the SMs, so this measures the sharded "
+                "path's overhead, not multi-GPU scaling"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.shards and args.impl == "ours":
+        run_shards(args, dict(WORKLOADS[args.workload], **({"N": args.n} if args.n else {})))
+        return
     if args.workload == "ensemble" and args.impl == "ours":
         run_ensemble(args, WORKLOADS["ensemble"])
         return
