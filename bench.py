@@ -509,9 +509,10 @@ def pair_roofline(workload, model, N, kcode, prec, stage_ms, clocks, tuned):
             "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
 
 
-def secondary_pair(workload, K, W, local):
-    """A short run of one pair configuration in the default precision and kernels
-    (its own system, L2 flush, clock record and energy error), for the default line."""
+def secondary_pair(workload, K, W, local, prec="mixed"):
+    """A short run of one pair configuration in the default kernels of `prec` (its own
+    system, L2 flush, clock record and energy errors after the W warm-up steps and
+    after all W + K steps), for the default line."""
     import torch
 
     from paper_1212_0262_gb300 import System, binding
@@ -520,13 +521,14 @@ def secondary_pair(workload, K, W, local):
     model, N = w["model"], w["N"]
     stream = torch.cuda.Stream()
     lib = binding.load()
-    with System(model, N, w["eps"], w["dt"], w["seed"], precision="mixed") as s:
+    with System(model, N, w["eps"], w["dt"], w["seed"], precision=prec) as s:
         s.set_stream(stream)
         e0 = sum(s.energy())
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         if W:
             pair_timed_steps(lib, s._h, stream, flush, W)
         torch.cuda.synchronize()
+        e_w = sum(s.energy())
         sampler = ClockSampler(device_uuid(local))
         l0 = s.launch_count
         elapsed_ms, stage_ms = pair_timed_steps(lib, s._h, stream, flush, K)
@@ -537,9 +539,10 @@ def secondary_pair(workload, K, W, local):
         kcode = s.force_kernel
         del flush
     return {"workload": w["name"], "value": 3.0 * N * N * K / (elapsed_ms * 1e-3), "unit": w["unit"],
-            "steps": K, "warmup": W, "ms_per_step": elapsed_ms / K, "precision": "mixed",
+            "steps": K, "warmup": W, "ms_per_step": elapsed_ms / K, "precision": prec,
             "rel_energy_error": abs((e1 - e0) / e0), "energy_error_steps": W + K,
-            "roofline": pair_roofline(workload, model, N, kcode, "mixed", stage_ms, clocks, []),
+            "rel_energy_error_after_warmup": abs((e_w - e0) / e0),
+            "roofline": pair_roofline(workload, model, N, kcode, prec, stage_ms, clocks, []),
             "gpu_launches": launches, "clocks": clocks, "l2": "flushed (256 MB write) before every timed step"}
 
 
@@ -743,6 +746,13 @@ def run_ours(args, w):
         # 20 / 10 / 10 steps: the closing kick-only stage of each timed call (a force
         # pass not counted in the 3 N^2 per step) stays within 1.6-3% of the time
         secondary = {"ring": secondary_pair("ring", 20, 3, local), "grav2d": secondary_pair("grav2d", 10, 3, local)}
+        # the FP64 kernels on the same systems: 1 + 2 steps, so that both precisions state
+        # their energy error after the same 3 steps (the mixed runs' warm-up)
+        for wl in ("ring", "grav2d"):
+            f64 = secondary_pair(wl, 2, 1, local, prec="fp64")
+            secondary[wl]["fp64"] = f64
+            secondary[wl]["energy_error_3_steps"] = {"mixed": secondary[wl]["rel_energy_error_after_warmup"],
+                                                     "fp64": f64["rel_energy_error"]}
         ens, _, _, m = ensemble_measure("mixed", 10, 3, local, repeats=3)
         ens.close()
         m.pop("pairs_per_stage")
