@@ -199,7 +199,7 @@ md_ctx *create_context(int model, int64_t N, int64_t n_total, int64_t row0, doub
     md_free(c);
     return nullptr;
   }
-  if (model == MD_HMF && hmf_sincos_table(c) != MD_OK) {
+  if (model == MD_HMF && hmf_sincos_table(c, true) != MD_OK) {
     g_err = c->err;
     md_free(c);
     return nullptr;

@@ -363,15 +363,23 @@ int launch_stage(md_ctx *c, double kick, double drift, double *fout) {
 
 }  // namespace
 
-// The sine/cosine table of this device, once per device (made on the host in long
-// double, rounded to double).
-int hmf_sincos_table(md_ctx *c) {
+// The sine/cosine table of this device (made on the host in long double, rounded to
+// double) and the shared-memory attribute of the kernels that hold it: set up once per
+// device, and again if (probe) a read of one entry finds the device copy gone (a device
+// reset drops both).  Synchronous; not to be called inside a stream capture.
+int hmf_sincos_table(md_ctx *c, bool probe) {
   static std::mutex mu;
   static bool done[kMaxDevicesTab] = {};
+  static double2 t[kTabN];
   if (c->device < 0 || c->device >= kMaxDevicesTab) return set_err(c, MD_EINVAL, "device %d", c->device);
   std::lock_guard<std::mutex> lk(mu);
-  if (done[c->device]) return MD_OK;
-  static double2 t[kTabN];
+  if (done[c->device]) {
+    if (!probe) return MD_OK;
+    double2 e1;
+    MD_CUDA(c, cudaMemcpyFromSymbol(&e1, g_sincos_tab, sizeof e1, sizeof(double2)));
+    if (e1.x == t[1].x && e1.y == t[1].y) return MD_OK;
+    done[c->device] = false;
+  }
   const long double pi = 3.141592653589793238462643383279502884L;
   for (int k = 0; k < kTabN; k++) {
     const long double x = (long double)k * pi / (long double)(kTabN / 2);
@@ -403,7 +411,7 @@ void hmf_sums_raw(cudaStream_t st, int nsm, int grid_cap, const double *q, int64
 }
 
 int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2) {
-  int rc = hmf_sincos_table(c);  // HMF contexts have it already; Ring ones (md_magnetization) may not
+  int rc = hmf_sincos_table(c, false);  // HMF contexts have it already; Ring ones (md_magnetization) may not
   if (rc) return rc;
   auto kern = hmf_sums_kernel<false>;
   int g = grid_for(c, (const void *)kern, c->N, 0, kTabBytes);

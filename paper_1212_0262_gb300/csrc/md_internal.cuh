@@ -199,7 +199,7 @@ int hmf_magnetization_terminal(md_ctx *c, double cx, double cy, double *lq);
 
 // hmf.cu
 int hmf_prime(md_ctx *c);                                         // sums of the current angles
-int hmf_sincos_table(md_ctx *c);  // the FP64 stages' sine/cosine table on the context's device (once per device)
+int hmf_sincos_table(md_ctx *c, bool probe);  // the FP64 stages' sine/cosine table on the context's device
 int hmf_stage(md_ctx *c, int mode, double kick, double drift, double *fout);
 int hmf_sums_fp64(md_ctx *c, double *d_out2);                     // FP64 (sum cos, sum sin) into device out
 int hmf_sums_fp64_of(md_ctx *c, const double *q, double *d_out2);

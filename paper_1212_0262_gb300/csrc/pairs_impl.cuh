@@ -365,7 +365,7 @@ struct RingMixed {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
     const float4 *sm = (const float4 *)smb;
     const float2 he = f2((float)a.epsd);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 2; k++) {
       const float4 A = sm[2 * k], B = sm[2 * k + 1];
       const float2 nsj = make_float2(A.x, A.y), cj = make_float2(A.z, A.w);
@@ -440,7 +440,7 @@ struct GravMixed {
         st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
       }
     };
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 2; k++) body(k);
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -458,7 +458,7 @@ struct GravMixed {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll 1
+#pragma unroll 4
     for (int k8 = 0; k8 < TJ / 8; k8++) {
       float v[16];
 #pragma unroll
@@ -701,7 +701,7 @@ struct Grav3DMixed {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 2; k++) {
       const float4 A = sm[2 * k], B = sm[2 * k + 1];
       const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w), nz = make_float2(B.x, B.y);
@@ -726,7 +726,7 @@ struct Grav3DMixed {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll 1
+#pragma unroll 4
     for (int k8 = 0; k8 < TJ / 8; k8++) {
       float vxy[16], vz[8];
 #pragma unroll
@@ -1105,7 +1105,7 @@ struct RingMixedAdj {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t i0, int64_t j0) {
     const float4 *sm = (const float4 *)smb;
     const float2 he = f2((float)a.epsd), m34 = f2(-0.75f);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 2; k++) {
       const float4 A = sm[3 * k], B = sm[3 * k + 1], L = sm[3 * k + 2];
       const float2 nsj = make_float2(A.x, A.y), cj = make_float2(A.z, A.w);
@@ -1178,7 +1178,7 @@ struct GravMixedAdj {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd), m2 = f2(-2.f);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 2; k++) {
       const float4 X = sm[2 * k], V = sm[2 * k + 1];
       const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
@@ -1254,7 +1254,7 @@ struct Grav3DMixedAdj {
   __device__ static void tile(State &st, const unsigned char *smb, const PairArgs &a, int64_t, int64_t) {
     const float4 *sm = (const float4 *)smb;
     const float2 e2 = f2((float)a.epsd), m3 = f2(-3.f);
-#pragma unroll 1
+#pragma unroll 2
     for (int k = 0; k < TJ / 2; k++) {
       const float4 A = sm[3 * k], B = sm[3 * k + 1], C = sm[3 * k + 2];
       const float2 nx = make_float2(A.x, A.y), ny = make_float2(A.z, A.w), nz = make_float2(B.x, B.y);
@@ -1677,7 +1677,7 @@ struct RingTC {
     const float *sm = (const float *)smb;
     const float2 he = f2((float)a.epsd);
     const int lane = threadIdx.x & 31, t = lane & 3;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < TJ / 8; k++) {
       const float2 bs = *(const float2 *)(sm + k * 128 + lane * 2);
       const float2 bh = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
@@ -1722,7 +1722,7 @@ struct RingTC {
     const float *sm = (const float *)smb;
     const float2 he = f2((float)a.epsd);
     const int lane = threadIdx.x & 31, t = lane & 3, w = threadIdx.x >> 5;
-#pragma unroll 1
+#pragma unroll 2
     for (int k4 = 0; k4 < TJ / 32; k4++) {
       float v[8];
 #pragma unroll
