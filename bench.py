@@ -110,7 +110,7 @@ def parse():
                          "own parser takes --n for one of its options")
     ap.add_argument("--tune", action="append", default=[], help="md_set_tuning key=value (repeatable)")
     ap.add_argument("--repeats", type=int, default=5,
-                    help="timed regions of K steps each; value is the median (HMF and ensemble workloads)")
+                    help="timed regions of K steps each; value is the median")
     ap.add_argument("--shards", type=int, default=0,
                     help="time the row-shard path instead: the system split among this many shard "
                          "contexts on this GPU, md_shard_step with an exchange after every stage")
@@ -611,16 +611,24 @@ def run_ours(args, w):
             repeats_ms.append(float(t.item()))
         elapsed_ms = sorted(repeats_ms)[len(repeats_ms) // 2]
     else:
-        # compute-bound kernels on L2-sized inputs: flush L2 between timed steps
-        elapsed_ms, stage_ms = pair_timed_steps(lib, h, stream, flush, K)
+        # compute-bound kernels on L2-sized inputs: flush L2 between timed steps; `repeats`
+        # timed regions of K steps, the median one reported (with its per-stage times)
+        repeats_ms = []
+        runs = []
+        for _ in range(max(1, args.repeats)):
+            torch.cuda.synchronize()
+            if ws > 1:
+                torch.distributed.barrier()
+            el, st_ms = pair_timed_steps(lib, h, stream, flush, K)
+            t = torch.tensor([el], dtype=torch.float64, device=dev)
+            if ws > 1:
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            runs.append((float(t.item()), st_ms))
+            repeats_ms.append(float(t.item()))
+        elapsed_ms, stage_ms = sorted(runs, key=lambda x: x[0])[len(runs) // 2]
     torch.cuda.synchronize()
-    launches = (sysm.launch_count - launches0) // (len(repeats_ms) if repeats_ms else 1)
+    launches = (sysm.launch_count - launches0) // len(repeats_ms)
     clocks = sampler.stop()
-    if repeats_ms is None:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        if ws > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     torch.cuda.synchronize()
     t_en = time.perf_counter()
     e1 = sum(sysm.energy())

@@ -17,8 +17,10 @@
 // sym.cu): one pair launch per part, each over the whole GPU, walking the
 // triangular (system, i-tile, j-tile) units of its systems stream-K style and
 // writing row and column partials, then one finish launch with a CTA per
-// (system, tile, chunk of 16 column-partial rows) that sums them in a fixed
-// order and runs the epilogue.  (The one-sided form shares one launch between
+// (system, tile, chunk of column-partial rows: 64 for the Ring part's 256-output
+// tiles, 16 for the 2D part's 2048) that sums them in a fixed order and runs the
+// epilogue; the grid holds only the chunks each tile has (a tile t sums the rows
+// above it, ceil(t / chunk) chunks).  (The one-sided form shares one launch between
 // the parts, split by md_batch_set_tuning's `split`.)
 #include <algorithm>
 #include <vector>
@@ -38,7 +40,7 @@ struct SysDesc {
   int64_t ubeg;  // first unit of the system in its part
   int64_t rbeg;  // first row (i-tile) of the system in its part
   int64_t fbeg;  // symmetric form: first finish CTA of the system in its part
-  int nc;        // symmetric form: chunk slots per tile
+  int64_t nfin;  // symmetric form: finish CTAs of the system (chunks of all its tiles)
   double epsd, dt;
 };
 
@@ -227,8 +229,13 @@ __global__ void __launch_bounds__(NT) batch_kernel(PartArgs ring, PartArgs grav)
 
 // ------------------------------------------------- Newton's-third-law form --
 
-constexpr int kSymChunkB = 16;     // column-partial rows per finish CTA
 constexpr int kFinishThreadsB = 256;
+
+// Column-partial rows per finish CTA, by the tile's outputs (TI NACC): longer chunks
+// where a CTA has fewer outputs to sum, twice the single-system finish's, as the
+// ensemble's tiles have few rows above them (small systems) and the finish phase is
+// bound by its CTA count rather than by its loads.
+__host__ __device__ constexpr int chunk_rows(int64_t outputs) { return outputs <= 256 ? 128 : outputs <= 512 ? 64 : 32; }
 
 // (system, local row) of part-local unit u in the triangular layout
 __device__ __forceinline__ void sym_locate(const PartArgs &A, int64_t u, int &s, int64_t &it, int64_t &jt) {
@@ -344,15 +351,16 @@ __device__ __noinline__ void batch_sym_finish(const PartArgs &A, int64_t f) {
   constexpr int64_t TI = (int64_t)NT * Pol::R;
   constexpr int OUT = (int)TI * NACC;
   __shared__ bool s_last;
+  constexpr int CH = chunk_rows(OUT);
   const int s = sys_of_fin(A, f);
   const SysDesc &S = A.sys[s];
-  const int64_t lf = f - S.fbeg, T = lf / S.nc;
-  const int c = (int)(lf % S.nc);
-  const int nch = T == 0 ? 1 : (int)((T + kSymChunkB - 1) / kSymChunkB);
-  if (c >= nch) return;
+  const int64_t lf = f - S.fbeg;
+  const int64_t T = fin_tile(lf, S.n_it, CH), tbeg = fin_prefix(T, CH);
+  const int c = (int)(lf - tbeg);
+  const int nch = T == 0 ? 1 : (int)((T + CH - 1) / CH);
   const int m = A.m;
-  const int64_t I_lo = (int64_t)c * kSymChunkB, I_hi = min(T, I_lo + kSymChunkB);
-  double *chunk = A.chunks + (S.fbeg + T * S.nc) * OUT;
+  const int64_t I_lo = (int64_t)c * CH, I_hi = min(T, I_lo + CH);
+  double *chunk = A.chunks + (S.fbeg + tbeg) * OUT;
   for (int o = threadIdx.x; o < OUT; o += kFinishThreadsB) {
     const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);
     CompSum cs{0.f, 0.f};
@@ -457,7 +465,7 @@ struct md_batch {
   int graph_key[2] = {-1, -1};
   int64_t graph_launches[2] = {0, 0};
   // unit / row layout uploaded for tile shapes and form (layout_key)
-  int64_t layout_key[5] = {-1, -1, -1, -1, -1};
+  int64_t layout_key[7] = {-1, -1, -1, -1, -1, -1, -1};
   int64_t Ur = 0, Ug = 0, rows_r = 0, rows_g = 0, nfin_r = 0, nfin_g = 0;
   int64_t rec_bytes_r = 0, rec_bytes_g = 0;  // forward-record bytes of each part's systems
   int nr = 0;
@@ -500,7 +508,8 @@ void drop_graphs(md_batch *b) {
 // Descriptors and the unit / row layout of both parts: tile sizes (TI, TJ) per
 // part, and the one-sided (rectangular unit table) or symmetric (triangular,
 // n_jt = m n_it) form.
-int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym, std::vector<SysDesc> &hs) {
+int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], const int nacc[2], bool sym,
+                 std::vector<SysDesc> &hs) {
   hs.clear();
   b->Ur = b->Ug = b->rows_r = b->rows_g = b->nfin_r = b->nfin_g = 0;
   b->rec_bytes_r = b->rec_bytes_g = 0;
@@ -522,7 +531,7 @@ int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym
       d.n_jt = sym ? m * d.n_it : (c->N + tj - 1) / tj;
       d.epsd = want == MD_RING ? 0.5 * c->eps : c->eps;
       d.dt = c->dt;
-      d.nc = (int)std::max<int64_t>(1, (d.n_it - 1 + kSymChunkB - 1) / kSymChunkB);
+      d.nfin = fin_prefix(d.n_it, chunk_rows(ti * nacc[pass]));
       int64_t &U = pass == 0 ? b->Ur : b->Ug;
       int64_t &rows = pass == 0 ? b->rows_r : b->rows_g;
       int64_t &nfin = pass == 0 ? b->nfin_r : b->nfin_g;
@@ -531,7 +540,7 @@ int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym
       d.fbeg = nfin;
       U += sym ? sym_rowstart(d.n_it, d.n_jt, (int)m) : d.n_it * d.n_jt;
       rows += d.n_it;
-      nfin += d.n_it * d.nc;
+      nfin += d.nfin;
       // forward records: Ring tensor-core fragments (symmetric form) or interleaved FP32
       (pass == 0 ? b->rec_bytes_r : b->rec_bytes_g) += c->N * (pass == 0 ? (sym ? 64 : 16) : 8);
       hs.push_back(d);
@@ -544,11 +553,11 @@ int build_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym
 // Upload the layout for (TI, TJ, form) unless it is the current one.  Never runs
 // inside a stream capture: the first step of md_batch_step and every autotune
 // trial run uncaptured first.
-int ensure_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sym) {
-  const int64_t key[5] = {TI[0], TJ[0], TI[1], TJ[1], sym ? 1 : 0};
-  if (std::equal(key, key + 5, b->layout_key)) return MD_OK;
+int ensure_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], const int nacc[2], bool sym) {
+  const int64_t key[7] = {TI[0], TJ[0], TI[1], TJ[1], sym ? 1 : 0, nacc[0], nacc[1]};
+  if (std::equal(key, key + 7, b->layout_key)) return MD_OK;
   std::vector<SysDesc> hs;
-  build_layout(b, TI, TJ, sym, hs);
+  build_layout(b, TI, TJ, nacc, sym, hs);
   if (hs.size() > b->d_sys_count) {
     dev_free(b->d_sys);
     b->d_sys = (SysDesc *)dev_alloc(hs.size() * sizeof(SysDesc));
@@ -557,7 +566,7 @@ int ensure_layout(md_batch *b, const int64_t TI[2], const int64_t TJ[2], bool sy
   }
   B_CUDA(b, cudaStreamSynchronize(b->stream));  // no launch may still read the old layout
   B_CUDA(b, cudaMemcpy(b->d_sys, hs.data(), hs.size() * sizeof(SysDesc), cudaMemcpyHostToDevice));
-  std::copy(key, key + 5, b->layout_key);
+  std::copy(key, key + 7, b->layout_key);
   return MD_OK;
 }
 
@@ -619,7 +628,8 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   constexpr int64_t TIr = (int64_t)NT * PolR::R, TIg = (int64_t)NT * PolG::R;
   constexpr int NAr = PolR::NACC, NAg = PolG::NACC;
   const int64_t TI[2] = {TIr, TIg}, TJ[2] = {PolR::TJ, PolG::TJ};
-  int rc = ensure_layout(b, TI, TJ, true);
+  const int nacc[2] = {NAr, NAg};
+  int rc = ensure_layout(b, TI, TJ, nacc, true);
   if (rc) return rc;
   // full GPU for each part in turn: CTA counts from each kernel's own occupancy
   auto kern_r = batch_sym_pairs_kernel<PolR>;
@@ -695,7 +705,8 @@ int launch_batch(md_batch *b, double bc, double dc) {
   constexpr int64_t TI = (int64_t)NT * PolR::R;
   static_assert(PolR::R == PolG::R && PolR::TJ == PolG::TJ, "parts share the tile shape");
   const int64_t TIs[2] = {TI, TI}, TJs[2] = {PolR::TJ, PolG::TJ};
-  int rc = ensure_layout(b, TIs, TJs, false);
+  const int naccs[2] = {PolR::NACC, PolG::NACC};
+  int rc = ensure_layout(b, TIs, TJs, naccs, false);
   if (rc) return rc;
   auto kern = batch_kernel<PolR, PolG, MIXED, MODE>;
   const int occ = occupancy(b, (const void *)kern);
