@@ -16,12 +16,13 @@
 // (every unordered pair of a system once, as the single-system stages in
 // sym.cu): one pair launch per part, each over the whole GPU, walking the
 // triangular (system, i-tile, j-tile) units of its systems stream-K style and
-// writing row and column partials, then one finish launch with a CTA per
-// (system, tile, chunk of column-partial rows: 64 for the Ring part's 256-output
-// tiles, 16 for the 2D part's 2048) that sums them in a fixed order and runs the
-// epilogue; the grid holds only the chunks each tile has (a tile t sums the rows
-// above it, ceil(t / chunk) chunks).  (The one-sided form shares one launch between
-// the parts, split by md_batch_set_tuning's `split`.)
+// writing row and column partials (diagonal units too: their above-diagonal
+// blocks are evaluated once, with column sums), then one finish launch with a CTA
+// per (system, tile, chunk of column-partial rows: 128 for the Ring part's
+// 256-output tiles, 32 for the 2D part's 2048) that sums them in a fixed order and
+// runs the epilogue; the grid holds only the chunks each tile has (tile t sums the
+// rows 0 .. t, ceil((t + 1) / chunk) chunks).  (The one-sided form shares one launch
+// between the parts, split by md_batch_set_tuning's `split`.)
 #include <algorithm>
 #include <vector>
 
@@ -237,6 +238,27 @@ constexpr int kFinishThreadsB = 256;
 // bound by its CTA count rather than by its loads.
 __host__ __device__ constexpr int chunk_rows(int64_t outputs) { return outputs <= 256 ? 128 : outputs <= 512 ? 64 : 32; }
 
+// Finish CTAs: tile t sums the column partials of its units (I, t m .. t m + m - 1)
+// for I = 0 .. t (its own diagonal units included: their above-diagonal blocks) in
+// ceil((t + 1) / ch) chunks of ch rows I.  CTAs of tiles 0 .. T-1:
+// sum_{s=1}^{T} ceil(s / ch) = ch q (q + 1) / 2 + r (q + 1) with T = q ch + r.
+__host__ __device__ __forceinline__ int64_t fin_prefix(int64_t T, int ch) {
+  const int64_t q = T / ch, r = T % ch;
+  return (int64_t)ch * q * (q + 1) / 2 + r * (q + 1);
+}
+
+// The tile whose chunks hold finish CTA f of a system of n_it tiles: the largest T
+// with fin_prefix(T) <= f.
+__device__ __forceinline__ int64_t fin_tile(int64_t f, int64_t n_it, int ch) {
+  int64_t lo = 0, hi = n_it - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (fin_prefix(mid, ch) <= f) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // (system, local row) of part-local unit u in the triangular layout
 __device__ __forceinline__ void sym_locate(const PartArgs &A, int64_t u, int &s, int64_t &it, int64_t &jt) {
   s = sys_of_unit(A, u);
@@ -248,8 +270,10 @@ __device__ __forceinline__ void sym_locate(const PartArgs &A, int64_t u, int &s,
 
 // Pair phase of one part: the part's CTAs walk its triangular units (systems
 // one after the other), write the row partials of the rows they cover and the
-// column partial of every off-diagonal unit.  smem: the j-tile double buffer,
-// then the per-warp column sums.
+// column partial of every unit (a diagonal unit's: the sums of its above-diagonal
+// blocks, Pol::tile_diag, which evaluates each unordered pair of the tile's own
+// particles once, off the 16 x 16 (Ring) or 256 x 256 (2D) squares on the
+// diagonal).  smem: the j-tile double buffer, then the per-warp column sums.
 template <class Pol>
 __device__ __forceinline__ void batch_sym_pairs(const PartArgs &A, int64_t cta, unsigned char *smem) {
   constexpr int TJ = Pol::TJ, NACC = Pol::NACC, NW = NT / 32;
@@ -291,10 +315,10 @@ __device__ __forceinline__ void batch_sym_pairs(const PartArgs &A, int64_t cta, 
     }
     __syncthreads();
     const bool diag = jt < (int64_t)m * (it + 1);
-    if (diag) Pol::template tile<true>(st, buf, v, i0, jt * TJ);
+    if (diag) Pol::tile_diag(st, buf, v, colsm, (int)(jt - (int64_t)m * it));
     else Pol::tile_sym(st, buf, v, colsm);
     __syncthreads();
-    if (!diag) {
+    {
       float *dst = A.colslot + u * (int64_t)(TJ * NACC);
       for (int idx = threadIdx.x; idx < TJ * NACC; idx += NT) {
         float x = colsm[idx];
@@ -357,9 +381,9 @@ __device__ __noinline__ void batch_sym_finish(const PartArgs &A, int64_t f) {
   const int64_t lf = f - S.fbeg;
   const int64_t T = fin_tile(lf, S.n_it, CH), tbeg = fin_prefix(T, CH);
   const int c = (int)(lf - tbeg);
-  const int nch = T == 0 ? 1 : (int)((T + CH - 1) / CH);
+  const int nch = (int)(T / CH + 1);
   const int m = A.m;
-  const int64_t I_lo = (int64_t)c * CH, I_hi = min(T, I_lo + CH);
+  const int64_t I_lo = (int64_t)c * CH, I_hi = min(T + 1, I_lo + CH);
   double *chunk = A.chunks + (S.fbeg + tbeg) * OUT;
   for (int o = threadIdx.x; o < OUT; o += kFinishThreadsB) {
     const int jsub = o / (TJ * NACC), rest = o % (TJ * NACC);

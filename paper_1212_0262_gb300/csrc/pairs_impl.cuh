@@ -189,27 +189,14 @@ __host__ __device__ __forceinline__ int64_t sym_rowstart(int64_t I, int64_t n_jt
   return I * n_jt - (int64_t)m * I * (I - 1) / 2;
 }
 
-// Finish phase of the Newton's-third-law form: tile t sums the column partials of
-// the rows I < t in max(1, ceil(t / ch)) chunks of ch rows, one CTA per chunk.  CTAs of
-// tiles 0 .. T-1: 1 + sum_{t=1}^{T-1} ceil(t / ch) = 1 + ch q (q + 1) / 2 + r (q + 1)
-// with T - 1 = q ch + r (0 for T = 0).
-__host__ __device__ __forceinline__ int64_t fin_prefix(int64_t T, int ch) {
-  if (T <= 0) return 0;
-  const int64_t q = (T - 1) / ch, r = (T - 1) % ch;
-  return 1 + (int64_t)ch * q * (q + 1) / 2 + r * (q + 1);
-}
-
-// The tile whose chunks hold finish CTA f of a layout of n_it tiles: the largest T with
-// fin_prefix(T) <= f.
-__device__ __forceinline__ int64_t fin_tile(int64_t f, int64_t n_it, int ch) {
-  int64_t lo = 0, hi = n_it - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (fin_prefix(mid, ch) <= f) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
+// Policies with a Newton's-third-law diagonal tile (tile_diag: the above-diagonal
+// pairs of an i-tile with its own particles evaluated once, with column sums).  Their
+// diagonal units write column partials too, and the finish phase of tile T adds the
+// column partials of the rows I <= T (else I < T).
+template <class P, class = void>
+struct HasDiagSym : std::false_type {};
+template <class P>
+struct HasDiagSym<P, std::void_t<decltype(&P::tile_diag)>> : std::true_type {};
 
 // The row holding unit u: the largest I < n_it with rowstart(I) <= u.
 __device__ int64_t sym_row_of_unit(int64_t u, int64_t n_it, int64_t n_jt, int m) {
@@ -517,6 +504,89 @@ struct GravMixed {
       csum_add2(st.cs[r][0], st.fx[r]);
       csum_add2(st.cs[r][1], st.fy[r]);
       st.fx[r] = st.fy[r] = f2(0.f);
+    }
+  }
+  // Diagonal tile kd (columns kd TJ .. kd TJ + TJ - 1 of the tile's own particles)
+  // of the Newton's-third-law variant.  Row group r holds rows r NT + tid, so the
+  // G = TJ / NT groups from G kd on are the columns' own particles: groups below
+  // lie above the diagonal and are evaluated as in tile_sym (row and column sums),
+  // the G own groups one-sided as in tile<> (each ordered pair on its row; the self
+  // term is exactly zero), and groups above are skipped (their pairs with these
+  // columns are above-diagonal pairs of the tile kd' = r / G).  colsm gets every
+  // column (zero for kd = 0, where no group lies above).
+  template <int KD>
+  __device__ static void tile_diag_k(State &st, const unsigned char *smb, const PairArgs &a, float *colsm) {
+    constexpr int G = TJ / NT, RS = G * KD, RE = RS + G;
+    static_assert(TJ % NT == 0 && RE <= R, "diagonal tile layout");
+    const float4 *sm = (const float4 *)smb;
+    const float2 e2 = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if constexpr (RS == 0) {
+      for (int idx = lane; idx < 2 * TJ; idx += 32) colsm[w * TJ * 2 + idx] = 0.f;
+#pragma unroll 1
+      for (int k = 0; k < TJ / 2; k++) {
+        const float4 X = sm[k];
+        const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
+#pragma unroll
+        for (int r = RS; r < RE; r++) {
+          float2 dx = __fadd2_rn(st.x[r], nx);
+          float2 dy = __fadd2_rn(st.y[r], ny);
+          float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+          float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+          st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
+          st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int k8 = 0; k8 < TJ / 8; k8++) {
+        float v[16];
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+          const float4 X = sm[4 * k8 + kk];
+          const float2 nx = make_float2(X.x, X.y), ny = make_float2(X.z, X.w);
+          float2 cx = f2(0.f), cy = f2(0.f);
+#pragma unroll
+          for (int r = 0; r < RE; r++) {
+            float2 dx = __fadd2_rn(st.x[r], nx);
+            float2 dy = __fadd2_rn(st.y[r], ny);
+            float2 s = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, e2));
+            float2 inv = make_float2(mufu_rcp(s.x), mufu_rcp(s.y));
+            st.fx[r] = __ffma2_rn(dx, inv, st.fx[r]);
+            st.fy[r] = __ffma2_rn(dy, inv, st.fy[r]);
+            if (r < RS) {
+              cx = __ffma2_rn(dx, inv, cx);
+              cy = __ffma2_rn(dy, inv, cy);
+            }
+          }
+          v[4 * kk + 0] = cx.x;
+          v[4 * kk + 1] = cx.y;
+          v[4 * kk + 2] = cy.x;
+          v[4 * kk + 3] = cy.y;
+        }
+        float sum = butterfly_sum<16, 16>(v, lane);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if ((lane & 1) == 0) {
+          const int vi = lane >> 1;
+          const int j = 8 * k8 + 2 * (vi >> 2) + (vi & 1);
+          colsm[(w * TJ + j) * 2 + ((vi >> 1) & 1)] = sum;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RE; r++) {
+      csum_add2(st.cs[r][0], st.fx[r]);
+      csum_add2(st.cs[r][1], st.fy[r]);
+      st.fx[r] = st.fy[r] = f2(0.f);
+    }
+  }
+  __device__ static void tile_diag(State &st, const unsigned char *smb, const PairArgs &a, float *colsm, int kd) {
+    static_assert(NT * R == 4 * TJ, "four column blocks per diagonal tile");
+    switch (kd) {
+      case 0: tile_diag_k<0>(st, smb, a, colsm); break;
+      case 1: tile_diag_k<1>(st, smb, a, colsm); break;
+      case 2: tile_diag_k<2>(st, smb, a, colsm); break;
+      default: tile_diag_k<3>(st, smb, a, colsm); break;
     }
   }
 };
@@ -1653,9 +1723,18 @@ struct RingTC {
   static constexpr int NR = 2 * RM;           // rows g and g+8 of each m-block
   static constexpr int FMT = 1;               // tensor-core fragment records
   static_assert(THREADS * R == 16 * RM * (THREADS / 32), "tile rows: warps x RM m-blocks x 16");
+  static_assert(RM % 2 == 0, "m-blocks are dealt to the warps in pairs");
+  static constexpr int NW = THREADS / 32;
+  // m-block (16 rows) of the tile held as this warp's r-th: the pair p = r / 2 of
+  // blocks {2 NW p + w, 2 NW p + 2 NW - 1 - w}, so that every warp's blocks add up to
+  // the same number of above-diagonal pairs in a diagonal tile (tile_diag)
+  __device__ static int mblock(int r) {
+    const int w = threadIdx.x >> 5, p = r >> 1;
+    return (r & 1) ? 2 * NW * p + 2 * NW - 1 - w : 2 * NW * p + w;
+  }
   __device__ static int mrow(int rr) {        // row offset in the tile of item rr = 2 r + h
-    const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
-    return w * 16 * RM + 16 * (rr >> 1) + g + 8 * (rr & 1);
+    const int g = (threadIdx.x & 31) >> 2;
+    return 16 * mblock(rr >> 1) + g + 8 * (rr & 1);
   }
   __device__ static int row_of(int rr) { return (threadIdx.x & 3) == 0 ? mrow(rr) : -1; }
   struct State {
@@ -1779,6 +1858,98 @@ struct RingTC {
         v[2 * kk + 1] = col.y;
       }
       // lane (g, t) ends with n-block 4 k4 + (g >> 1), column 2t + (g & 1)
+      const float sum = butterfly_sum<8, 16>(v, lane);
+      colsm[w * TJ + 8 * (4 * k4 + (lane >> 3)) + 2 * t + ((lane >> 2) & 1)] = sum;
+    }
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        csum_add2(st.cs[r][h], st.acc[r][h]);
+        st.acc[r][h] = f2(0.f);
+      }
+  }
+  // Diagonal tile of the Newton's-third-law variant (TI = TJ: the columns are the
+  // tile's own particles).  m-block b (rows 16b .. 16b+15) against n-block k (columns
+  // 8k .. 8k+7): k >= 2b + 2 lies above the diagonal and is evaluated as in tile_sym
+  // (row and column sums); k = 2b, 2b+1 is the block's own 16 x 16 square, evaluated
+  // one-sided as in tile<true> (each ordered pair on its row, the self term masked);
+  // k < 2b mirrors an above-diagonal block of another m-block and is skipped.  Every
+  // warp's m-blocks (mblock) have the same number of n-blocks to do; colsm gets
+  // every column (zero where none of the warp's m-blocks lies above it).
+  __device__ static void tile_diag(State &st, const unsigned char *smb, const PairArgs &a, float *colsm, int) {
+    static_assert(16 * RM * NW == TJ, "diagonal tiles are square");
+    const float *sm = (const float *)smb;
+    const float2 he = f2((float)a.epsd);
+    const int lane = threadIdx.x & 31, t = lane & 3, w = threadIdx.x >> 5;
+    // one pair term: row sum, and the column sum when the pair lies above the diagonal
+    auto term = [&](int r, const float (&dS)[4], const float (&dH)[4], float2 &col, bool above, int k) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const float2 S = make_float2(dS[2 * h], dS[2 * h + 1]);
+        const float2 sh = make_float2(dH[2 * h], dH[2 * h + 1]);
+        const float2 d = __ffma2_rn(sh, sh, he);
+        const float2 y = make_float2(mufu_rsqrt(d.x), mufu_rsqrt(d.y));
+        float2 qq = __fmul2_rn(S, y);
+        if (!above) {
+          const int i = mrow(2 * r + h), j = 8 * k + 2 * t;
+          if (i == j) qq.x = 0.f;
+          if (i == j + 1) qq.y = 0.f;
+        }
+        const float2 y2 = __fmul2_rn(y, y);
+        st.acc[r][h] = __ffma2_rn(qq, y2, st.acc[r][h]);
+        if (above) col = __ffma2_rn(qq, y2, col);
+      }
+    };
+#pragma unroll 1
+    for (int k4 = 0; k4 < TJ / 32; k4++) {
+      unsigned b[4][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const int k = 4 * k4 + kk;
+        const float2 bs = *(const float2 *)(sm + k * 128 + lane * 2);
+        const float2 bh = *(const float2 *)(sm + k * 128 + 64 + lane * 2);
+        b[kk][0] = __float_as_uint(bs.x);
+        b[kk][1] = __float_as_uint(bs.y);
+        b[kk][2] = __float_as_uint(bh.x);
+        b[kk][3] = __float_as_uint(bh.y);
+      }
+      float2 col[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) col[kk] = f2(0.f);
+#pragma unroll
+      for (int r = 0; r < RM; r++) {
+        // the m-block's own n-blocks kb, kb + 1 (kb even: both in one group of 4)
+        const int kb = 2 * mblock(r);
+        if (4 * k4 >= kb + 2) {
+          // the whole group lies above the m-block: as tile_sym
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++) {
+            float dS[4], dH[4];
+            mma_tf32(dS, st.aS[r], b[kk][0], b[kk][1]);
+            mma_tf32(dH, st.aH[r], b[kk][2], b[kk][3]);
+            term(r, dS, dH, col[kk], true, 4 * k4 + kk);
+          }
+        } else if (4 * k4 + 4 > kb) {
+          // the group holds the m-block's own square (and, before it, skipped
+          // n-blocks or, after it, n-blocks above)
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++) {
+            const int k = 4 * k4 + kk;
+            if (k < kb) continue;
+            float dS[4], dH[4];
+            mma_tf32(dS, st.aS[r], b[kk][0], b[kk][1]);
+            mma_tf32(dH, st.aH[r], b[kk][2], b[kk][3]);
+            term(r, dS, dH, col[kk], k >= kb + 2, k);
+          }
+        }
+      }
+      float v[8];
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        v[2 * kk] = col[kk].x;
+        v[2 * kk + 1] = col[kk].y;
+      }
       const float sum = butterfly_sum<8, 16>(v, lane);
       colsm[w * TJ + 8 * (4 * k4 + (lane >> 3)) + 2 * t + ((lane >> 2) & 1)] = sum;
     }

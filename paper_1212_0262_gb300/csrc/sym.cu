@@ -12,10 +12,13 @@
 // Units.  i-tiles of TI = m TJ particles (m = TI/TJ), j-tiles of TJ.  Row I of
 // the unit table holds the j-tiles J = m I .. n_jt - 1 (n_jt = m n_it), so
 // rowstart(I) = I n_jt - m I (I - 1) / 2 and U = rowstart(n_it).  A unit whose
-// j-tile lies inside its i-tile (J < m (I + 1), "diagonal") evaluates its
-// TI x TJ block in full for the i-rows only, self pairs masked; every other unit
-// evaluates its block once: the i-rows accumulate in registers across the CTA's
-// consecutive units of the row (as in the one-sided kernel), and the sums over
+// j-tile lies inside its i-tile (J < m (I + 1), "diagonal") holds pairs of the
+// tile's own particles: the FP32 Ring and 2D policies (tile_diag) evaluate the
+// pairs above the diagonal once, as below, and only the squares on the diagonal
+// (16 x 16 for Ring, 256 x 256 for 2D) for the i-rows alone; the other policies
+// evaluate the whole TI x TJ block for the i-rows only, self pairs masked.  Every
+// other unit evaluates its block once: the i-rows accumulate in registers across
+// the CTA's consecutive units of the row (as in the one-sided kernel), and the sums over
 // the block's i-rows for each of its TJ j's (warp butterflies, then the warps in
 // a fixed order through shared memory) are stored as that unit's column partial
 // (FP32, [U][TJ][NACC]).
@@ -23,10 +26,12 @@
 // Pair phase (sym_pairs_kernel, stream-K).  CTA c takes units
 // [U c / P, U (c+1) / P) in row-major order and writes the row partials of the
 // rows it covers (rowfull[T] when it covered all of row T, else the one-sided
-// kernel's two slots per CTA) and the column partial of each off-diagonal unit.
+// kernel's two slots per CTA) and the column partial of each off-diagonal unit
+// (and of each diagonal one, with tile_diag).
 //
-// Finish phase (sym_finish_kernel).  Tile T needs its row partials and the m T
-// column partials of the units (I', J), I' < T, J in tile T.  One CTA per
+// Finish phase (sym_finish_kernel).  Tile T needs its row partials and the
+// column partials of the units (I', J), J in tile T, I' < T (I' <= T with
+// tile_diag).  One CTA per
 // (tile, chunk of sym_chunk rows I') sums a chunk's column partials per particle
 // and component (compensated FP32, then one double); the last chunk of a tile to
 // arrive (atomic ticket, no waiting) adds the row partials in CTA order and the
@@ -49,7 +54,7 @@ struct SymArgs {
   int m;             // TI / TJ
   int nc;            // chunk slots per tile in the finish phase
   double *rowfull;   // [n_it][NACC][TI] row partials of rows covered by one CTA
-  void *colslot;     // [U][TJ][NACC] column partials of the off-diagonal units (Pol::ColT:
+  void *colslot;     // [U][TJ][NACC] column partials of the units (Pol::ColT:
                      // FP32 for the mixed policies, FP64 for the FP64 ones)
   double *chunks;    // [n_it][nc][TI][NACC] chunk sums of the column partials
 };
@@ -72,6 +77,7 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
   static_assert(TILE_BYTES % 16 == 0, "tile must be a whole number of 16-byte chunks");
   static_assert(TI % TJ == 0, "i-tiles must be whole numbers of j-tiles");
   using ColT = typename Pol::ColT;
+  constexpr bool DIAG_SYM = HasDiagSym<Pol>::value;
   __shared__ __align__(16) unsigned char sbuf[2][TILE_BYTES];
   __shared__ __align__(16) unsigned char colraw[NW * TJ * NACC * sizeof(ColT)];
   ColT *colsm = (ColT *)colraw;
@@ -108,10 +114,11 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
     }
     __syncthreads();
     const bool diag = jt < (int64_t)m * (it + 1);
-    if (diag) Pol::template tile<true>(st, sbuf[buf], a, i0, jt * TJ);
-    else Pol::tile_sym(st, sbuf[buf], a, colsm);
+    if (!diag) Pol::tile_sym(st, sbuf[buf], a, colsm);
+    else if constexpr (DIAG_SYM) Pol::tile_diag(st, sbuf[buf], a, colsm, (int)(jt - (int64_t)m * it));
+    else Pol::template tile<true>(st, sbuf[buf], a, i0, jt * TJ);
     __syncthreads();
-    if (!diag) {
+    if (!diag || DIAG_SYM) {
       // column partial of this unit: the warps' sums in a fixed order (colsm is
       // rewritten only after the next unit's first barrier)
       ColT *dst = (ColT *)s.colslot + u * (int64_t)(TJ * NACC);
@@ -147,11 +154,11 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
   }
 }
 
-// Finish phase, one CTA per (tile T, chunk c of sym_chunk rows I' < T): the
-// chunk's column partials summed per particle and component (compensated FP32)
-// into one double; the last chunk of the tile to arrive (atomic ticket, no
-// waiting) adds the row partials (CTA order) and the chunk sums (chunk order)
-// and runs the stage epilogue.  Tiles with T = 0 have one empty chunk.
+// Finish phase, one CTA per (tile T, chunk c of sym_chunk rows I' < T, or I' <= T
+// with tile_diag): the chunk's column partials summed per particle and component
+// (compensated FP32) into one double; the last chunk of the tile to arrive (atomic
+// ticket, no waiting) adds the row partials (CTA order) and the chunk sums (chunk
+// order) and runs the stage epilogue.  A tile with no rows I' has one empty chunk.
 constexpr int kFinishThreads = 256;
 
 // Column-partial rows per finish CTA: about 16K loads per CTA whatever the tile's
@@ -171,10 +178,11 @@ __global__ void __launch_bounds__(kFinishThreads) sym_finish_kernel(PairArgs a, 
   const int64_t T = blockIdx.x / s.nc;
   const int c = (int)(blockIdx.x % s.nc);
   constexpr int CH = sym_chunk<Pol>();
-  const int nch = T == 0 ? 1 : (int)((T + CH - 1) / CH);
+  const int64_t rows = T + (HasDiagSym<Pol>::value ? 1 : 0);  // column-partial rows I of tile T
+  const int nch = rows == 0 ? 1 : (int)((rows + CH - 1) / CH);
   if (c >= nch) return;
   const int m = s.m;
-  const int64_t I_lo = (int64_t)c * CH, I_hi = min(T, I_lo + CH);
+  const int64_t I_lo = (int64_t)c * CH, I_hi = min(rows, I_lo + CH);
   double *chunk = s.chunks + (T * s.nc) * OUT;
   using ColT = typename Pol::ColT;
   const ColT *col = (const ColT *)s.colslot;
@@ -259,7 +267,8 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.P = (int)P;
   int rc = ensure_pair_buffers(c, (int)TI, a.P, NACC);
   if (rc) return rc;
-  s.nc = (int)std::max<int64_t>(1, (a.n_it - 1 + sym_chunk<Pol>() - 1) / sym_chunk<Pol>());
+  const int64_t max_rows = a.n_it - 1 + (HasDiagSym<Pol>::value ? 1 : 0);  // of the last tile
+  s.nc = (int)std::max<int64_t>(1, (max_rows + sym_chunk<Pol>() - 1) / sym_chunk<Pol>());
   const size_t need_row = (size_t)a.n_it * NACC * TI * sizeof(double);
   const size_t need_col = (size_t)a.U * TJ * NACC * sizeof(typename Pol::ColT);
   const size_t need_chunk = (size_t)a.n_it * s.nc * NACC * TI * sizeof(double);
