@@ -33,6 +33,8 @@ namespace {
 constexpr int kGraphSteps = 10;  // even: three mirror flips per step keep the parity
 // Record bytes of the systems one wave of the Newton's-third-law pair phase works on.
 constexpr int64_t kWaveRecordBytes = 32ll << 20;
+// Virtual CTAs per CTA of the Newton's-third-law pair phase, at least.
+constexpr int kMinWaves = 4;
 
 struct SysDesc {
   double *q, *p, *f;
@@ -55,7 +57,8 @@ struct PartArgs {
   double *slots;
   unsigned *tickets;
   // symmetric form
-  int waves;         // virtual CTAs per physical CTA: P = waves x grid, CTA c runs c, grid + c, ...
+  int waves;         // virtual CTAs per physical CTA: P = waves x grid
+  unsigned *next;    // next virtual CTA to take (the finish kernel sets it back to 0)
   int m;             // TI / TJ of the part
   int64_t nfin;      // finish CTAs of the part
   double *rowfull;   // [rows][NACC][TI]
@@ -444,17 +447,29 @@ constexpr int sym_smem_bytes() {
 
 // One launch per part, each sized by its own occupancy (the parts' systems are
 // disjoint, so the launches simply follow each other on the stream).
-// The part's P = waves x gridDim.x stream-K ranges are virtual CTAs: CTA c runs c,
-// gridDim.x + c, ... in turn, so at any time all CTAs work in the same 1/waves of the
-// unit list (the same few systems), whose j-records then stay in L2.
+// The part's P = waves x gridDim.x stream-K ranges are virtual CTAs, which the CTAs
+// take in increasing order from an atomic counter: a CTA that the SM's warp
+// schedulers served faster takes more of them (the CTAs sharing an SM progress
+// unevenly, and with a static split the SM's last CTA ran alone at the end), and at
+// any time all CTAs work in about the same 1/waves of the unit list (the same few
+// systems), whose j-records then stay in L2.
 template <class Pol>
 __global__ void __launch_bounds__(NT, Pol::MINB) batch_sym_pairs_kernel(PartArgs part) {
   __shared__ __align__(16) unsigned char smem[sym_smem_bytes<Pol>()];
-  for (int w = 0; w < part.waves; w++) batch_sym_pairs<Pol>(part, (int64_t)w * gridDim.x + blockIdx.x, smem);
+  __shared__ unsigned s_vc;
+  for (;;) {
+    if (threadIdx.x == 0) s_vc = atomicAdd(part.next, 1u);
+    __syncthreads();
+    const unsigned vc = s_vc;
+    __syncthreads();
+    if (vc >= (unsigned)part.P) break;
+    batch_sym_pairs<Pol>(part, (int64_t)vc, smem);
+  }
 }
 
 template <class PolR, class PolG, int MODE>
 __global__ void __launch_bounds__(kFinishThreadsB) batch_sym_finish_kernel(PartArgs ring, PartArgs grav) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ring.next = *grav.next = 0u;  // the pair kernels have ended
   if ((int64_t)blockIdx.x < ring.nfin)
     batch_sym_finish<PolR, MD_RING, MODE>(ring, blockIdx.x);
   else
@@ -604,7 +619,8 @@ int grow(md_batch *b, T *&ptr, size_t &have, size_t need, const char *what) {
 }
 
 int ensure_tickets(md_batch *b) {
-  const size_t nt = (size_t)(b->rows_r + b->rows_g);
+  // a ticket per row of both parts, then the two parts' virtual-CTA counters
+  const size_t nt = (size_t)(b->rows_r + b->rows_g) + 2;
   if (nt > b->tickets_count) {
     dev_free(b->tickets);
     b->tickets = (unsigned *)dev_alloc(nt * sizeof(unsigned));
@@ -661,10 +677,11 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   const int occ_r = occupancy(b, (const void *)kern_r), occ_g = occupancy(b, (const void *)kern_g);
   const int64_t Gr = std::min<int64_t>((int64_t)b->nsm * occ_r, b->Ur);
   const int64_t Gg = std::min<int64_t>((int64_t)b->nsm * occ_g, b->Ug);
-  // waves: the part's j-records over about a quarter of L2 (129 MB), at least 16 units
-  // per virtual CTA
+  // waves: the part's j-records over about a quarter of L2 (129 MB), and at least
+  // kMinWaves virtual CTAs per CTA to even out the CTAs' uneven progress; at least 16
+  // units per virtual CTA
   auto waves_of = [&](int64_t rec_bytes, int64_t U, int64_t G) -> int {
-    int64_t w = (rec_bytes + kWaveRecordBytes - 1) / kWaveRecordBytes;
+    int64_t w = std::max<int64_t>(kMinWaves, (rec_bytes + kWaveRecordBytes - 1) / kWaveRecordBytes);
     if (w > U / (16 * (G > 0 ? G : 1))) w = U / (16 * (G > 0 ? G : 1));
     return (int)std::max<int64_t>(1, std::min<int64_t>(w, 16));
   };
@@ -686,6 +703,7 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ar.U = b->Ur;
   ar.P = (int)Pr;
   ar.waves = Wr;
+  ar.next = b->tickets + b->rows_r + b->rows_g;
   ar.m = (int)(TIr / PolR::TJ);
   ar.nfin = b->nfin_r;
   ar.slots = b->slots;
@@ -698,6 +716,7 @@ int launch_batch_sym(md_batch *b, double bc, double dc) {
   ag.U = b->Ug;
   ag.P = (int)Pg;
   ag.waves = Wg;
+  ag.next = ar.next + 1;
   ag.m = (int)(TIg / PolG::TJ);
   ag.nfin = b->nfin_g;
   ag.slots = b->slots + slot_r;
