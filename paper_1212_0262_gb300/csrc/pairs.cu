@@ -6,12 +6,14 @@
 // TI = NT*R particles lives in registers (R per thread); j-tiles of TJ particles
 // of a position "mirror" are staged in shared memory with cp.async, double
 // buffered.  Every i visits every j (Newton's third law is not used, as in the
-// paper).  Work is split stream-K style: the grid is P persistent CTAs, and CTA
-// c takes the contiguous range [U c / P, U (c+1) / P) of the U = n_it * n_jt
-// (i-tile, j-tile) units in i-major order, so every CTA does the same number of
-// pair interactions.  An i-tile covered by several CTAs is finished by the last
-// of them to arrive (atomic ticket per i-tile, no waiting), which adds the FP64
-// partial sums in CTA order: results are deterministic.
+// paper).  Work is split stream-K style: the U = n_it * n_jt (i-tile, j-tile)
+// units in i-major order form P contiguous ranges [U c / P, U (c+1) / P)
+// ("virtual CTAs", about four per resident CTA), which the persistent CTAs take
+// in increasing order from an atomic counter (take_vcta), so every range holds the
+// same number of pair interactions and a CTA that its SM served faster takes more
+// ranges.  An i-tile covered by several ranges is finished by the last of them to
+// arrive (atomic ticket per i-tile, no waiting), which adds the FP64 partial sums
+// in range order: results are deterministic.
 //
 // Pair arithmetic (d = theta_i - theta_j, r = r_i - r_j):
 //   Ring:  f_i = -(1/(2 sqrt2 N)) sum_j sin d / (1 - cos d + eps)^(3/2)
@@ -54,11 +56,7 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
   static_assert(TILE_BYTES % 16 == 0, "tile must be a whole number of 16-byte chunks");
   __shared__ __align__(16) unsigned char sbuf[2][TILE_BYTES];
   __shared__ bool s_last;
-
-  const int64_t cta = blockIdx.x;
-  const int64_t u0 = unit_begin(a.U, a.P, cta), u1 = unit_begin(a.U, a.P, cta + 1);
-  if (u0 >= u1) return;
-  const int64_t first_row = u0 / a.n_jt;
+  __shared__ unsigned s_vc;
   const unsigned char *mir = (const unsigned char *)a.mirror_in;
 
   auto prefetch = [&](int buf, int64_t jt) {
@@ -67,100 +65,109 @@ __global__ void __launch_bounds__(NT, StreamkMinBlocks<Pol>::value) streamk_kern
     cp_async_commit();
   };
 
-  typename Pol::State st;
-  int64_t it = u0 / a.n_jt, jt = u0 % a.n_jt;
-  bool row_from_start = (jt == 0);
-  const int64_t ibase = SHARD ? a.row0 : 0;
-  int64_t i0 = ibase + it * TI;  // tile base; each thread's rows come from Pol::row_of
-  Pol::load(st, a.mirror_in, i0);
-  prefetch(0, jt);
+  for (;;) {
+    const int64_t cta = take_vcta(a.sched, s_vc);  // virtual CTA: its range, slots and tickets
+    if (cta >= a.P) break;
+    const int64_t u0 = unit_begin(a.U, a.P, cta), u1 = unit_begin(a.U, a.P, cta + 1);
+    if (u0 >= u1) continue;
+    const int64_t first_row = u0 / a.n_jt;
 
-  for (int64_t u = u0; u < u1; u++) {
-    const int buf = (int)((u - u0) & 1);
-    if (u + 1 < u1) {
-      prefetch(buf ^ 1, jt + 1 == a.n_jt ? 0 : jt + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const int64_t j0 = jt * TJ;
-    const bool diag = Pol::MASK && (j0 < i0 + TI) && (i0 < j0 + TJ);
-    if (diag)
-      Pol::template tile<true>(st, sbuf[buf], a, i0, j0);
-    else
-      Pol::template tile<false>(st, sbuf[buf], a, i0, j0);
-    __syncthreads();
-    jt++;
-    const bool row_end = (jt == a.n_jt);
-    if (row_end || u + 1 == u1) {
-      if (row_end && row_from_start) {
-        // this CTA covered the whole i-tile: finish it directly
-#pragma unroll
-        for (int r = 0; r < Pol::NR; r++) {
-          double ex[NACC];
-          Pol::total(st, r, ex);
-          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-          if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, ex);
-        }
+    typename Pol::State st;
+    int64_t it = u0 / a.n_jt, jt = u0 % a.n_jt;
+    bool row_from_start = (jt == 0);
+    const int64_t ibase = SHARD ? a.row0 : 0;
+    int64_t i0 = ibase + it * TI;  // tile base; each thread's rows come from Pol::row_of
+    Pol::load(st, a.mirror_in, i0);
+    prefetch(0, jt);
+
+    for (int64_t u = u0; u < u1; u++) {
+      const int buf = (int)((u - u0) & 1);
+      if (u + 1 < u1) {
+        prefetch(buf ^ 1, jt + 1 == a.n_jt ? 0 : jt + 1);
+        cp_async_wait<1>();
       } else {
-        // partial coverage: publish, and let the last contributor finish
-        const int slot = (it == first_row) ? 0 : 1;
-        double *sp = a.slots + ((cta * 2 + slot) * NACC) * TI;
-#pragma unroll
-        for (int r = 0; r < Pol::NR; r++) {
-          double ex[NACC];
-          Pol::total(st, r, ex);
-          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-          if (lr >= 0)
-#pragma unroll
-            for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
-        }
-        __threadfence();
-        __syncthreads();
-        const int64_t cf = cta_of_unit(a.U, a.P, it * a.n_jt);
-        const int64_t cl = cta_of_unit(a.U, a.P, (it + 1) * a.n_jt - 1);
-        if (threadIdx.x == 0) {
-          unsigned cnt = atomicAdd(&a.tickets[it], 1u) + 1u;
-          s_last = (cnt == (unsigned)(cl - cf + 1));
-        }
-        __syncthreads();
-        if (s_last) {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int64_t j0 = jt * TJ;
+      const bool diag = Pol::MASK && (j0 < i0 + TI) && (i0 < j0 + TJ);
+      if (diag)
+        Pol::template tile<true>(st, sbuf[buf], a, i0, j0);
+      else
+        Pol::template tile<false>(st, sbuf[buf], a, i0, j0);
+      __syncthreads();
+      jt++;
+      const bool row_end = (jt == a.n_jt);
+      if (row_end || u + 1 == u1) {
+        if (row_end && row_from_start) {
+          // this CTA covered the whole i-tile: finish it directly
+  #pragma unroll
+          for (int r = 0; r < Pol::NR; r++) {
+            double ex[NACC];
+            Pol::total(st, r, ex);
+            const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, ex);
+          }
+        } else {
+          // partial coverage: publish, and let the last contributor finish
+          const int slot = (it == first_row) ? 0 : 1;
+          double *sp = a.slots + ((cta * 2 + slot) * NACC) * TI;
+  #pragma unroll
+          for (int r = 0; r < Pol::NR; r++) {
+            double ex[NACC];
+            Pol::total(st, r, ex);
+            const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+            if (lr >= 0)
+  #pragma unroll
+              for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
+          }
           __threadfence();
-          double tot[Pol::NR][NACC];
-#pragma unroll
-          for (int r = 0; r < Pol::NR; r++)
-#pragma unroll
-            for (int d = 0; d < NACC; d++) tot[r][d] = 0.0;
-          for (int64_t c2 = cf; c2 <= cl; c2++) {
-            const int64_t fr = unit_begin(a.U, a.P, c2) / a.n_jt;
-            const int sl = (it == fr) ? 0 : 1;
-            const double *src = a.slots + ((c2 * 2 + sl) * NACC) * TI;
-#pragma unroll
+          __syncthreads();
+          const int64_t cf = cta_of_unit(a.U, a.P, it * a.n_jt);
+          const int64_t cl = cta_of_unit(a.U, a.P, (it + 1) * a.n_jt - 1);
+          if (threadIdx.x == 0) {
+            unsigned cnt = atomicAdd(&a.tickets[it], 1u) + 1u;
+            s_last = (cnt == (unsigned)(cl - cf + 1));
+          }
+          __syncthreads();
+          if (s_last) {
+            __threadfence();
+            double tot[Pol::NR][NACC];
+  #pragma unroll
+            for (int r = 0; r < Pol::NR; r++)
+  #pragma unroll
+              for (int d = 0; d < NACC; d++) tot[r][d] = 0.0;
+            for (int64_t c2 = cf; c2 <= cl; c2++) {
+              const int64_t fr = unit_begin(a.U, a.P, c2) / a.n_jt;
+              const int sl = (it == fr) ? 0 : 1;
+              const double *src = a.slots + ((c2 * 2 + sl) * NACC) * TI;
+  #pragma unroll
+              for (int r = 0; r < Pol::NR; r++) {
+                const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+                if (lr >= 0)
+  #pragma unroll
+                  for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + lr);
+              }
+            }
+  #pragma unroll
             for (int r = 0; r < Pol::NR; r++) {
               const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-              if (lr >= 0)
-#pragma unroll
-                for (int d = 0; d < NACC; d++) tot[r][d] += __ldcg(src + d * TI + lr);
+              if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, tot[r]);
             }
+            if (threadIdx.x == 0) a.tickets[it] = 0u;
           }
-#pragma unroll
-          for (int r = 0; r < Pol::NR; r++) {
-            const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-            if (lr >= 0) finish<Pol, MODEL, MIXED, MODE, SHARD>(a, i0 + lr, tot[r]);
-          }
-          if (threadIdx.x == 0) a.tickets[it] = 0u;
         }
-      }
-      if (row_end && u + 1 < u1) {
-        it++;
-        jt = 0;
-        row_from_start = true;
-        i0 = ibase + it * TI;
-        Pol::load(st, a.mirror_in, i0);
+        if (row_end && u + 1 < u1) {
+          it++;
+          jt = 0;
+          row_from_start = true;
+          i0 = ibase + it * TI;
+          Pol::load(st, a.mirror_in, i0);
+        }
       }
     }
   }
+  vcta_done(a.sched);
 }
 
 // Whole mirror from the FP64 state (and lambda_p for adjoint records), padding
@@ -287,11 +294,11 @@ int launch_streamk(md_ctx *c, PairArgs a) {
   a.n_it = (c->N + TI - 1) / TI;
   a.n_jt = (c->N + Pol::TJ - 1) / Pol::TJ;
   a.U = a.n_it * a.n_jt;
-  int64_t P = (int64_t)c->nsm * occ;
-  if (P > a.U) P = a.U;
-  a.P = (int)P;
+  const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
+  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
   int rc = ensure_pair_buffers(c, (int)TI, a.P, Pol::NACC);
   if (rc) return rc;
+  a.sched = pair_sched(c);
   a.mirror_in = c->mirror[c->mirror_cur];
   a.mirror_out = c->mirror[1 - c->mirror_cur];
   a.q = c->q;
@@ -299,7 +306,7 @@ int launch_streamk(md_ctx *c, PairArgs a) {
   a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
-  kern<<<a.P, NT, 0, c->stream>>>(a);
+  kern<<<(int)G, NT, 0, c->stream>>>(a);
   MD_LAUNCHED(c);
   if (MODE == STAGE_KICK_DRIFT || ((MODE == STAGE_ADJOINT || MODE == STAGE_TANGENT) && a.drift != 0.0))
     c->mirror_cur = 1 - c->mirror_cur;
@@ -420,11 +427,11 @@ int launch_streamk_shard(md_ctx *c, PairArgs a) {
   a.n_it = (c->N + TI - 1) / TI;
   a.n_jt = (c->n_total + Pol::TJ - 1) / Pol::TJ;
   a.U = a.n_it * a.n_jt;
-  int64_t P = (int64_t)c->nsm * occ;
-  if (P > a.U) P = a.U;
-  a.P = (int)P;
+  const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
+  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
   int rc = ensure_pair_buffers(c, (int)TI, a.P, Pol::NACC);
   if (rc) return rc;
+  a.sched = pair_sched(c);
   a.mirror_in = c->mirror[c->mirror_cur];
   a.mirror_out = c->mirror[1 - c->mirror_cur];
   a.q = c->q;
@@ -432,7 +439,7 @@ int launch_streamk_shard(md_ctx *c, PairArgs a) {
   a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
-  kern<<<a.P, NT, 0, c->stream>>>(a);
+  kern<<<(int)G, NT, 0, c->stream>>>(a);
   MD_LAUNCHED(c);
   if (MODE == STAGE_KICK_DRIFT) c->mirror_cur = 1 - c->mirror_cur;
   return MD_OK;
@@ -474,7 +481,8 @@ int ensure_pair_buffers(md_ctx *c, int TI, int P, int nacc) {
     }
     c->sk_slots_bytes = need_slots;
   }
-  size_t n_it = (size_t)((c->N + TI - 1) / TI);
+  // a ticket per i-tile, then the dynamic stream-K counters (pair_sched)
+  size_t n_it = (size_t)((c->N + TI - 1) / TI) + 2;
   if (n_it > c->sk_tickets_count) {
     dev_free(c->sk_tickets);
     c->sk_tickets = (unsigned *)dev_alloc(n_it * sizeof(unsigned));

@@ -167,6 +167,8 @@ struct PairArgs {
   // state arrays q, p, fout hold those rows only (leading dimension nrow); the
   // mirror and N stay global
   int64_t row0, nrow;
+  // dynamic stream-K: [0] next virtual CTA to take, [1] CTAs done (both 0 between launches)
+  unsigned *sched;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -182,6 +184,47 @@ __device__ __forceinline__ void cp_async_wait() {
 __host__ __device__ __forceinline__ int64_t unit_begin(int64_t U, int P, int64_t c) { return (U * c) / P; }
 // CTA whose range holds unit u: max c with U c / P <= u.
 __device__ __forceinline__ int64_t cta_of_unit(int64_t U, int P, int64_t u) { return ((u + 1) * P - 1) / U; }
+
+// Dynamic stream-K.  The U units are split into P static ranges ("virtual CTAs",
+// several per CTA), which the CTAs of the launch take in increasing order from
+// sched[0]: the CTAs that share an SM progress unevenly under its warp schedulers,
+// and with one static range per CTA the SM's last CTA ran alone, at a fraction of
+// the SM's throughput, at the end of every launch.  The ranges keep every partial
+// row and ticket of the static scheme; only their order of execution changes.
+__device__ __forceinline__ int64_t take_vcta(unsigned *sched, unsigned &s_slot) {
+  if (threadIdx.x == 0) s_slot = atomicAdd(sched, 1u);
+  __syncthreads();
+  const unsigned v = s_slot;
+  __syncthreads();
+  return (int64_t)v;
+}
+// After the CTA's last take: the last CTA of the launch to get here sets both
+// counters back to 0 (every other CTA has taken its last virtual CTA before it
+// counted itself done).
+__device__ __forceinline__ void vcta_done(unsigned *sched) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+      atomicExch(sched, 0u);
+      atomicExch(sched + 1, 0u);
+    }
+  }
+}
+
+// The two dynamic stream-K counters of a context: after the stream-K tickets (see
+// ensure_pair_buffers).
+inline unsigned *pair_sched(md_ctx *c) { return c->sk_tickets + c->sk_tickets_count - 2; }
+
+// Virtual CTAs of a dynamic stream-K launch of G CTAs over U units: kVctaPerCta per
+// CTA, at least 16 units each.
+constexpr int kVctaPerCta = 4;
+inline int64_t vcta_count(int64_t G, int64_t U) {
+  int64_t P = G * kVctaPerCta;
+  if (P > U / 16) P = U / 16;
+  if (P < G) P = G;
+  if (P > U) P = U;
+  return P < 1 ? 1 : P;
+}
 
 // Triangular unit table of the Newton's-third-law form: row I (i-tile of m
 // j-tiles) holds the j-tiles J = m I .. n_jt - 1.

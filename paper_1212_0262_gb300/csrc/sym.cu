@@ -23,11 +23,12 @@
 // a fixed order through shared memory) are stored as that unit's column partial
 // (FP32, [U][TJ][NACC]).
 //
-// Pair phase (sym_pairs_kernel, stream-K).  CTA c takes units
+// Pair phase (sym_pairs_kernel, stream-K).  Virtual CTA c (taken by the
+// persistent CTAs in increasing order, take_vcta) covers units
 // [U c / P, U (c+1) / P) in row-major order and writes the row partials of the
 // rows it covers (rowfull[T] when it covered all of row T, else the one-sided
-// kernel's two slots per CTA) and the column partial of each off-diagonal unit
-// (and of each diagonal one, with tile_diag).
+// kernel's two slots per virtual CTA) and the column partial of each off-diagonal
+// unit (and of each diagonal one, with tile_diag).
 //
 // Finish phase (sym_finish_kernel).  Tile T needs its row partials and the
 // column partials of the units (I', J), J in tile T, I' < T (I' <= T with
@@ -81,10 +82,7 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
   __shared__ __align__(16) unsigned char sbuf[2][TILE_BYTES];
   __shared__ __align__(16) unsigned char colraw[NW * TJ * NACC * sizeof(ColT)];
   ColT *colsm = (ColT *)colraw;
-
-  const int64_t cta = blockIdx.x;
-  const int64_t u0 = unit_begin(a.U, a.P, cta), u1 = unit_begin(a.U, a.P, cta + 1);
-  if (u0 >= u1) return;
+  __shared__ unsigned s_vc;
   const int m = s.m;
   const unsigned char *mir = (const unsigned char *)a.mirror_in;
   auto prefetch = [&](int buf, int64_t jt) {
@@ -93,65 +91,73 @@ __global__ void __launch_bounds__(Pol::THREADS, Pol::MINB) sym_pairs_kernel(Pair
     cp_async_commit();
   };
 
-  typename Pol::State st;
-  int64_t it = sym_row_of_unit(u0, a.n_it, a.n_jt, m);
-  const int64_t first_row = it;
-  int64_t jt = (int64_t)m * it + (u0 - sym_rowstart(it, a.n_jt, m));
-  bool row_from_start = (jt == (int64_t)m * it);
-  int64_t i0 = it * TI;
-  Pol::load(st, a.mirror_in, i0);
-  prefetch(0, jt);
+  for (;;) {
+    const int64_t cta = take_vcta(a.sched, s_vc);  // virtual CTA: its range and slots
+    if (cta >= a.P) break;
+    const int64_t u0 = unit_begin(a.U, a.P, cta), u1 = unit_begin(a.U, a.P, cta + 1);
+    if (u0 >= u1) continue;
 
-  for (int64_t u = u0; u < u1; u++) {
-    const int buf = (int)((u - u0) & 1);
-    const bool row_end = (jt + 1 == a.n_jt);
-    const int64_t next_jt = row_end ? (int64_t)m * (it + 1) : jt + 1;
-    if (u + 1 < u1) {
-      prefetch(buf ^ 1, next_jt);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const bool diag = jt < (int64_t)m * (it + 1);
-    if (!diag) Pol::tile_sym(st, sbuf[buf], a, colsm);
-    else if constexpr (DIAG_SYM) Pol::tile_diag(st, sbuf[buf], a, colsm, (int)(jt - (int64_t)m * it));
-    else Pol::template tile<true>(st, sbuf[buf], a, i0, jt * TJ);
-    __syncthreads();
-    if (!diag || DIAG_SYM) {
-      // column partial of this unit: the warps' sums in a fixed order (colsm is
-      // rewritten only after the next unit's first barrier)
-      ColT *dst = (ColT *)s.colslot + u * (int64_t)(TJ * NACC);
-      for (int idx = threadIdx.x; idx < TJ * NACC; idx += THR) {
-        ColT v = colsm[idx];
-#pragma unroll
-        for (int w = 1; w < NW; w++) v += colsm[w * TJ * NACC + idx];
-        dst[idx] = v;
+    typename Pol::State st;
+    int64_t it = sym_row_of_unit(u0, a.n_it, a.n_jt, m);
+    const int64_t first_row = it;
+    int64_t jt = (int64_t)m * it + (u0 - sym_rowstart(it, a.n_jt, m));
+    bool row_from_start = (jt == (int64_t)m * it);
+    int64_t i0 = it * TI;
+    Pol::load(st, a.mirror_in, i0);
+    prefetch(0, jt);
+
+    for (int64_t u = u0; u < u1; u++) {
+      const int buf = (int)((u - u0) & 1);
+      const bool row_end = (jt + 1 == a.n_jt);
+      const int64_t next_jt = row_end ? (int64_t)m * (it + 1) : jt + 1;
+      if (u + 1 < u1) {
+        prefetch(buf ^ 1, next_jt);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
-    }
-    if (row_end || u + 1 == u1) {
-      // this CTA's part of row it
-      double *sp = (row_end && row_from_start)
-                       ? s.rowfull + it * NACC * TI
-                       : a.slots + ((cta * 2 + (it == first_row ? 0 : 1)) * NACC) * TI;
-#pragma unroll
-      for (int r = 0; r < Pol::NR; r++) {
-        double ex[NACC];
-        Pol::total(st, r, ex);
-        const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
-        if (lr >= 0)
-#pragma unroll
-          for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
+      __syncthreads();
+      const bool diag = jt < (int64_t)m * (it + 1);
+      if (!diag) Pol::tile_sym(st, sbuf[buf], a, colsm);
+      else if constexpr (DIAG_SYM) Pol::tile_diag(st, sbuf[buf], a, colsm, (int)(jt - (int64_t)m * it));
+      else Pol::template tile<true>(st, sbuf[buf], a, i0, jt * TJ);
+      __syncthreads();
+      if (!diag || DIAG_SYM) {
+        // column partial of this unit: the warps' sums in a fixed order (colsm is
+        // rewritten only after the next unit's first barrier)
+        ColT *dst = (ColT *)s.colslot + u * (int64_t)(TJ * NACC);
+        for (int idx = threadIdx.x; idx < TJ * NACC; idx += THR) {
+          ColT v = colsm[idx];
+  #pragma unroll
+          for (int w = 1; w < NW; w++) v += colsm[w * TJ * NACC + idx];
+          dst[idx] = v;
+        }
       }
-      if (row_end && u + 1 < u1) {
-        it++;
-        row_from_start = true;
-        i0 = it * TI;
-        Pol::load(st, a.mirror_in, i0);
+      if (row_end || u + 1 == u1) {
+        // this CTA's part of row it
+        double *sp = (row_end && row_from_start)
+                         ? s.rowfull + it * NACC * TI
+                         : a.slots + ((cta * 2 + (it == first_row ? 0 : 1)) * NACC) * TI;
+  #pragma unroll
+        for (int r = 0; r < Pol::NR; r++) {
+          double ex[NACC];
+          Pol::total(st, r, ex);
+          const int lr = Pol::row_of(r);  // row offset in the tile, -1: another lane's
+          if (lr >= 0)
+  #pragma unroll
+            for (int d = 0; d < NACC; d++) sp[d * TI + lr] = ex[d];
+        }
+        if (row_end && u + 1 < u1) {
+          it++;
+          row_from_start = true;
+          i0 = it * TI;
+          Pol::load(st, a.mirror_in, i0);
+        }
       }
+      jt = next_jt;
     }
-    jt = next_jt;
   }
+  vcta_done(a.sched);
 }
 
 // Finish phase, one CTA per (tile T, chunk c of sym_chunk rows I' < T, or I' <= T
@@ -262,9 +268,8 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.n_it = (c->N + TI - 1) / TI;
   a.n_jt = s.m * a.n_it;
   a.U = sym_rowstart(a.n_it, a.n_jt, s.m);
-  int64_t P = (int64_t)c->nsm * occ;
-  if (P > a.U) P = a.U;
-  a.P = (int)P;
+  const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
+  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
   int rc = ensure_pair_buffers(c, (int)TI, a.P, NACC);
   if (rc) return rc;
   const int64_t max_rows = a.n_it - 1 + (HasDiagSym<Pol>::value ? 1 : 0);  // of the last tile
@@ -300,7 +305,8 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.epsd = MODEL == MD_RING ? 0.5 * c->eps : c->eps;  // 2D, 3D, sheets: eps
   a.slots = c->sk_slots;
   a.tickets = c->sk_tickets;
-  kern<<<a.P, THR, 0, c->stream>>>(a, s);
+  a.sched = pair_sched(c);
+  kern<<<(int)G, THR, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
   sym_finish_kernel<Pol, MODEL, MIXED, MODE><<<a.n_it * s.nc, kFinishThreads, 0, c->stream>>>(a, s);
   MD_LAUNCHED(c);
