@@ -129,6 +129,9 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "r_mixed"          i-particles per thread of the FP32 pair kernels (4 or 8)
  *   "r_fp64"           i-particles per thread of the FP64 pair kernels (2 or 4)
  *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
+ *   "pair_vcta"        stream-K ranges per resident CTA of the pair kernels, which the
+ *                      CTAs take in turn from a counter (1 to 32; 0 = the kernel's
+ *                      measured default: 8 for the symmetric Ring kernel, 4 otherwise)
  *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = default: 4 for the FP32
  *                      sine/cosine stages, the occupancy limit otherwise)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32

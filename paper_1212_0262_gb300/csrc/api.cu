@@ -306,6 +306,7 @@ int md_set_tuning(md_ctx *c, const char *key, int64_t value) {
   if (k == "r_mixed" && (value == 4 || value == 8)) c->pt.r_mixed = (int)value;
   else if (k == "r_fp64" && (value == 2 || value == 4)) c->pt.r_fp64 = (int)value;
   else if (k == "pair_ctas_per_sm" && value >= 0 && value <= 32) c->pt.ctas_per_sm = (int)value;
+  else if (k == "pair_vcta" && value >= 0 && value <= 32) c->pt.vcta = (int)value;
   else if (k == "hmf_ctas_per_sm" && value >= 0 && value <= 32) c->ht.ctas_per_sm = (int)value;
   else if (k == "ring_tc" && value >= 0 && value <= 2) c->pt.ring_tc = (int)value;
   else if (k == "symmetric" && (value == 0 || value == 1)) c->pt.symmetric = (int)value;

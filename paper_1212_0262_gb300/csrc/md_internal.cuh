@@ -23,6 +23,7 @@ struct PairTuning {
   int ring_tc = 1;    // Ring FP32: sin(d) and sin(d/2) from tensor-core MMAs (split TF32); 1: 4, 2: 2 m-blocks per warp
   int symmetric = 1;  // forward stages: each unordered pair once (Newton's third law)
   int ctas_per_sm = 0;  // 0: occupancy-derived
+  int vcta = 0;         // stream-K ranges per resident CTA (0: the kernel's default)
 };
 
 struct HmfTuning {

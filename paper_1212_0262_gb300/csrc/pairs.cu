@@ -295,7 +295,7 @@ int launch_streamk(md_ctx *c, PairArgs a) {
   a.n_jt = (c->N + Pol::TJ - 1) / Pol::TJ;
   a.U = a.n_it * a.n_jt;
   const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
-  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
+  a.P = (int)vcta_count(G, a.U, c->pt.vcta > 0 ? c->pt.vcta : 4);  // virtual CTAs
   int rc = ensure_pair_buffers(c, (int)TI, a.P, Pol::NACC);
   if (rc) return rc;
   a.sched = pair_sched(c);
@@ -428,7 +428,7 @@ int launch_streamk_shard(md_ctx *c, PairArgs a) {
   a.n_jt = (c->n_total + Pol::TJ - 1) / Pol::TJ;
   a.U = a.n_it * a.n_jt;
   const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
-  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
+  a.P = (int)vcta_count(G, a.U, c->pt.vcta > 0 ? c->pt.vcta : 4);  // virtual CTAs
   int rc = ensure_pair_buffers(c, (int)TI, a.P, Pol::NACC);
   if (rc) return rc;
   a.sched = pair_sched(c);

@@ -215,11 +215,10 @@ __device__ __forceinline__ void vcta_done(unsigned *sched) {
 // ensure_pair_buffers).
 inline unsigned *pair_sched(md_ctx *c) { return c->sk_tickets + c->sk_tickets_count - 2; }
 
-// Virtual CTAs of a dynamic stream-K launch of G CTAs over U units: kVctaPerCta per
-// CTA, at least 16 units each.
-constexpr int kVctaPerCta = 4;
-inline int64_t vcta_count(int64_t G, int64_t U) {
-  int64_t P = G * kVctaPerCta;
+// Virtual CTAs of a dynamic stream-K launch of G CTAs over U units: k per CTA (the
+// pair_vcta tuning, else the kernel's default), at least 16 units each.
+inline int64_t vcta_count(int64_t G, int64_t U, int k) {
+  int64_t P = G * k;
   if (P > U / 16) P = U / 16;
   if (P < G) P = G;
   if (P > U) P = U;

@@ -269,7 +269,9 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.n_jt = s.m * a.n_it;
   a.U = sym_rowstart(a.n_it, a.n_jt, s.m);
   const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
-  a.P = (int)vcta_count(G, a.U);                                      // virtual CTAs
+  // virtual CTAs: 8 per CTA for the Ring tensor-core kernel, 4 for the others (measured)
+  const int kv = c->pt.vcta > 0 ? c->pt.vcta : (Pol::FMT == 1 ? 8 : 4);
+  a.P = (int)vcta_count(G, a.U, kv);
   int rc = ensure_pair_buffers(c, (int)TI, a.P, NACC);
   if (rc) return rc;
   const int64_t max_rows = a.n_it - 1 + (HasDiagSym<Pol>::value ? 1 : 0);  // of the last tile
