@@ -132,3 +132,28 @@ def test_symmetric_falls_back_to_one_sided_beyond_the_column_cap():
     fo, scale = ora.force_rows(1, q, rows, 0.01, with_abs=True)
     assert np.all(np.abs(f[rows] - fo[0]) <= 2e-5 * scale[0])
     s.close()
+
+
+@pytest.mark.parametrize("symmetric", [1, 0])
+@pytest.mark.parametrize("model", [1, 2])
+def test_stream_k_range_counts_keep_parity(model, symmetric):
+    """pair_vcta: the units split into 1, 3, 5 or 32 ranges per resident CTA (fewer
+    where that would leave under 16 units a range), taken by the CTAs from a counter
+    that the launch's last CTA sets back to 0.  Forces match the oracle within the
+    FP32 bound for every split, over several consecutive launches (a counter left
+    non-zero would skip ranges of the next launch), and a split gives the same bits
+    every time."""
+    N = 40_000
+    q, _ = inputs.default_state(model, N, 1000 + N)
+    fo = ora.force(model, q, EPS[model])
+    scale = ora.force_abs(model, q, EPS[model])
+    for k in (1, 3, 5, 32):
+        s, _, _ = _sym(model, N, symmetric=symmetric)
+        s.set_tuning("pair_vcta", k)
+        s.set_state(q, np.zeros_like(q))
+        fs = [s.force() for _ in range(3)]
+        for f in fs:
+            err = np.abs(f - fo)
+            assert np.all(err <= 2e-5 * scale + 1e-300), (k, (err / np.maximum(scale, 1e-300)).max())
+        assert np.array_equal(fs[0], fs[1]) and np.array_equal(fs[0], fs[2]), k
+        s.close()
