@@ -131,7 +131,8 @@ int md_set_eps(md_ctx *ctx, double eps);
  *   "pair_ctas_per_sm" CTAs per SM of the pair kernels (0 = occupancy limit)
  *   "pair_vcta"        stream-K ranges per resident CTA of the pair kernels, which the
  *                      CTAs take in turn from a counter (1 to 32; 0 = the kernel's
- *                      measured default: 8 for the symmetric Ring kernel, 4 otherwise)
+ *                      measured default: 8 for the symmetric FP32 Ring kernel, 3 for the
+ *                      symmetric FP64 3D kernel, 4 otherwise)
  *   "hmf_ctas_per_sm"  CTAs per SM of the HMF stage kernels (0 = default: 4 for the FP32
  *                      sine/cosine stages, the occupancy limit otherwise)
  *   "ring_tc"          Ring FP32: sin(d) and sin(d/2) of Eq. 9 from split-TF32

@@ -269,8 +269,10 @@ int launch_sym(md_ctx *c, PairArgs a) {
   a.n_jt = s.m * a.n_it;
   a.U = sym_rowstart(a.n_it, a.n_jt, s.m);
   const int64_t G = std::min<int64_t>((int64_t)c->nsm * occ, a.U);  // CTAs
-  // virtual CTAs: 8 per CTA for the Ring tensor-core kernel, 4 for the others (measured)
-  const int kv = c->pt.vcta > 0 ? c->pt.vcta : (Pol::FMT == 1 ? 8 : 4);
+  // virtual CTAs per CTA, measured at the bench sizes (sweeps of 1-16 show sharp dips at
+  // single values, 4 for these two among them): 8 for the Ring tensor-core kernel, 3 for
+  // the FP64 3D kernel, 4 for the others
+  const int kv = c->pt.vcta > 0 ? c->pt.vcta : Pol::FMT == 1 ? 8 : (MODEL == MD_GRAV3D && !MIXED) ? 3 : 4;
   a.P = (int)vcta_count(G, a.U, kv);
   int rc = ensure_pair_buffers(c, (int)TI, a.P, NACC);
   if (rc) return rc;
