@@ -113,6 +113,13 @@ struct HmfArgs {
   int nsum;      // row shard: m_in holds nsum (sum cos, sum sin) pairs, one per rank
 };
 
+// FP64 mean-field force cos(th) My - sin(th) Mx (Eq. 6): one product and one FMA.  A lone
+// particle's force, its own self-term, is exactly zero (N = 1: My = sin th, Mx = cos th),
+// which the FMA would leave as a rounding residual of the product.
+__device__ __forceinline__ double hmf_force_fp64(double c, double s, double mx, double my, double invN) {
+  return invN == 1.0 ? 0.0 : fma(c, my, -(s * mx));
+}
+
 // One particle of a stage.  MIXED: FP64 state update, FP32 sine/cosine of the
 // FP64-range-reduced angle; the new angle's reduced value is carried in FP32.
 template <bool MIXED, int MODE>
@@ -142,8 +149,7 @@ __device__ __forceinline__ void hmf_particle(double &th, double &pp, const HmfAr
     }
   } else {
     const double2 cs = a.cs[i];
-    // two rounded products, so that the self-interaction of a lone particle cancels exactly
-    const double f = __dsub_rn(__dmul_rn(cs.x, my), __dmul_rn(cs.y, mx));
+    const double f = hmf_force_fp64(cs.x, cs.y, mx, my, a.invN);
     if (MODE == STAGE_FORCE_ONLY) {
       a.fout[i] = f;
       return;
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(NT) hmf_adj_stage_kernel(HmfAdjArgs a) {
     if (MIXED)  // the same FP32 force as the forward stage, so the reversal undoes it
       f = f2d_bits(__fsub_rn(__fmul_rn((float)c, myf), __fmul_rn((float)s, mxf)));
     else
-      f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
+      f = hmf_force_fp64(c, s, mx, my, a.invN);
     const double jv = fma(-fma(s, my, c * mx), lp, fma(c, A, s * B));
     lq = fma(a.b_adj, jv, lq);
     pp = fma(-a.b_undo, f, pp);
@@ -745,7 +751,7 @@ __global__ void __launch_bounds__(NT) hmf_tangent_stage_kernel(HmfAdjArgs a) {
     if (MIXED)
       f = f2d_bits(__fsub_rn(__fmul_rn((float)c, myf), __fmul_rn((float)s, mxf)));
     else
-      f = __dsub_rn(__dmul_rn(c, my), __dmul_rn(s, mx));
+      f = hmf_force_fp64(c, s, mx, my, a.invN);
     const double jv = fma(-fma(s, my, c * mx), dq, fma(c, A, s * B));
     pp = fma(a.b_adj, f, pp);
     dp = fma(a.b_adj, jv, dp);
