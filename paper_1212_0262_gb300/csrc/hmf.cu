@@ -25,6 +25,7 @@
 #include <mutex>
 
 #include "md_internal.cuh"
+#include "sincos_fp64.cuh"
 
 namespace {
 
@@ -38,45 +39,17 @@ constexpr int kFlush = 256;
 
 // ------------------------------------------------ FP64 sine and cosine ------
 //
-// Table-driven argument reduction (Tang, "Table-driven implementation of the
-// exponential function", ACM TOMS 15, 1989; used for sine and cosine by Gal and
-// Bachelis, ACM TOMS 17, 1991): theta = k h + r with h = pi/2048, k the nearest
-// integer to theta / h and |r| <= h/2 (1 + 1e-5) < 7.7e-4, then
-//   sin(theta) = S_k (1 + cm) + C_k sr,   cos(theta) = C_k (1 + cm) - S_k sr
-// with (S_k, C_k) = (sin, cos)(k h) from a 4096-entry FP64 table (k mod 4096) and
-//   sr = sin r = r - r^3 / 6                    (first omitted term r^5/5! < 2.3e-18)
-//   cm = cos r - 1 = r^2 (-1/2 + r^2 / 24)      (first omitted term r^6/6! < 3e-22)
-// k comes from the 1.5 * 2^52 rounding constant (its integer in the low mantissa bits),
-// and r = theta - k h from two FMAs with h split into h1 = fl(h) and h2 = fl(h - h1)
-// (each FMA forms k h_i exactly and rounds once; h - h1 - h2 is below 2e-36).
-// 13 FP64 operations instead of a full range reduction and two longer polynomials;
-// |theta| >= 2^30 (where k's rounding leaves |r| less tightly bounded), infinities and
-// NaN (found from the exponent bits, on the integer pipe) use sincos.  The table
-// (64 KB) sits in dynamic shared memory of the kernels that use it.
-constexpr int kTabN = 4096;
+// Table-driven (sincos_fp64.cuh): theta = k pi/2048 + r, a 4096-entry FP64 table of
+// (sin, cos)(k pi/2048) in dynamic shared memory (64 KB) of the kernels that use it,
+// k and the terms of sin r and cos r below 2^-33 in FP32, 8 FP64 operations per angle;
+// |theta| >= 2^20, infinities and NaN use sincos.
+constexpr int kTabN = sc64::kTabN;
 constexpr int kTabBytes = kTabN * (int)sizeof(double2);
-constexpr double kTabH1 = 0x1.921fb54442d18p-10;  // pi / 2048 rounded to double
-constexpr double kTabH2 = 0x1.1a62633145c07p-64;  // pi / 2048 - kTabH1
-constexpr double kTabInvH = 0x1.45f306dc9c883p+9; // 2048 / pi
-constexpr double kRint = 6755399441055744.0;      // 1.5 * 2^52
 
 __device__ double2 g_sincos_tab[kTabN];  // (sin, cos)(k pi / 2048), k = 0 .. 4095
 
 __device__ __forceinline__ void sincos_tab(double th, const double2 *__restrict__ tab, double *sp, double *cp) {
-  if (((__double2hiint(th) >> 20) & 0x7ff) >= 1023 + 30) {  // |theta| >= 2^30, inf or NaN
-    sincos(th, sp, cp);
-    return;
-  }
-  const double m = fma(th, kTabInvH, kRint);
-  const int idx = __double2loint(m) & (kTabN - 1);
-  const double k = m - kRint;
-  const double r = fma(-k, kTabH2, fma(-k, kTabH1, th));
-  const double r2 = r * r;
-  const double sr = fma(r2 * r, -1.0 / 6.0, r);
-  const double cm = r2 * fma(r2, 1.0 / 24.0, -0.5);
-  const double2 t = tab[idx];
-  *sp = fma(t.x, cm, fma(t.y, sr, t.x));
-  *cp = fma(t.y, cm, fma(-t.x, sr, t.y));
+  sc64::sincos_tab(th, tab, sp, cp);
 }
 
 // The table into shared memory (every thread of the CTA takes part).
