@@ -51,6 +51,11 @@ WORKLOADS = {
 }
 # algorithmic bytes per particle per fused HMF stage: read + write FP64 theta and p
 HMF_BYTES_PER_PARTICLE_STAGE = 32
+# FP64-pipe operations per particle of the FP64 HMF stage (its bound): the force
+# cos(theta) My - sin(theta) Mx (product + FMA), the kick and the drift (2 FMA), the
+# table-driven sine and cosine of the new angle (8: exact FMA reduction, r^2, cos r - 1,
+# sin r, two FMAs each for the angle addition)
+HMF_FP64_OPS_PER_PARTICLE_STAGE = 12
 # FP32-pipe operations and SFU operations per pair in the mixed pair kernels
 PAIR_OPS = {1: (8, 1), 2: (6, 1), 3: (11, 1), 4: (4, 0)}
 # Per force-kernel variant (md_force_kernel): name, FP32 operations and SFU operations
@@ -509,6 +514,25 @@ def pair_roofline(workload, model, N, kcode, prec, stage_ms, clocks, tuned):
             "pair_terms_per_launch": terms, "avg_launch_ms": avg_ms}
 
 
+def hmf_fp64_roofline(particle_steps_per_s, rates, clocks):
+    """Roofline object of the FP64 HMF path, which the FP64 pipe bounds: 3 stages per step
+    of HMF_FP64_OPS_PER_PARTICLE_STAGE FP64 operations per particle, against the SM count
+    times the measured FP64 FMA rate per SM per clock (mdp_pipe_rates) at the SM clock
+    sampled during the timed region (the rate's own clock without one); also the
+    fraction at the maximum clock."""
+    nsm, dfma = float(rates[0]), float(rates[13])
+    mhz = clocks.get("sm_mhz") or float(rates[14])
+    max_mhz = clocks.get("sm_max_mhz") or mhz
+    achieved = particle_steps_per_s * 3 * HMF_FP64_OPS_PER_PARTICLE_STAGE
+    peak = nsm * dfma * mhz * 1e6
+    return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "FP64 op/s",
+            "frac": achieved / peak, "frac_at_max_clock": achieved / (peak * max_mhz / mhz), "traffic": None,
+            "kernel": "hmf_stage_kernel<fp64, kick+drift>",
+            "peak_derivation": {"sms": nsm, "fp64_ops_per_sm_clk": dfma,
+                                "fp64_ops_per_particle_stage": HMF_FP64_OPS_PER_PARTICLE_STAGE,
+                                "sm_mhz": mhz, "sm_max_mhz": max_mhz}}
+
+
 def secondary_pair(workload, K, W, local, prec="mixed"):
     """A short run of one pair configuration in the default kernels of `prec` (its own
     system, L2 flush, clock record and energy errors after the W warm-up steps and
@@ -655,6 +679,17 @@ def run_ours(args, w):
                     "timed_region_bytes": region_bytes, "avg_launch_ms": avg_ms, "launches": n_launch,
                     "timing": "CUDA events around md_step(K) on its stream",
                     "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"}
+        if args.prec == "fp64":
+            # the FP64 stage is bound by the FP64 pipe, not by HBM: that roofline, with the
+            # HBM figures beside it (a failure here leaves the HBM object and says why)
+            try:
+                hbm = roofline
+                roofline = hmf_fp64_roofline(N * K / (elapsed_ms * 1e-3), pipe_rates(), clocks)
+                roofline.update({"hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
+                                 "avg_launch_ms": avg_ms, "launches": n_launch, "timing": hbm["timing"]})
+            except Exception as e:  # noqa: BLE001 -- the line is printed either way
+                roofline = hbm
+                roofline["fp64_pipe_error"] = repr(e)
     else:
         units_per_step = 3 * N * N
         value = ws * 3 * N * N * K / (elapsed_ms * 1e-3)
@@ -693,6 +728,11 @@ def run_ours(args, w):
                 res[prec] = {"value": units / (ms * 1e-3), "ms_per_step": ms / ksh,
                              "rel_energy_error": abs((e_b - e_a) / e_a), "steps": ksh + 1}
         extra["fp64_path"] = res["fp64"]
+        if model == 0:  # its FP64-pipe roofline at the clock sampled in the timed region above
+            try:
+                extra["fp64_path"]["roofline"] = hmf_fp64_roofline(res["fp64"]["value"], pipe_rates(), clocks)
+            except Exception as e:  # noqa: BLE001 -- the line is printed either way
+                extra["fp64_path"]["roofline"] = {"error": repr(e)}
         extra["mixed_path_long_run"] = res["mixed"]
         T = res["mixed"]["steps"] * w["dt"]
         extra["energy_error"] = {"mixed_after_%d_steps" % (res["mixed"]["steps"]): res["mixed"]["rel_energy_error"],

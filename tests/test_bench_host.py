@@ -75,3 +75,22 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0
+
+
+def test_fp64_hmf_roofline_counts_three_stages_of_fp64_operations(bench):
+    """The FP64 HMF path's roofline: 3 stages x 12 FP64 operations per particle-step
+    against SMs x FP64 FMA per SM per clock x the sampled SM clock; without a clock
+    record, the rate's own clock."""
+    import numpy as np
+
+    rates = np.zeros(19)
+    rates[0], rates[13], rates[14] = 152, 2.0, 1900.0
+    r = bench.hmf_fp64_roofline(1.45e10, rates, {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0})
+    assert r["bound"] == "alu" and r["pipe"] == "fp64" and r["unit"] == "FP64 op/s"
+    assert r["achieved"] == pytest.approx(1.45e10 * 3 * 12)
+    assert r["peak"] == pytest.approx(152 * 2.0 * 2070e6)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) and 0.8 < r["frac"] < 0.85
+    assert r["frac_at_max_clock"] == pytest.approx(r["frac"])
+    r2 = bench.hmf_fp64_roofline(1.45e10, rates, {})
+    assert r2["peak"] == pytest.approx(152 * 2.0 * 1900e6)
+    json.dumps(r)
